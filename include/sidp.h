@@ -1,0 +1,172 @@
+/*
+ * libsidp -- sparse invariant-domain-preserving DG-SEM stage update with subcell
+ * convex limiting on Cartesian quadrilateral meshes (Pazner, arXiv 2004.08503),
+ * for NVIDIA GB300 (sm_103a).  Plain C ABI: pointers and sizes only.
+ *
+ * Method (one forward-Euler stage, Sec. 4, Eq. subcell-fct / convex-fct):
+ *   high-order DG-SEM residual r^H (strong form, Eq. dg-strong / ho-update, Lax-Friedrichs
+ *   flux Eq. lax-friedrichs) -> sparsified low-order IDP residual r^L (Eq. dg-idp, graph
+ *   viscosity Eq. dij) -> bar states (Eq. bar-states) and local bounds (Sec. 4.1.1, 4.3)
+ *   -> subcell antidiffusive fluxes (Sec. 4.1.3) -> nodal limiting coefficients (Zalesak
+ *   for the scalar or the density; Euler: specific-entropy minimum by a line search,
+ *   Eq. convex-provisional) -> face coefficients and limited update.  Time stepping is
+ *   SSP-RK3 with dt = CFL min_i m_i / (2 sum_{j != i} d-hat_ij) (Eq. cfl-low, Sec. 5).
+ *
+ * Conventions
+ *   - Mesh: nx*ny square elements of side h on [x0,x1]x[y0,y1] (h = (x1-x0)/nx = (y1-y0)/ny).
+ *     Element e = ey*nx + ex; node i = a*(p+1) + b inside it (a: y index, b: x index) at
+ *     (x0 + (ex + xi_b) h, y0 + (ey + xi_a) h), xi the Gauss-Lobatto points on [0,1].
+ *     Library node order: global node g = e*(p+1)^2 + i;  N = nx*ny*(p+1)^2.
+ *   - Host state arrays are field-major float64 [nc][N] (nc = 1 scalar, 4 Euler with
+ *     (rho, rho vx, rho vy, rho E)); they are owned by the caller and copied.
+ *   - The library owns all device memory.  Device buffers are only lent out by
+ *     sidp_device_state; the pointer stays valid until sidp_destroy.
+ *   - Every entry point returns a status and never throws.  sidp_step / sidp_stage
+ *     are asynchronous on the context's stream; sidp_get_* synchronise it.
+ *   - One context is used by one host thread at a time.
+ */
+#ifndef SIDP_H
+#define SIDP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SIDP_OK = 0,
+  SIDP_ERR_ARG = 1,          /* invalid argument or configuration                      */
+  SIDP_ERR_CUDA = 2,         /* a CUDA runtime call failed (see sidp_last_error)        */
+  SIDP_ERR_NONFINITE = 3,    /* the state holds NaN/Inf                                 */
+  SIDP_ERR_BOUNDS = 4,       /* inadmissible state (rho <= 0 or p <= 0 for Euler)       */
+  SIDP_ERR_ROOTFIND_CAP = 5, /* the entropy line search hit its iteration cap           */
+  SIDP_ERR_STATE = 6,        /* call out of order (e.g. stage 2 before stage 1)         */
+  SIDP_ERR_OOM = 7           /* device allocation failed                                */
+} sidp_status;
+
+typedef enum { SIDP_LAW_BURGERS2D = 1, SIDP_LAW_EULER2D = 2, SIDP_LAW_ADVECTION2D = 3 } sidp_law;
+typedef enum { SIDP_FP64 = 0, SIDP_MIXED = 1 } sidp_precision;
+typedef enum { SIDP_BC_PERIODIC = 0, SIDP_BC_OUTFLOW = 1, SIDP_BC_EXACT_STATE = 2 } sidp_bc;
+typedef enum { SIDP_LIMITER_NONE = 0, SIDP_LIMITER_LOW_ORDER = 1, SIDP_LIMITER_SUBCELL = 2 } sidp_limiter;
+
+typedef struct {
+  int law;          /* sidp_law.  Burgers: f(u) = u^2/2 (1,1) (Sec. 5.5); Euler: Eq. euler-flux;
+                       advection: f(u) = beta u with constant beta (Sec. 3.3)                     */
+  int p;            /* polynomial degree, 1..7                                                   */
+  int nx, ny;       /* elements per direction, >= 1                                              */
+  int precision;    /* SIDP_FP64: everything in float64.  SIDP_MIXED: float32 state and stage
+                       arithmetic, float64 time step reduction                                   */
+  double x0, x1, y0, y1;  /* domain; elements must be square                                     */
+  int bc[4];        /* sidp_bc for the W, E, S, N sides.  Periodic must be paired (W with E,
+                       S with N).  Outflow: ghost = interior trace.  Exact: ghost traces set by
+                       sidp_set_ghost_state                                                       */
+  double cfl;       /* in (0, 1]; the paper uses 1/2 (Sec. 5)                                    */
+  double gamma;     /* Euler ratio of specific heats, 1 < gamma <= 5/3 (wave-speed bound valid)  */
+  double adv_beta[2]; /* advection velocity                                                      */
+  int limiter;      /* sidp_limiter: HO target only, LO IDP only, or subcell FCT/convex limiting */
+} sidp_config;
+
+typedef struct {
+  double t;                     /* simulated time advanced by sidp_step                       */
+  long long steps;              /* SSP-RK3 steps taken by sidp_step                            */
+  double last_dt;               /* dt of the last step (or of the last sidp_compute_dt)         */
+  double mass[4];               /* sum_i m_i u_i per field (Sec. 2.4 conservation)              */
+  double umin[4], umax[4];      /* nodal min / max per field                                   */
+  double rho_min, p_min;        /* Euler: min density and pressure (0 for scalar laws)          */
+  double max_bound_violation;   /* max over stages and nodes of the relative excess of the
+                                   limited field (scalar or rho) over its local bounds          */
+  double max_entropy_violation; /* Euler: max over stages of max(0, 1 - sigma(u_i)/K_i)          */
+  int rootfind_max_iters;       /* largest iteration count of the entropy line search           */
+  long long rootfind_cap_hits;  /* line searches stopped by the iteration cap                   */
+  long long nonfinite;          /* number of non-finite values in the current state              */
+} sidp_diag;
+
+typedef struct sidp_ctx sidp_ctx;
+typedef struct sidp_batch sidp_batch;
+
+/* Create a context on the current CUDA device.  `cuda_stream` is a cudaStream_t (NULL for the
+ * legacy default stream); all work of the context is ordered on it.  Validates cfg (Sec. 2 mesh
+ * and law, Sec. 5 CFL) and allocates 3 state buffers plus small scratch.  On error *out = NULL. */
+sidp_status sidp_create(sidp_ctx** out, const sidp_config* cfg, void* cuda_stream);
+sidp_status sidp_destroy(sidp_ctx* ctx);
+
+/* Number of nodes N and fields nc. */
+sidp_status sidp_sizes(const sidp_ctx* ctx, long long* n_nodes, int* nc);
+
+/* Physical coordinates of all nodes in library node order (caller-owned arrays of N doubles). */
+sidp_status sidp_node_coords(const sidp_ctx* ctx, double* x, double* y);
+
+/* Copy a host float64 [nc][N] state in (rounded to float32 in SIDP_MIXED).  Euler states with
+ * rho <= 0 or p <= 0 anywhere return SIDP_ERR_BOUNDS (the invariant set of Sec. 4.3) and are
+ * not copied; non-finite values return SIDP_ERR_NONFINITE.  Resets the stage sequence. */
+sidp_status sidp_set_state(sidp_ctx* ctx, const double* u);
+
+/* Copy a state out as float64 [nc][N].  which = 0: the current solution u^n; 1: the stage-1
+ * result u^(1); 2: the stage-2 result u^(2) (SSP-RK3, Sec. 5).  Synchronises the stream. */
+sidp_status sidp_get_state(sidp_ctx* ctx, int which, double* u);
+
+/* Ghost trace for SIDP_BC_EXACT_STATE on `side` (0 W, 1 E, 2 S, 3 N): float64 [nc][n_side][p+1]
+ * with n_side = ny for W/E and nx for S/N, ordered along the side. */
+sidp_status sidp_set_ghost_state(sidp_ctx* ctx, int side, const double* u);
+
+/* Lend the device buffer of u^n: *dptr = device pointer of [nc][N] values of type *dtype
+ * (0 float64, 1 float32); *field_stride = N.  Valid until sidp_destroy. */
+sidp_status sidp_device_state(sidp_ctx* ctx, void** dptr, int* dtype, long long* field_stride);
+
+/* Eq. cfl-low: dt = cfl * min_i m_i / (2 sum_{j != i} d-hat_ij) on u^n; synchronises. */
+sidp_status sidp_compute_dt(sidp_ctx* ctx, double* dt);
+
+/* One SSP-RK3 stage with a given dt (k = 1, 2, 3; Sec. 5):
+ *   k=1: u^(1) = FE(u^n);  k=2: u^(2) = 3/4 u^n + 1/4 FE(u^(1));  k=3: u^n <- 1/3 u^n + 2/3 FE(u^(2)).
+ * FE is the limited forward-Euler update of Eq. subcell-fct / convex-fct.  Asynchronous. */
+sidp_status sidp_stage(sidp_ctx* ctx, int k, double dt);
+
+/* nsteps SSP-RK3 steps, each with dt from Eq. cfl-low evaluated on u^n (computed on the
+ * device; no host synchronisation).  Asynchronous.  The first call captures one step as a
+ * CUDA graph (when use_graph is on) and later calls replay it. */
+sidp_status sidp_step(sidp_ctx* ctx, int nsteps);
+
+/* Enable (1) or disable (0) CUDA-graph replay in sidp_step (default 1). */
+sidp_status sidp_set_graph(sidp_ctx* ctx, int use_graph);
+
+/* Enable (1) / disable (0) per-stage bound statistics (default 1); off saves one entropy
+ * evaluation per node and a few reductions per stage. */
+sidp_status sidp_set_stats(sidp_ctx* ctx, int on);
+
+/* Debug capture: when on, every later stage writes its local bounds (lo, hi of the limited field;
+ * K_i = min sigma for Euler) and nodal alpha-tilde to device buffers that sidp_get_bounds copies
+ * out (caller-owned arrays of N doubles each; any pointer may be NULL). */
+sidp_status sidp_set_debug(sidp_ctx* ctx, int on);
+sidp_status sidp_get_bounds(sidp_ctx* ctx, double* lo, double* hi, double* K, double* alpha);
+
+/* Diagnostics of the current state plus the statistics accumulated since the last set_state
+ * (struct above).  Synchronises. */
+sidp_status sidp_get_diag(sidp_ctx* ctx, sidp_diag* out);
+
+/* Wait for all work queued on the context's stream. */
+sidp_status sidp_synchronize(sidp_ctx* ctx);
+
+const char* sidp_status_str(sidp_status s);
+/* Message of the last error on this context (static storage when ctx is NULL). */
+const char* sidp_last_error(const sidp_ctx* ctx);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent problems (each its own mesh, p, law, BCs, dt) advanced together: one
+ * launch per RK stage covers every instance (a task table of (instance, element tile)
+ * entries, grouped by p), and a whole step is captured in one CUDA graph.  All configs
+ * of a batch must share law and precision. */
+sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int count, void* cuda_stream);
+sidp_status sidp_batch_destroy(sidp_batch* b);
+sidp_status sidp_batch_sizes(const sidp_batch* b, int i, long long* n_nodes, int* nc);
+sidp_status sidp_batch_total_nodes(const sidp_batch* b, long long* n_nodes);
+sidp_status sidp_batch_node_coords(const sidp_batch* b, int i, double* x, double* y);
+sidp_status sidp_batch_set_state(sidp_batch* b, int i, const double* u);
+sidp_status sidp_batch_get_state(sidp_batch* b, int i, double* u);
+sidp_status sidp_batch_step(sidp_batch* b, int nsteps);
+sidp_status sidp_batch_get_diag(sidp_batch* b, int i, sidp_diag* out);
+sidp_status sidp_batch_synchronize(sidp_batch* b);
+const char* sidp_batch_last_error(const sidp_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SIDP_H */

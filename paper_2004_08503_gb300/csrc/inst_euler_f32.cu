@@ -1,0 +1,7 @@
+// Stage and time-step kernels of the euler law in float (one translation unit per law and
+// precision so that the builds run in parallel).
+#include "sidp_kernels.cuh"
+
+namespace sidp {
+SIDP_INSTANTIATE(LAW_EULER, LawEuler, float)
+}  // namespace sidp
