@@ -83,8 +83,9 @@ typedef struct {
 typedef struct sidp_ctx sidp_ctx;
 typedef struct sidp_batch sidp_batch;
 
-/* Create a context on the current CUDA device.  `cuda_stream` is a cudaStream_t (NULL for the
- * legacy default stream); all work of the context is ordered on it.  Validates cfg (Sec. 2 mesh
+/* Create a context on the current CUDA device.  `cuda_stream` is a cudaStream_t; with NULL the
+ * library creates (and later destroys) its own non-blocking stream.  All work of the context is
+ * ordered on that stream.  Validates cfg (Sec. 2 mesh
  * and law, Sec. 5 CFL) and allocates 3 state buffers plus small scratch.  On error *out = NULL. */
 sidp_status sidp_create(sidp_ctx** out, const sidp_config* cfg, void* cuda_stream);
 sidp_status sidp_destroy(sidp_ctx* ctx);
@@ -103,6 +104,13 @@ sidp_status sidp_set_state(sidp_ctx* ctx, const double* u);
 /* Copy a state out as float64 [nc][N].  which = 0: the current solution u^n; 1: the stage-1
  * result u^(1); 2: the stage-2 result u^(2) (SSP-RK3, Sec. 5).  Synchronises the stream. */
 sidp_status sidp_get_state(sidp_ctx* ctx, int which, double* u);
+
+/* Asynchronous state transfer in the library's storage type (float64 for SIDP_FP64, float32
+ * for SIDP_MIXED), field-major [nc][N], ordered on the context's stream.  Use page-locked host
+ * memory for full bandwidth.  No validation and no conversion: the caller owns the contents.
+ * The host buffer must stay valid until sidp_synchronize (or any synchronising call). */
+sidp_status sidp_upload_state(sidp_ctx* ctx, const void* host);
+sidp_status sidp_download_state(sidp_ctx* ctx, int which, void* host);
 
 /* Ghost trace for SIDP_BC_EXACT_STATE on `side` (0 W, 1 E, 2 S, 3 N): float64 [nc][n_side][p+1]
  * with n_side = ny for W/E and nx for S/N, ordered along the side. */

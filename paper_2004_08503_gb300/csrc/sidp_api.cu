@@ -386,6 +386,20 @@ sidp_status sidp_get_state(sidp_ctx* c, int which, double* u) {
   return c->mixed ? download<float>(c, c->d_u[which], u, c->nc * c->N) : download<double>(c, c->d_u[which], u, c->nc * c->N);
 }
 
+sidp_status sidp_upload_state(sidp_ctx* c, const void* host) {
+  if (!c || !host) return fail(c, SIDP_ERR_ARG, "null argument");
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_u[0], host, (size_t)c->nc * c->N * c->esize, cudaMemcpyHostToDevice, c->stream));
+  c->stage_done = 0;
+  return SIDP_OK;
+}
+
+sidp_status sidp_download_state(sidp_ctx* c, int which, void* host) {
+  if (!c || !host) return fail(c, SIDP_ERR_ARG, "null argument");
+  if (which < 0 || which > 2) return fail(c, SIDP_ERR_ARG, "which must be 0, 1 or 2");
+  CUDA_TRY(c, cudaMemcpyAsync(host, c->d_u[which], (size_t)c->nc * c->N * c->esize, cudaMemcpyDeviceToHost, c->stream));
+  return SIDP_OK;
+}
+
 sidp_status sidp_set_ghost_state(sidp_ctx* c, int side, const double* u) {
   if (!c || !u || side < 0 || side > 3) return fail(c, SIDP_ERR_ARG, "bad argument");
   const long long nside = (side < 2) ? c->cfg.ny : c->cfg.nx;

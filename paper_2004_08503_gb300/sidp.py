@@ -57,6 +57,8 @@ _SIGS = {
     "sidp_set_state": (ctypes.c_int, [_P, _D]),
     "sidp_get_state": (ctypes.c_int, [_P, ctypes.c_int, _D]),
     "sidp_set_ghost_state": (ctypes.c_int, [_P, ctypes.c_int, _D]),
+    "sidp_upload_state": (ctypes.c_int, [_P, _P]),
+    "sidp_download_state": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "sidp_device_state": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]),
     "sidp_compute_dt": (ctypes.c_int, [_P, _D]),
     "sidp_stage": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
@@ -170,6 +172,15 @@ def sidp_get_state(ctx, which=0):
     u = np.empty((nc, n))
     _check(load().sidp_get_state(ctx, which, _ptr(u)), ctx)
     return u
+
+
+def sidp_upload_state(ctx, host_ptr):
+    """host_ptr: address of a host buffer in the storage type (e.g. a pinned torch tensor's data_ptr())."""
+    _check(load().sidp_upload_state(ctx, host_ptr), ctx)
+
+
+def sidp_download_state(ctx, which, host_ptr):
+    _check(load().sidp_download_state(ctx, which, host_ptr), ctx)
 
 
 def sidp_set_ghost_state(ctx, side, u):
