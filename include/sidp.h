@@ -123,6 +123,19 @@ sidp_status sidp_device_state(sidp_ctx* ctx, void** dptr, int* dtype, long long*
 /* Eq. cfl-low: dt = cfl * min_i m_i / (2 sum_{j != i} d-hat_ij) on u^n; synchronises. */
 sidp_status sidp_compute_dt(sidp_ctx* ctx, double* dt);
 
+/* The time step of sidp_compute_dt for a caller-owned device state, with no device allocation.
+ * The paper has no counterpart: this serves callers that cannot allocate device memory where
+ * they need a time step (an application whose pool allocator owns all device memory, a real-time
+ * loop that cannot afford cudaMalloc's synchronisation, code holding only a raw device pointer).
+ * d_state: device pointer to the [nc][N] state in the storage type of cfg->precision (float64 or
+ * float32), library node order; d_dt: device pointer to one double that receives
+ * cfl * min_i m_i / (2 sum_{j != i} d-hat_ij) (0 when no wave moves).  Asynchronous on
+ * cuda_stream.  Periodic and outflow sides only.  Scratch lives in a fixed 512 KiB device array
+ * shared by all calls: at most 65536 * 256 = 16,777,216 nodes (else SIDP_ERR_ARG), and calls that
+ * overlap on the GPU race.  The first call on a device looks the array up (cudaGetSymbolAddress);
+ * make it before any stream capture. */
+sidp_status sidp_compute_dt_static(const sidp_config* cfg, const void* d_state, double* d_dt, void* cuda_stream);
+
 /* One SSP-RK3 stage with a given dt (k = 1, 2, 3; Sec. 5):
  *   k=1: u^(1) = FE(u^n);  k=2: u^(2) = 3/4 u^n + 1/4 FE(u^(1));  k=3: u^n <- 1/3 u^n + 2/3 FE(u^(2)).
  * FE is the limited forward-Euler update of Eq. subcell-fct / convex-fct.  Asynchronous. */

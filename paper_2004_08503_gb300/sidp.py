@@ -61,6 +61,7 @@ _SIGS = {
     "sidp_download_state": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "sidp_device_state": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]),
     "sidp_compute_dt": (ctypes.c_int, [_P, _D]),
+    "sidp_compute_dt_static": (ctypes.c_int, [ctypes.POINTER(sidp_config), _P, _P, _P]),
     "sidp_stage": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
     "sidp_step": (ctypes.c_int, [_P, ctypes.c_int]),
     "sidp_set_graph": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -198,6 +199,11 @@ def sidp_compute_dt(ctx):
     d = ctypes.c_double()
     _check(load().sidp_compute_dt(ctx, ctypes.byref(d)), ctx)
     return d.value
+
+
+def sidp_compute_dt_static(cfg, d_state, d_dt, stream=None):
+    """Time step for a caller-owned device state (device pointers as ints); allocates nothing."""
+    _check(load().sidp_compute_dt_static(ctypes.byref(cfg), d_state, d_dt, _stream_handle(stream)))
 
 
 def sidp_stage(ctx, k, dt):
