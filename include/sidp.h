@@ -146,6 +146,11 @@ sidp_status sidp_stage(sidp_ctx* ctx, int k, double dt);
  * CUDA graph (when use_graph is on) and later calls replay it. */
 sidp_status sidp_step(sidp_ctx* ctx, int nsteps);
 
+/* Element tile (elements per CTA along x and y) that the stage kernels use; chosen per
+ * (law, p, precision) by timing the candidates at the first sidp_step (SIDP_TILE=<0..3> forces
+ * one, SIDP_AUTOTUNE=0 keeps the default, SIDP_TUNE_FILE=<path> persists the choices). */
+sidp_status sidp_get_tile(const sidp_ctx* ctx, int* tx, int* ty);
+
 /* Enable (1) or disable (0) CUDA-graph replay in sidp_step (default 1). */
 sidp_status sidp_set_graph(sidp_ctx* ctx, int use_graph);
 

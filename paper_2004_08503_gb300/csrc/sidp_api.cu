@@ -2,11 +2,13 @@
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
-#include "../../include/sidp.h"
+#include "sidp.h"
 #include "sidp_internal.h"
 
 using namespace sidp;
@@ -14,14 +16,18 @@ using namespace sidp;
 namespace {
 
 // ---------------------------------------------------------------- small kernels
-__global__ void k_set_scalar(double* dst, double v) { *dst = v; }
+__global__ void k_set_scalar(double* dst, double v) {
+  dst[0] = v;
+  *reinterpret_cast<float*>(dst + 2) = (float)v;
+}
 
 // dt = cfl * min (Eq. cfl-low with the CFL constant); 0 when no wave moves; advances the clock
 // and re-arms the min accumulator for the next step.
 __global__ void k_dt_finalize(unsigned long long* bits, double cfl, double* dt, double* clock) {
   const double mn = __longlong_as_double((long long)*bits);
   const double v = (mn < DBL_MAX) ? cfl * mn : 0.0;
-  *dt = v;
+  dt[0] = v;
+  *reinterpret_cast<float*>(dt + 2) = (float)v;
   if (clock) *clock += v;
   *bits = (unsigned long long)__double_as_longlong(DBL_MAX);
 }
@@ -100,7 +106,7 @@ struct sidp_ctx {
   bool own_stream = false;
   void* d_u[3] = {nullptr, nullptr, nullptr};  // u^n, u^(1), u^(2)
   void* d_ghost[4] = {nullptr, nullptr, nullptr, nullptr};
-  double* d_scal = nullptr;  // [0] dt, [1] clock
+  double* d_scal = nullptr;  // [0] dt, [1] clock, [2] dt as float32
   unsigned long long* d_bits = nullptr;
   StageStats* d_stats = nullptr;
   double* d_dbg = nullptr;  // 4 * N
@@ -112,6 +118,8 @@ struct sidp_ctx {
   long long steps = 0;
   cudaGraphExec_t graph = nullptr;
   bool graph_warm = false;
+  int tile = 0;          // index into kTiles[p]
+  bool tuned = false;
   double xi[kMaxN], w[kMaxN], D[kMaxN * kMaxN];
   std::string err;
 };
@@ -131,6 +139,11 @@ sidp_status fail(sidp_ctx* c, sidp_status s, const std::string& msg) {
       return fail(ctx, SIDP_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));         \
   } while (0)
 
+// d_scal layout: [0] dt (float64), [1] simulated time, [2] dt as float32 (low 4 bytes)
+template <typename T> const T* dt_ptr(const sidp_ctx* c);
+template <> const double* dt_ptr<double>(const sidp_ctx* c) { return c->d_scal; }
+template <> const float* dt_ptr<float>(const sidp_ctx* c) { return reinterpret_cast<const float*>(c->d_scal + 2); }
+
 template <typename T>
 void fill_launch(const sidp_ctx* c, StageLaunch<T>& L) {
   std::memset(&L, 0, sizeof(L));
@@ -142,12 +155,12 @@ void fill_launch(const sidp_ctx* c, StageLaunch<T>& L) {
     L.inst.ghost[s] = static_cast<const T*>(c->d_ghost[s]);
   }
   L.inst.h = c->h;
+  L.inst.hT = T(c->h);
   L.inst.dt = c->d_scal;
+  L.inst.dtT = dt_ptr<T>(c);
   for (int i = 0; i < c->n; ++i) L.tab.w[i] = T(c->w[i]);
   for (int i = 0; i < c->n * c->n; ++i) L.tab.D[i] = T(c->D[i]);
-  L.lp.gamma = c->cfg.gamma;
-  L.lp.beta[0] = c->cfg.adv_beta[0];
-  L.lp.beta[1] = c->cfg.adv_beta[1];
+  L.lp = make_law_params<T>(c->cfg.gamma, c->cfg.adv_beta);
   L.limiter = c->cfg.limiter;
   if (c->debug) {
     L.inst.dbg_lo = c->d_dbg;
@@ -158,22 +171,26 @@ void fill_launch(const sidp_ctx* c, StageLaunch<T>& L) {
   L.inst.stats = c->stats_on ? c->d_stats : nullptr;
 }
 
-template <typename T>
-cudaError_t dispatch_stage(int law, int p, const StageLaunch<T>& a, cudaStream_t s) {
-  switch (law) {
-    case LAW_BURGERS: return launch_stage_law<LAW_BURGERS, T>(p, a, s);
-    case LAW_EULER: return launch_stage_law<LAW_EULER, T>(p, a, s);
-    case LAW_ADVECTION: return launch_stage_law<LAW_ADVECTION, T>(p, a, s);
+template <int LAW, typename T>
+cudaError_t launch_law(int p, int tile, const StageLaunch<T>& a, unsigned long long* bits, cudaStream_t s) {
+  switch (p) {
+    case 1: return launch_p<LAW, T, 1>(tile, a, bits, s);
+    case 2: return launch_p<LAW, T, 2>(tile, a, bits, s);
+    case 3: return launch_p<LAW, T, 3>(tile, a, bits, s);
+    case 4: return launch_p<LAW, T, 4>(tile, a, bits, s);
+    case 5: return launch_p<LAW, T, 5>(tile, a, bits, s);
+    case 6: return launch_p<LAW, T, 6>(tile, a, bits, s);
+    case 7: return launch_p<LAW, T, 7>(tile, a, bits, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <typename T>
-cudaError_t dispatch_dt(int law, int p, const StageLaunch<T>& a, unsigned long long* bits, cudaStream_t s) {
+cudaError_t dispatch(int law, int p, int tile, const StageLaunch<T>& a, unsigned long long* bits, cudaStream_t s) {
   switch (law) {
-    case LAW_BURGERS: return launch_dt_law<LAW_BURGERS, T>(p, a, bits, s);
-    case LAW_EULER: return launch_dt_law<LAW_EULER, T>(p, a, bits, s);
-    case LAW_ADVECTION: return launch_dt_law<LAW_ADVECTION, T>(p, a, bits, s);
+    case LAW_BURGERS: return launch_law<LAW_BURGERS, T>(p, tile, a, bits, s);
+    case LAW_EULER: return launch_law<LAW_EULER, T>(p, tile, a, bits, s);
+    case LAW_ADVECTION: return launch_law<LAW_ADVECTION, T>(p, tile, a, bits, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -189,7 +206,7 @@ cudaError_t run_stage_t(sidp_ctx* c, int k) {
   if (k == 1) { L.inst.uin = un; L.inst.u0 = un; L.inst.uout = u1; L.inst.c0 = T(0); L.inst.c1 = T(1); }
   else if (k == 2) { L.inst.uin = u1; L.inst.u0 = un; L.inst.uout = u2; L.inst.c0 = T(0.75); L.inst.c1 = T(0.25); }
   else { L.inst.uin = u2; L.inst.u0 = un; L.inst.uout = un; L.inst.c0 = T(1.0 / 3.0); L.inst.c1 = T(2.0 / 3.0); }
-  return dispatch_stage<T>(c->cfg.law, c->cfg.p, L, c->stream);
+  return dispatch<T>(c->cfg.law, c->cfg.p, c->tile, L, nullptr, c->stream);
 }
 
 cudaError_t run_stage(sidp_ctx* c, int k) { return c->mixed ? run_stage_t<float>(c, k) : run_stage_t<double>(c, k); }
@@ -199,7 +216,7 @@ cudaError_t run_dt_t(sidp_ctx* c, bool advance_clock) {
   StageLaunch<T> L;
   fill_launch(c, L);
   L.inst.uin = static_cast<const T*>(c->d_u[0]);
-  cudaError_t e = dispatch_dt<T>(c->cfg.law, c->cfg.p, L, c->d_bits, c->stream);
+  cudaError_t e = dispatch<T>(c->cfg.law, c->cfg.p, c->tile, L, c->d_bits, c->stream);
   if (e != cudaSuccess) return e;
   k_dt_finalize<<<1, 1, 0, c->stream>>>(c->d_bits, c->cfg.cfl, c->d_scal, advance_clock ? c->d_scal + 1 : nullptr);
   return cudaGetLastError();
@@ -211,6 +228,89 @@ cudaError_t run_step(sidp_ctx* c) {
   cudaError_t e = run_dt(c, true);
   for (int k = 1; k <= 3 && e == cudaSuccess; ++k) e = run_stage(c, k);
   return e;
+}
+
+// ---------------------------------------------------------------- tile autotuner
+// Picks the element tile shape per (law, p, precision) by timing stage 1 of every candidate in
+// kTiles[p] on the context's current state, once per process (results are identical across
+// shapes: each face and node is evaluated from the same inputs in the same order).  SIDP_TILE=<i>
+// forces a candidate, SIDP_AUTOTUNE=0 keeps the default; SIDP_TUNE_FILE=<path> loads and stores
+// the table ("law p precision tile" lines).
+std::mutex g_tune_mu;
+int g_tune[4][kMaxP + 1][2];
+bool g_tune_init = false;
+
+void tune_table_init() {
+  if (g_tune_init) return;
+  for (auto& a : g_tune)
+    for (auto& b : a) b[0] = b[1] = -1;
+  if (const char* f = std::getenv("SIDP_TUNE_FILE")) {
+    if (FILE* fp = std::fopen(f, "r")) {
+      int law, p, mixed, tile;
+      while (std::fscanf(fp, "%d %d %d %d", &law, &p, &mixed, &tile) == 4)
+        if (law >= 1 && law <= 3 && p >= 1 && p <= kMaxP && (mixed == 0 || mixed == 1) && tile >= 0 && tile < kNumTiles)
+          g_tune[law][p][mixed] = tile;
+      std::fclose(fp);
+    }
+  }
+  g_tune_init = true;
+}
+
+void tune_table_store() {
+  const char* f = std::getenv("SIDP_TUNE_FILE");
+  if (!f) return;
+  if (FILE* fp = std::fopen(f, "w")) {
+    for (int law = 1; law <= 3; ++law)
+      for (int p = 1; p <= kMaxP; ++p)
+        for (int m = 0; m < 2; ++m)
+          if (g_tune[law][p][m] >= 0) std::fprintf(fp, "%d %d %d %d\n", law, p, m, g_tune[law][p][m]);
+    std::fclose(fp);
+  }
+}
+
+cudaError_t run_stage(sidp_ctx* c, int k);
+cudaError_t run_dt(sidp_ctx* c, bool adv);
+
+cudaError_t autotune(sidp_ctx* c) {
+  if (c->tuned) return cudaSuccess;
+  c->tuned = true;
+  if (const char* f = std::getenv("SIDP_TILE")) {
+    const int t = std::atoi(f);
+    if (t >= 0 && t < kNumTiles) c->tile = t;
+    return cudaSuccess;
+  }
+  const char* off = std::getenv("SIDP_AUTOTUNE");
+  if (off && off[0] == '0') return cudaSuccess;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_table_init();
+  int& slot = g_tune[c->cfg.law][c->cfg.p][c->mixed ? 1 : 0];
+  if (slot >= 0) { c->tile = slot; return cudaSuccess; }
+  cudaEvent_t e0, e1;
+  cudaError_t err = cudaEventCreate(&e0);
+  if (err != cudaSuccess) return err;
+  if ((err = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return err; }
+  float best = 1e30f;
+  int best_t = 0;
+  const int saved = c->tile;
+  for (int t = 0; t < kNumTiles && err == cudaSuccess; ++t) {
+    c->tile = t;
+    if ((err = run_dt(c, false)) != cudaSuccess) break;
+    if ((err = run_stage(c, 1)) != cudaSuccess) break;  // warm-up (and kernel attributes)
+    cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < 3 && err == cudaSuccess; ++r) err = run_stage(c, 1);
+    cudaEventRecord(e1, c->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    if (err == cudaSuccess && ms < best) { best = ms; best_t = t; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) { c->tile = saved; return err; }
+  c->tile = best_t;
+  slot = best_t;
+  tune_table_store();
+  return cudaSuccess;
 }
 
 void drop_graph(sidp_ctx* c) {
@@ -299,14 +399,14 @@ sidp_status sidp_create(sidp_ctx** out, const sidp_config* cfg, void* cuda_strea
   const size_t bytes = (size_t)c->nc * c->N * c->esize;
   for (int i = 0; i < 3; ++i)
     if (cudaMalloc(&c->d_u[i], bytes) != cudaSuccess) return bail(SIDP_ERR_OOM, "state allocation failed");
-  if (cudaMalloc(&c->d_scal, 2 * sizeof(double)) != cudaSuccess ||
+  if (cudaMalloc(&c->d_scal, 4 * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_bits, sizeof(unsigned long long)) != cudaSuccess ||
       cudaMalloc(&c->d_stats, sizeof(StageStats)) != cudaSuccess ||
       cudaMalloc(&c->d_wtab, kMaxN * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_part, kDiagBlocks * kDiagK * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_diag, kDiagK * sizeof(double)) != cudaSuccess)
     return bail(SIDP_ERR_OOM, "scratch allocation failed");
-  double zero2[2] = {0.0, 0.0};
+  double zero2[4] = {0.0, 0.0, 0.0, 0.0};
   const unsigned long long big = (unsigned long long)0x7fefffffffffffffULL;  // DBL_MAX bits
   StageStats zs{};
   if ((e = cudaMemcpy(c->d_scal, zero2, sizeof(zero2), cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -443,6 +543,10 @@ sidp_status sidp_step(sidp_ctx* c, int nsteps) {
   if (!c || nsteps < 0) return fail(c, SIDP_ERR_ARG, "bad argument");
   if (c->stage_done != 0) return fail(c, SIDP_ERR_STATE, "an SSP-RK3 step is half done (stage 1 or 2 ran)");
   int done = 0;
+  if (nsteps > 0 && !c->tuned) {
+    drop_graph(c);
+    CUDA_TRY(c, autotune(c));
+  }
   if (!c->use_graph || !c->graph_warm) {
     // first step eagerly: sets kernel attributes outside any capture
     if (nsteps > 0) {
@@ -542,6 +646,13 @@ sidp_status sidp_get_diag(sidp_ctx* c, sidp_diag* out) {
   out->rootfind_max_iters = (int)ss.rootfind_max_iters;
   out->rootfind_cap_hits = (long long)ss.rootfind_cap_hits;
   if (out->nonfinite) return fail(c, SIDP_ERR_NONFINITE, "state holds non-finite values");
+  return SIDP_OK;
+}
+
+sidp_status sidp_get_tile(const sidp_ctx* c, int* tx, int* ty) {
+  if (!c) return fail(nullptr, SIDP_ERR_ARG, "null context");
+  if (tx) *tx = kTiles[c->cfg.p][c->tile].tx;
+  if (ty) *ty = kTiles[c->cfg.p][c->tile].ty;
   return SIDP_OK;
 }
 

@@ -1,5 +1,5 @@
 // Batched execution of independent problems (placeholder until the batched scheduler lands).
-#include "../../include/sidp.h"
+#include "sidp.h"
 
 struct sidp_batch {
   int unused;

@@ -11,9 +11,51 @@ constexpr int kMaxN = kMaxP + 1;
 enum Law { LAW_BURGERS = 1, LAW_EULER = 2, LAW_ADVECTION = 3 };
 
 // Physical parameters of a law.
-struct LawParams {
-  double gamma;      // Euler
-  double beta[2];    // advection
+// Law constants in the stage precision T, computed once on the host (float kernels must not
+// convert from float64 per call: float64 throughput on this GPU is a small fraction of float32).
+template <typename T>
+struct LawParamsT {
+  T gamma;      // Euler ratio of specific heats
+  T gm1;        // gamma - 1
+  T half_gm1;   // (gamma - 1) / 2
+  T inv_gm1;    // 1 / (gamma - 1)
+  T c_gp;       // (gamma + 1) / (2 gamma)
+  T neg_e;      // -(gamma - 1) / (2 gamma)
+  T inv_e;      // 2 gamma / (gamma - 1): exponent of the two-rarefaction pressure
+  T beta[2];    // advection velocity
+  int pow7;     // inv_e == 7 (gamma = 1.4): the float path multiplies instead of calling pow
+};
+
+template <typename T>
+inline LawParamsT<T> make_law_params(double gamma, const double* beta) {
+  LawParamsT<T> p{};
+  const double g = gamma > 1.0 ? gamma : 1.4;
+  p.gamma = T(g);
+  p.gm1 = T(g - 1.0);
+  p.half_gm1 = T(0.5 * (g - 1.0));
+  p.inv_gm1 = T(1.0 / (g - 1.0));
+  p.c_gp = T((g + 1.0) / (2.0 * g));
+  p.neg_e = T(-(g - 1.0) / (2.0 * g));
+  p.inv_e = T(2.0 * g / (g - 1.0));
+  p.beta[0] = T(beta[0]);
+  p.beta[1] = T(beta[1]);
+  p.pow7 = (2.0 * g / (g - 1.0) > 7.0 - 1e-12 && 2.0 * g / (g - 1.0) < 7.0 + 1e-12) ? 1 : 0;
+  return p;
+}
+
+// Element tile shapes (elements along x, y per CTA) for each degree; index 0 is the default and
+// the autotuner picks among them per (law, p, precision).
+struct TileShape { int tx, ty; };
+constexpr int kNumTiles = 4;
+constexpr TileShape kTiles[kMaxP + 1][kNumTiles] = {
+    {{0, 0}, {0, 0}, {0, 0}, {0, 0}},
+    {{8, 8}, {16, 4}, {4, 16}, {16, 8}},  // p=1: 256 / 256 / 256 / 512 threads
+    {{5, 5}, {7, 4}, {4, 7}, {7, 7}},     // p=2: 225 / 252 / 252 / 441
+    {{4, 4}, {8, 2}, {2, 8}, {8, 4}},     // p=3: 256 / 256 / 256 / 512
+    {{3, 3}, {5, 2}, {2, 5}, {4, 5}},     // p=4: 225 / 250 / 250 / 500
+    {{2, 3}, {3, 2}, {7, 1}, {3, 4}},     // p=5: 216 / 216 / 252 / 432
+    {{2, 2}, {5, 1}, {1, 5}, {3, 3}},     // p=6: 196 / 245 / 245 / 441
+    {{2, 2}, {4, 1}, {1, 4}, {4, 2}},     // p=7: 256 / 256 / 256 / 512
 };
 
 // Reference-element tables for one degree p, in the stage precision T.
@@ -39,11 +81,13 @@ struct Instance {
   const T* u0;       // u^n (RK combination), [nc][N]
   T* uout;           // stage output, [nc][N]
   const T* ghost[4]; // exact-state ghost traces [nc][n_side*(p+1)] (or null)
-  const double* dt;  // device scalar
+  const double* dt;  // device scalar (float64 copy, for the clock and the host)
+  const T* dtT;      // the same dt in the stage precision
   long long N;       // nodes per field
   int nx, ny;
   int bc[4];
   double h;
+  T hT;              // h in the stage precision
   T c0, c1;          // RK combination uout = c0 u0 + c1 FE(uin)
   // debug outputs (null = off), per node
   double* dbg_lo;
@@ -57,14 +101,9 @@ template <typename T>
 struct StageLaunch {
   Instance<T> inst;
   Tables<T> tab;
-  LawParams lp;
+  LawParamsT<T> lp;
   int limiter;
 };
-
-// Launchers (one translation unit per law and precision).
-template <typename T> cudaError_t launch_stage(int law, int p, const StageLaunch<T>& a, cudaStream_t s);
-template <typename T> cudaError_t launch_dt(int law, int p, const StageLaunch<T>& a,
-                                            unsigned long long* dtmin_bits, cudaStream_t s);
 
 // Host tables (float64), computed once.
 void gll_tables(int p, double* xi, double* w, double* D);
@@ -72,14 +111,16 @@ void gll_tables(int p, double* xi, double* w, double* D);
 }  // namespace sidp
 
 namespace sidp {
-// Per-law launchers, explicitly specialised in inst_<law>_<precision>.cu.
-template <int LAW, typename T> cudaError_t launch_stage_law(int p, const StageLaunch<T>& a, cudaStream_t s);
-template <int LAW, typename T>
-cudaError_t launch_dt_law(int p, const StageLaunch<T>& a, unsigned long long* bits, cudaStream_t s);
-#define SIDP_DECLARE(LAWID, TT)                                                                      \
-  template <> cudaError_t launch_stage_law<LAWID, TT>(int, const StageLaunch<TT>&, cudaStream_t);   \
-  template <> cudaError_t launch_dt_law<LAWID, TT>(int, const StageLaunch<TT>&, unsigned long long*, \
-                                                   cudaStream_t);
+// Launcher of the stage kernel (dt_bits == nullptr) or the time-step kernel (dt_bits != nullptr)
+// for one law, precision and degree with tile shape kTiles[P][tile]; explicitly specialised in
+// the inst_<law>_<precision>*.cu translation units.
+template <int LAW, typename T, int P>
+cudaError_t launch_p(int tile, const StageLaunch<T>& a, unsigned long long* dt_bits, cudaStream_t s);
+#define SIDP_DECLARE_P(LAWID, TT, P) \
+  template <> cudaError_t launch_p<LAWID, TT, P>(int, const StageLaunch<TT>&, unsigned long long*, cudaStream_t);
+#define SIDP_DECLARE(LAWID, TT) \
+  SIDP_DECLARE_P(LAWID, TT, 1) SIDP_DECLARE_P(LAWID, TT, 2) SIDP_DECLARE_P(LAWID, TT, 3) SIDP_DECLARE_P(LAWID, TT, 4) \
+  SIDP_DECLARE_P(LAWID, TT, 5) SIDP_DECLARE_P(LAWID, TT, 6) SIDP_DECLARE_P(LAWID, TT, 7)
 SIDP_DECLARE(LAW_BURGERS, double)
 SIDP_DECLARE(LAW_BURGERS, float)
 SIDP_DECLARE(LAW_EULER, double)
@@ -87,4 +128,19 @@ SIDP_DECLARE(LAW_EULER, float)
 SIDP_DECLARE(LAW_ADVECTION, double)
 SIDP_DECLARE(LAW_ADVECTION, float)
 #undef SIDP_DECLARE
+#undef SIDP_DECLARE_P
+
+// Instantiate launch_p for one law/precision/degree (used by the inst_*.cu files).
+#define SIDP_INSTANTIATE_P(LAWID, LAWTPL, TT, P)                                                       \
+  template <>                                                                                          \
+  cudaError_t launch_p<LAWID, TT, P>(int tile, const StageLaunch<TT>& a, unsigned long long* bits,     \
+                                     cudaStream_t s) {                                                 \
+    switch (tile) {                                                                                    \
+      case 0: return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT>(a, bits, s);     \
+      case 1: return launch_tile<P, kTiles[P][1].tx, kTiles[P][1].ty, LAWTPL<TT>, TT>(a, bits, s);     \
+      case 2: return launch_tile<P, kTiles[P][2].tx, kTiles[P][2].ty, LAWTPL<TT>, TT>(a, bits, s);     \
+      case 3: return launch_tile<P, kTiles[P][3].tx, kTiles[P][3].ty, LAWTPL<TT>, TT>(a, bits, s);     \
+      default: return cudaErrorInvalidValue;                                                           \
+    }                                                                                                  \
+  }
 }  // namespace sidp

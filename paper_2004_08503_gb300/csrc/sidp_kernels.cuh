@@ -1,26 +1,27 @@
-// Fused stage kernel and CFL time-step kernel, templated on degree P, law and precision T.
+// Fused stage kernel and CFL time-step kernel, templated on degree P, element tile TX x TY,
+// law and precision T.
 //
-// One CTA owns EPB elements; one thread owns one node (a, b) of one element.  A stage is
-// element-local once the 4(p+1) face-neighbour nodes are known, so the whole forward-Euler
-// update (Sec. 4, Eq. subcell-fct / convex-fct) plus the SSP-RK3 combination (Sec. 5) runs in
-// one kernel with three CTA barriers:
-//   A  load u (coalesced, element-major SoA) and the one face-neighbour node this thread
-//      touches in x and in y; node aux (velocity, pressure, sound speed), fluxes F_x, F_y and
-//      the entropy function sigma into shared memory
-//   B  subcell faces: thread b evaluates the x face to its left (q = b; q = 0 is the element
-//      face, with the neighbour's trace) and thread b = p also the right element face (q = n).
-//      Each face stores its flux -- the Lax-Friedrichs flux Eq. lax-friedrichs on element faces,
-//      the Rusanov flux of the sparsified operator on interior subcell faces (Eq. dg-idp with
-//      D-hat of Eq. didp and d_ij of Eq. dij) -- and the bar state of the limited field
-//      (Eq. bar-states).  Same for y.
-//   C  r^H (strong form, Eq. ho-update: line contraction with D_1D plus face corrections),
-//      r^L (difference of face fluxes), u^L, local bounds (Sec. 4.1.1 / 4.3), r = r^H - r^L
-//   D  subcell fluxes r-bar (prefix sums along lines, Sec. 4.1.3), nodal alpha-tilde
-//      (Zalesak on field 0; Euler: entropy line search over the gamma-scaled candidates)
+// A CTA owns a tile of TX x TY elements (an (TX n) x (TY n) grid of nodes, n = P + 1), one thread
+// per node.  A stage is element-local once the face-neighbour traces are known, so the whole
+// forward-Euler update (Sec. 4, Eq. subcell-fct / convex-fct) and the SSP-RK3 combination (Sec. 5)
+// run in one kernel:
+//   A  every node of the tile, plus the one-node halo around the tile, is loaded once; its
+//      per-node quantities (velocity, pressure, sound speed, p^{-(g-1)/(2g)}, sigma) and fluxes
+//      F_x, F_y go to shared memory.  Tile slots of elements outside a ragged mesh edge hold the
+//      boundary ghost of the adjacent element, so faces need no special case.
+//   B  every face of the node grid -- interior subcell faces and element faces alike -- is
+//      evaluated once by a uniform loop over threads: lambda (Sec. 2.1.1), the face flux
+//      1/2 (F_L + F_R) - lambda/2 (u_R - u_L) (the Lax-Friedrichs flux Eq. lax-friedrichs on
+//      element faces; the sparsified operator Eq. didp with d_ij of Eq. dij on subcell faces),
+//      and the bar state of the limited field (Eq. bar-states).
+//   C  per node: r^H (strong form, Eq. ho-update: line contraction with D_1D plus the face
+//      corrections), r^L (difference of face fluxes), u^L, the local bounds (Sec. 4.1.1 and 4.3)
+//   D  subcell fluxes r-bar (prefix sums along element lines, Sec. 4.1.3) and alpha-tilde
+//      (Zalesak on field 0; Euler: entropy line search over the gamma_d-scaled candidates)
 //   E  alpha_{m,k} = min of the two adjacent alpha-tilde; limited update; RK combination.
-// Every face flux is computed once and used by both adjacent nodes, and both elements sharing
-// an element face evaluate its flux with identical (left, right) arguments, so the update is
-// conservative to rounding.
+// Each face flux is computed once and read by both adjacent nodes; faces on tile boundaries are
+// computed by both tiles from identical (left, right) arguments.  Hence the update is
+// conservative up to the rounding of the final sums.
 #pragma once
 #include <cfloat>
 #include "sidp_internal.h"
@@ -34,44 +35,57 @@ template <typename T> struct Prec;
 template <> struct Prec<double> { static constexpr double root_tol = 1e-13; };
 template <> struct Prec<float> { static constexpr float root_tol = 2e-6f; };
 
-// Elements per CTA: about 256 threads; the CTA is padded to whole warps.
-__host__ __device__ constexpr int epb_for(int P) { return ((P + 1) * (P + 1) >= 256) ? 1 : 256 / ((P + 1) * (P + 1)); }
-__host__ __device__ constexpr int stage_threads(int P) { return ((epb_for(P) * (P + 1) * (P + 1) + 31) / 32) * 32; }
+template <typename T, int NC> struct alignas(NC == 4 ? 4 * sizeof(T) : sizeof(T)) Vec { T v[NC]; };
 
-template <int P, class LAW, typename T>
-struct ElemSmem {
-  static constexpr int n = P + 1, NN = n * n, NC = LAW::NC, NF = n * (n + 1);
-  T u[NC][NN];
-  T fx[NC][NN];  // F_x at the nodes, later r_x
-  T fy[NC][NN];  // F_y at the nodes, later r_y
-  T sig[LAW::kEntropy ? NN : 1];
-  T fbx[NC][NF];  // x-face fluxes, [f][a*(n+1) + q]
-  T fby[NC][NF];  // y-face fluxes, [f][b*(n+1) + q]
-  T bbx[NF];      // x-face bar state of field 0
-  T bby[NF];
-  T alpha[NN];
-  typename LAW::Aux aux[NN];
+template <int P, int TX, int TY>
+struct TileGeom {
+  static constexpr int n = P + 1, NN = n * n, NE = TX * TY, NT = NE * NN;
+  static constexpr int NX = TX * n, NY = TY * n;
+  static constexpr int NH = 2 * NX + 2 * NY;  // halo slots: W[NY], E[NY], S[NX], N[NX]
+  static constexpr int NS = NT + NH;
+  static constexpr int hW = NT, hE = NT + NY, hS = NT + 2 * NY, hN = NT + 2 * NY + NX;
+  static constexpr int NFX = NY * (NX + 1), NFY = NX * (NY + 1);  // x faces [row][c], y faces [r][col]
+  static constexpr int THREADS = ((NT + 31) / 32) * 32;
+  static constexpr int MINB = (THREADS <= 256) ? 4 : 2;  // register budget for 32 resident warps per SM
+  __device__ __forceinline__ static int slot(int row, int col) {
+    const int ty = row / n, a = row - ty * n, tx = col / n, b = col - tx * n;
+    return (ty * TX + tx) * NN + a * n + b;
+  }
 };
 
-template <int P, class LAW, typename T>
-constexpr size_t stage_smem_bytes() {
-  return epb_for(P) * sizeof(ElemSmem<P, LAW, T>) + sizeof(T) * ((P + 1) * (P + 1) + (P + 1));
-}
+template <int P, int TX, int TY, class LAW, typename T>
+struct TileSmem {
+  using G = TileGeom<P, TX, TY>;
+  using V = Vec<T, LAW::NC>;
+  V u[G::NS];
+  V fx[G::NS];  // F_x, later r_x on the node slots
+  V fy[G::NS];  // F_y, later r_y
+  V fbx[G::NFX];
+  V fby[G::NFY];
+  typename LAW::Aux aux[G::NS];
+  T sig[LAW::kEntropy ? G::NS : 1];
+  T bbx[G::NFX];
+  T bby[G::NFY];
+  T alpha[G::NT];
+  T D[G::NN];
+  T w[G::n];
+};
 
-// Trace of the neighbouring element across `side` (0 W, 1 E, 2 S, 3 N) at position `pos`
-// along the face.  Outflow (reading: ghost = interior trace) copies `own`.
+// Trace of the neighbouring element across `side` (0 W, 1 E, 2 S, 3 N) of element (ex, ey) at
+// position `pos` along the face.  Periodic wraps; outflow (reading: ghost = interior trace) copies
+// the element's own trace node; exact-state reads the ghost buffer.
 template <int P, int NC, typename T>
-__device__ __forceinline__ void neighbor_state(const Instance<T>& I, int side, long long e, int ex, int ey,
-                                               int pos, const T* own, T* out) {
+__device__ __forceinline__ void neighbor_trace(const Instance<T>& I, int side, int ex, int ey, int pos, T* out) {
   constexpr int n = P + 1, NN = n * n;
+  const long long e = (long long)ey * I.nx + ex;
   long long ne = -1;
-  int nd = 0;
-  int bc = I.bc[side];
+  int nd = 0, own = 0;
+  const int bc = I.bc[side];
   switch (side) {
-    case 0: nd = pos * n + P; ne = (ex > 0) ? e - 1 : (bc == 0 ? e + (I.nx - 1) : -1); break;
-    case 1: nd = pos * n; ne = (ex < I.nx - 1) ? e + 1 : (bc == 0 ? e - (I.nx - 1) : -1); break;
-    case 2: nd = P * n + pos; ne = (ey > 0) ? e - I.nx : (bc == 0 ? e + (long long)(I.ny - 1) * I.nx : -1); break;
-    default: nd = pos; ne = (ey < I.ny - 1) ? e + I.nx : (bc == 0 ? e - (long long)(I.ny - 1) * I.nx : -1); break;
+    case 0: nd = pos * n + P; own = pos * n; ne = (ex > 0) ? e - 1 : (bc == 0 ? e + (I.nx - 1) : -1); break;
+    case 1: nd = pos * n; own = pos * n + P; ne = (ex < I.nx - 1) ? e + 1 : (bc == 0 ? e - (I.nx - 1) : -1); break;
+    case 2: nd = P * n + pos; own = pos; ne = (ey > 0) ? e - I.nx : (bc == 0 ? e + (long long)(I.ny - 1) * I.nx : -1); break;
+    default: nd = pos; own = P * n + pos; ne = (ey < I.ny - 1) ? e + I.nx : (bc == 0 ? e - (long long)(I.ny - 1) * I.nx : -1); break;
   }
   if (ne >= 0) {
 #pragma unroll
@@ -83,20 +97,82 @@ __device__ __forceinline__ void neighbor_state(const Instance<T>& I, int side, l
     for (int f = 0; f < NC; ++f) out[f] = I.ghost[side][(f * nside + along) * n + pos];
   } else {
 #pragma unroll
-    for (int f = 0; f < NC; ++f) out[f] = own[f];
+    for (int f = 0; f < NC; ++f) out[f] = I.uin[f * I.N + e * NN + own];
   }
 }
 
-// Face between left state L and right state R along +e_k: Rusanov / LF flux and bar state of field 0.
-template <class LAW, typename T>
-__device__ __forceinline__ void face_eval(int k, const T* uL, const typename LAW::Aux& aL, const T* FL,
-                                          const T* uR, const typename LAW::Aux& aR, const T* FR,
-                                          const LawParams& lp, T* fb, T& bar0) {
+// Node quantities of a slot: state, aux, fluxes and (Euler) sigma.
+template <class LAW, typename T, class S>
+__device__ __forceinline__ void fill_slot(S& s, int slot, const T* uu, const LawParamsT<T>& lp) {
   constexpr int NC = LAW::NC;
-  const T lam = LAW::lam(k, uL, aL, uR, aR, lp);
+  typename LAW::Aux ax;
+  LAW::aux(uu, ax, lp);
+  Vec<T, NC> vu, vx, vy;
 #pragma unroll
-  for (int f = 0; f < NC; ++f) fb[f] = T(0.5) * (FL[f] + FR[f]) - T(0.5) * lam * (uR[f] - uL[f]);
-  bar0 = (lam > T(0)) ? T(0.5) * (uL[0] + uR[0]) - (FR[0] - FL[0]) / (T(2) * lam) : T(0.5) * (uL[0] + uR[0]);
+  for (int f = 0; f < NC; ++f) vu.v[f] = uu[f];
+  LAW::flux(uu, ax, 0, vx.v, lp);
+  LAW::flux(uu, ax, 1, vy.v, lp);
+  s.u[slot] = vu;
+  s.fx[slot] = vx;
+  s.fy[slot] = vy;
+  s.aux[slot] = ax;
+  if constexpr (LAW::kEntropy) s.sig[slot] = LAW::sigma(uu, ax, lp);
+}
+
+// Phase A: node slots and the halo.  Returns true for threads that own an active mesh node.
+template <int P, int TX, int TY, class LAW, typename T, class S>
+__device__ __forceinline__ bool load_tile(S& s, const StageLaunch<T>& A, int tile_x, int tile_y, int& le, int& a,
+                                          int& b, long long& g) {
+  using G = TileGeom<P, TX, TY>;
+  constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
+  const Instance<T>& I = A.inst;
+  const int t = threadIdx.x;
+  const int ex0 = tile_x * TX, ey0 = tile_y * TY;
+  if (t < NN) s.D[t] = A.tab.D[t];
+  if (t < n) s.w[t] = A.tab.w[t];
+  bool act = false;
+  le = 0; a = 0; b = 0; g = 0;
+  if (t < G::NT) {
+    le = t / NN;
+    const int node = t - le * NN;
+    a = node / n;
+    b = node - a * n;
+    const int ex = ex0 + le % TX, ey = ey0 + le / TX;
+    T uu[NC];
+    if (ex < I.nx && ey < I.ny) {
+      act = true;
+      g = ((long long)ey * I.nx + ex) * NN + node;
+#pragma unroll
+      for (int f = 0; f < NC; ++f) uu[f] = I.uin[f * I.N + g];
+    } else if (ey < I.ny) {
+      neighbor_trace<P, NC>(I, 1, I.nx - 1, ey, a, uu);  // east of the mesh: ghost of the last element
+    } else if (ex < I.nx) {
+      neighbor_trace<P, NC>(I, 3, ex, I.ny - 1, b, uu);  // north of the mesh
+    } else {
+#pragma unroll
+      for (int f = 0; f < NC; ++f) uu[f] = I.uin[f * I.N + ((long long)ey0 * I.nx + ex0) * NN];
+    }
+    fill_slot<LAW>(s, t, uu, A.lp);
+  }
+  for (int h = t; h < G::NH; h += G::THREADS) {
+    T uu[NC];
+    int side, pos;
+    if (h < G::NY) { side = 0; pos = h; }
+    else if (h < 2 * G::NY) { side = 1; pos = h - G::NY; }
+    else if (h < 2 * G::NY + G::NX) { side = 2; pos = h - 2 * G::NY; }
+    else { side = 3; pos = h - 2 * G::NY - G::NX; }
+    int ex, ey, along;
+    if (side < 2) { ex = (side == 0) ? ex0 : ex0 + TX - 1; ey = ey0 + pos / n; along = pos % n; }
+    else { ey = (side == 2) ? ey0 : ey0 + TY - 1; ex = ex0 + pos / n; along = pos % n; }
+    if (ex < I.nx && ey < I.ny) {
+      neighbor_trace<P, NC>(I, side, ex, ey, along, uu);
+    } else {
+#pragma unroll
+      for (int f = 0; f < NC; ++f) uu[f] = I.uin[f * I.N + ((long long)ey0 * I.nx + ex0) * NN];
+    }
+    fill_slot<LAW>(s, G::NT + h, uu, A.lp);
+  }
+  return act;
 }
 
 // Euler: largest t in [0, tcap] such that every candidate u^L + t w_c (w_c = gamma_d dt/m (+-r-bar))
@@ -107,15 +183,25 @@ __device__ __forceinline__ void face_eval(int k, const T* uL, const typename LAW
 // actual evaluation, with a bisection step whenever the bracket did not halve.  Bounded by
 // kRootMaxIt iterations (then the feasible end is returned and the cap is counted).
 template <class LAW, typename T>
-__device__ T entropy_limit(const T* uL, T K, const T (*cand)[4], T tcap, const LawParams& lp,
-                           int& iters, int& caps) {
+__device__ __forceinline__ void candidate(int c, const T* xp, const T* xm, const T* yp, const T* ym, T sc, T* w) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const T v = (c == 0) ? xp[q] : (c == 1) ? -xm[q] : (c == 2) ? yp[q] : -ym[q];
+    w[q] = sc * v;
+  }
+}
+
+template <class LAW, typename T>
+__device__ T entropy_limit(const T* uL, T K, const T* xp, const T* xm, const T* yp, const T* ym, T sc, T tcap,
+                           const LawParamsT<T>& lp, int& iters, int& caps) {
   const T psi0 = LAW::psi(uL, K, lp);
   const T target = tmin(psi0, T(0));
   T t = tcap;
 #pragma unroll 1
   for (int c = 0; c < 4; ++c) {
     if (!(t > T(0))) break;
-    const T* w = cand[c];
+    T w[4];
+    candidate<LAW>(c, xp, xm, yp, ym, sc, w);
     T ut[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) ut[f] = uL[f] + t * w[f];
@@ -136,8 +222,7 @@ __device__ T entropy_limit(const T* uL, T K, const T (*cand)[4], T tcap, const L
       if (uR[0] > T(0)) {
         const T fR = LAW::psi(uR, K, lp) - target;
         if (fR >= T(0)) { tL = tR; fL = fR; break; }
-        // chord root (feasible side)
-        T tc = tL + fL * (tR - tL) / (fL - fR);
+        const T tc = tL + fL * (tR - tL) / (fL - fR);  // chord root: feasible side
         if (tc > tL && tc < tR) {
           T uc[4];
 #pragma unroll
@@ -145,8 +230,7 @@ __device__ T entropy_limit(const T* uL, T K, const T (*cand)[4], T tcap, const L
           const T fc = (uc[0] > T(0)) ? LAW::psi(uc, K, lp) - target : T(-1);
           if (uc[0] > T(0) && fc >= T(0)) { tL = tc; fL = fc; } else { tR = tc; }
         }
-        // tangent root from tR (infeasible side)
-        const T dR = LAW::psi_grad_dot(uR, K, w, lp);
+        const T dR = LAW::psi_grad_dot(uR, K, w, lp);  // tangent root from the old tR: infeasible side
         if (dR < T(0)) {
           const T tn = tR - fR / dR;
           if (tn > tL && tn < tR) {
@@ -158,7 +242,7 @@ __device__ T entropy_limit(const T* uL, T K, const T (*cand)[4], T tcap, const L
           }
         }
       }
-      if (tR - tL > T(0.5) * width) {  // ensure at least halving
+      if (tR - tL > T(0.5) * width) {  // guarantee at least a halving
         const T tm = T(0.5) * (tL + tR);
         T um[4];
 #pragma unroll
@@ -175,372 +259,350 @@ __device__ T entropy_limit(const T* uL, T K, const T (*cand)[4], T tcap, const L
 }
 
 template <typename T>
-__device__ __forceinline__ void block_max_atomic(T v, unsigned long long* dst) {
-  // v >= 0; reduce in the warp then one atomic per warp on the double bit pattern
-  double d = (double)v;
+__device__ __forceinline__ void warp_max_atomic(T v, unsigned long long* dst) {
+  double d = (double)v;  // v >= 0
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
   if ((threadIdx.x & 31) == 0 && d > 0.0) atomicMax(dst, (unsigned long long)__double_as_longlong(d));
 }
 
-template <int P, class LAW, typename T>
-__global__ void __launch_bounds__(stage_threads(P))
-k_stage(const StageLaunch<T> A) {
-  constexpr int n = P + 1, NN = n * n, NC = LAW::NC, NF = n * (n + 1), EPB = epb_for(P);
-  using Aux = typename LAW::Aux;
-  using ES = ElemSmem<P, LAW, T>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  ES* S = reinterpret_cast<ES*>(smem_raw);
-  T* sD = reinterpret_cast<T*>(S + EPB);
-  T* sw = sD + NN;
-
-  const Instance<T>& I = A.inst;
-  const LawParams& lp = A.lp;
-  const int tid = threadIdx.x;
-  const int le = tid / NN, node = tid - le * NN;
-  const int a = node / n, b = node - a * n;
-  const long long Ne = (long long)I.nx * I.ny;
-  const long long e = (long long)blockIdx.x * EPB + le;
-  const bool act = (le < EPB) && (e < Ne);
-  const int ex = act ? (int)(e % I.nx) : 0, ey = act ? (int)(e / I.nx) : 0;
-  ES& s = S[le < EPB ? le : 0];
-  if (tid < NN) sD[tid] = A.tab.D[tid];
-  if (tid < n) sw[tid] = A.tab.w[tid];
-
-  const double dtd = *I.dt;
-  const T dt = T(dtd);
-  const bool move = (dtd > 0.0) && (dtd < DBL_MAX);
-  const long long N = I.N;
-  const long long g = e * NN + node;
-  const T h = T(I.h);
-
-  // ---------------- A: node state, aux, fluxes, sigma; face-neighbour traces
-  T u[NC], fx[NC], fy[NC], hx[NC], hy[NC];
-  Aux ax, ahx, ahy;
-  T sig = T(0), Kh = T(FLT_MAX);
-  if (act) {
+// Face along +e_k between the left/lower slot L (read from shared memory) and a right/upper state
+// given in registers; writes the face flux and the bar state of field 0 at index fi.
+template <class LAW, typename T, class S>
+__device__ __forceinline__ void face_eval_r(S& s, int k, int L, const Vec<T, LAW::NC>& uR, const Vec<T, LAW::NC>& FR,
+                                            const typename LAW::Aux& aR, int fi, const LawParamsT<T>& lp) {
+  using V = Vec<T, LAW::NC>;
+  constexpr int NC = LAW::NC;
+  const V uL = s.u[L];
+  const V FL = k ? s.fy[L] : s.fx[L];
+  const typename LAW::Aux aL = s.aux[L];
+  const T lam = LAW::lam(k, uL.v, aL, uR.v, aR, lp);
+  V fb;
 #pragma unroll
-    for (int f = 0; f < NC; ++f) u[f] = I.uin[f * N + g];
-    if (b == 0) neighbor_state<P, NC>(I, 0, e, ex, ey, a, u, hx);
-    else if (b == P) neighbor_state<P, NC>(I, 1, e, ex, ey, a, u, hx);
-    if (a == 0) neighbor_state<P, NC>(I, 2, e, ex, ey, b, u, hy);
-    else if (a == P) neighbor_state<P, NC>(I, 3, e, ex, ey, b, u, hy);
-    LAW::aux(u, ax, lp);
-    LAW::flux(u, ax, 0, fx, lp);
-    LAW::flux(u, ax, 1, fy, lp);
-#pragma unroll
-    for (int f = 0; f < NC; ++f) { s.u[f][node] = u[f]; s.fx[f][node] = fx[f]; s.fy[f][node] = fy[f]; }
-    s.aux[node] = ax;
-    if constexpr (LAW::kEntropy) { sig = LAW::sigma(u, ax, lp); s.sig[node] = sig; }
+  for (int q = 0; q < NC; ++q) fb.v[q] = T(0.5) * (FL.v[q] + FR.v[q]) - T(0.5) * lam * (uR.v[q] - uL.v[q]);
+  const T bar = (lam > T(0)) ? T(0.5) * (uL.v[0] + uR.v[0]) - fdiv(FR.v[0] - FL.v[0], T(2) * lam)
+                             : T(0.5) * (uL.v[0] + uR.v[0]);
+  if (k == 0) { s.fbx[fi] = fb; s.bbx[fi] = bar; }
+  else { s.fby[fi] = fb; s.bby[fi] = bar; }
+}
+
+// One face of the tile's node grid: x faces f < NFX ([row][c], c = 0..NX), then y faces ([r][col]).
+template <int P, int TX, int TY, class LAW, typename T, class S>
+__device__ __forceinline__ void face_update(S& s, int f, const LawParamsT<T>& lp) {
+  using G = TileGeom<P, TX, TY>;
+  using V = Vec<T, LAW::NC>;
+  constexpr int NC = LAW::NC;
+  int L, R, k, fi;
+  if (f < G::NFX) {
+    const int row = f / (G::NX + 1), c = f - row * (G::NX + 1);
+    L = (c == 0) ? G::hW + row : G::slot(row, c - 1);
+    R = (c == G::NX) ? G::hE + row : G::slot(row, c);
+    k = 0;
+    fi = f;
+  } else {
+    fi = f - G::NFX;
+    const int r = fi / G::NX, col = fi - r * G::NX;  // consecutive threads: consecutive columns
+    L = (r == 0) ? G::hS + col : G::slot(r - 1, col);
+    R = (r == G::NY) ? G::hN + col : G::slot(r, col);
+    k = 1;
   }
+  const V* Fs = k ? s.fy : s.fx;
+  const V uL = s.u[L], uR = s.u[R];
+  const V FL = Fs[L], FR = Fs[R];
+  const typename LAW::Aux aL = s.aux[L], aR = s.aux[R];
+  const T lam = LAW::lam(k, uL.v, aL, uR.v, aR, lp);
+  V fb;
+#pragma unroll
+  for (int q = 0; q < NC; ++q) fb.v[q] = T(0.5) * (FL.v[q] + FR.v[q]) - T(0.5) * lam * (uR.v[q] - uL.v[q]);
+  const T bar = (lam > T(0)) ? T(0.5) * (uL.v[0] + uR.v[0]) - fdiv(FR.v[0] - FL.v[0], T(2) * lam)
+                             : T(0.5) * (uL.v[0] + uR.v[0]);
+  V* fbs = k ? s.fby : s.fbx;
+  T* bbs = k ? s.bby : s.bbx;
+  fbs[fi] = fb;
+  bbs[fi] = bar;
+}
+
+template <int P, int TX, int TY, class LAW, typename T>
+__global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
+k_stage(const StageLaunch<T> A) {
+  using G = TileGeom<P, TX, TY>;
+  using S = TileSmem<P, TX, TY, LAW, T>;
+  using V = Vec<T, LAW::NC>;
+  constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S& s = *reinterpret_cast<S*>(smem_raw);
+  const Instance<T>& I = A.inst;
+  const LawParamsT<T>& lp = A.lp;
+  const int t = threadIdx.x;
+  const int tiles_x = (I.nx + TX - 1) / TX;
+  const int tile_y = blockIdx.x / tiles_x, tile_x = blockIdx.x - tile_y * tiles_x;
+
+  // ---------------- A
+  int le, a, b;
+  long long g;
+  const bool act = load_tile<P, TX, TY, LAW>(s, A, tile_x, tile_y, le, a, b, g);
   __syncthreads();
 
-  // ---------------- B: subcell and element faces
-  if (act) {
-    T fb[NC], bar, tmpu[NC], tmpF[NC], hF[NC];
-    // x face q = b (left of the node)
-    if (b == 0) {
-      LAW::aux(hx, ahx, lp);
-      LAW::flux(hx, ahx, 0, hF, lp);
-      face_eval<LAW>(0, hx, ahx, hF, u, ax, fx, lp, fb, bar);
-      if constexpr (LAW::kEntropy) Kh = tmin(Kh, LAW::sigma(hx, ahx, lp));
-    } else {
-#pragma unroll
-      for (int f = 0; f < NC; ++f) { tmpu[f] = s.u[f][node - 1]; tmpF[f] = s.fx[f][node - 1]; }
-      face_eval<LAW>(0, tmpu, s.aux[node - 1], tmpF, u, ax, fx, lp, fb, bar);
-    }
-#pragma unroll
-    for (int f = 0; f < NC; ++f) s.fbx[f][a * (n + 1) + b] = fb[f];
-    s.bbx[a * (n + 1) + b] = bar;
-    if (b == P) {  // right element face
-      LAW::aux(hx, ahx, lp);
-      LAW::flux(hx, ahx, 0, hF, lp);
-      face_eval<LAW>(0, u, ax, fx, hx, ahx, hF, lp, fb, bar);
-#pragma unroll
-      for (int f = 0; f < NC; ++f) s.fbx[f][a * (n + 1) + n] = fb[f];
-      s.bbx[a * (n + 1) + n] = bar;
-      if constexpr (LAW::kEntropy) Kh = tmin(Kh, LAW::sigma(hx, ahx, lp));
-    }
-    // y face q = a (below the node)
-    if (a == 0) {
-      LAW::aux(hy, ahy, lp);
-      LAW::flux(hy, ahy, 1, hF, lp);
-      face_eval<LAW>(1, hy, ahy, hF, u, ax, fy, lp, fb, bar);
-      if constexpr (LAW::kEntropy) Kh = tmin(Kh, LAW::sigma(hy, ahy, lp));
-    } else {
-#pragma unroll
-      for (int f = 0; f < NC; ++f) { tmpu[f] = s.u[f][node - n]; tmpF[f] = s.fy[f][node - n]; }
-      face_eval<LAW>(1, tmpu, s.aux[node - n], tmpF, u, ax, fy, lp, fb, bar);
-    }
-#pragma unroll
-    for (int f = 0; f < NC; ++f) s.fby[f][b * (n + 1) + a] = fb[f];
-    s.bby[b * (n + 1) + a] = bar;
-    if (a == P) {
-      LAW::aux(hy, ahy, lp);
-      LAW::flux(hy, ahy, 1, hF, lp);
-      face_eval<LAW>(1, u, ax, fy, hy, ahy, hF, lp, fb, bar);
-#pragma unroll
-      for (int f = 0; f < NC; ++f) s.fby[f][b * (n + 1) + n] = fb[f];
-      s.bby[b * (n + 1) + n] = bar;
-      if constexpr (LAW::kEntropy) Kh = tmin(Kh, LAW::sigma(hy, ahy, lp));
+  // ---------------- B: every face once.  Each node slot's thread evaluates the x face on its left
+  // and the y face below it (its own side is still in registers); the NY + NX faces on the east
+  // and north edges of the tile follow in one extra pass.
+  if (t < G::NT) {
+    const int row = (le / TX) * n + a, col = (le % TX) * n + b;
+    const V uR = s.u[t];
+    const typename LAW::Aux aR = s.aux[t];
+    face_eval_r<LAW>(s, 0, (col == 0) ? G::hW + row : t - ((b == 0) ? NN - P : 1), uR, s.fx[t], aR,
+                     row * (G::NX + 1) + col, lp);
+    face_eval_r<LAW>(s, 1, (row == 0) ? G::hS + col : t - ((a == 0) ? TX * NN - P * n : n), uR, s.fy[t], aR,
+                     row * G::NX + col, lp);
+  }
+  for (int e2 = t; e2 < G::NY + G::NX; e2 += G::THREADS) {
+    if (e2 < G::NY) {  // east edge: slot (row, NX-1) | halo E
+      const int row = e2;
+      const int L = G::slot(row, G::NX - 1), R = G::hE + row;
+      face_eval_r<LAW>(s, 0, L, s.u[R], s.fx[R], s.aux[R], row * (G::NX + 1) + G::NX, lp);
+    } else {  // north edge: slot (NY-1, col) | halo N
+      const int col = e2 - G::NY;
+      const int L = G::slot(G::NY - 1, col), R = G::hN + col;
+      face_eval_r<LAW>(s, 1, L, s.u[R], s.fy[R], s.aux[R], G::NY * G::NX + col, lp);
     }
   }
   __syncthreads();
 
   // ---------------- C: residuals, low-order state, bounds
-  T uL[NC], rx[NC], ry[NC], uH[NC];
-  T lo = T(0), hi = T(0), K = T(0);
-  const T wa = sw[a], wb = sw[b];
-  const T m = h * h * wa * wb;
-  const T dtm = dt / m;
+  const T dt = *I.dtT;
+  const bool move = (dt > T(0)) && (dt < T(FLT_MAX));
+  const T h = I.hT;
+  const int row = (le / TX) * n + a, col = (le % TX) * n + b;
+  const int me = le * NN + a * n + b;
+  const int ix = row * (G::NX + 1) + col, iy = row * G::NX + col;  // left x face, bottom y face
+  const long long N = I.N;
+  T uL[NC], rx[NC], ry[NC];
+  T lo = T(0), hi = T(0), K = T(0), m = T(1), dtm = T(0);
   if (act) {
+    const V vu = s.u[me], vfx = s.fx[me], vfy = s.fy[me];
+    const V fl = s.fbx[ix], fr = s.fbx[ix + 1], fd = s.fby[iy], fu = s.fby[iy + G::NX];
+    const T wa = s.w[a], wb = s.w[b];
     const T hwa = h * wa, hwb = h * wb;
+    m = h * h * wa * wb;
+    dtm = move ? dt / m : T(0);
+    T sx[NC], sy[NC];
 #pragma unroll
-    for (int f = 0; f < NC; ++f) {
-      T sx = T(0), sy = T(0);
+    for (int q = 0; q < NC; ++q) { sx[q] = T(0); sy[q] = T(0); }
+    const int lx = le * NN + a * n, ly = le * NN + b;
 #pragma unroll
-      for (int c = 0; c < n; ++c) {
-        sx += sD[b * n + c] * s.fx[f][a * n + c];
-        sy += sD[a * n + c] * s.fy[f][c * n + b];
-      }
-      const T* fbxr = &s.fbx[f][a * (n + 1)];
-      const T* fbyr = &s.fby[f][b * (n + 1)];
-      if (b == 0) sx += fx[f] - fbxr[0];
-      if (b == P) sx += fbxr[n] - fx[f];
-      if (a == 0) sy += fy[f] - fbyr[0];
-      if (a == P) sy += fbyr[n] - fy[f];
-      const T rHx = -hwa * sx, rHy = -hwb * sy;
-      const T rLx = -hwa * (fbxr[b + 1] - fbxr[b]);
-      const T rLy = -hwb * (fbyr[a + 1] - fbyr[a]);
-      uL[f] = u[f] + dtm * (rLx + rLy);
-      uH[f] = u[f] + dtm * (rHx + rHy);
-      rx[f] = rHx - rLx;
-      ry[f] = rHy - rLy;
+    for (int c = 0; c < n; ++c) {
+      const V Fxc = s.fx[lx + c];
+      const V Fyc = s.fy[ly + c * n];
+      const T dx = s.D[b * n + c], dy = s.D[a * n + c];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) { sx[q] += dx * Fxc.v[q]; sy[q] += dy * Fyc.v[q]; }
     }
-    const T* bbr = &s.bbx[a * (n + 1)];
-    const T* bcl = &s.bby[b * (n + 1)];
-    lo = tmin(tmin(u[0], tmin(bbr[b], bbr[b + 1])), tmin(bcl[a], bcl[a + 1]));
-    hi = tmax(tmax(u[0], tmax(bbr[b], bbr[b + 1])), tmax(bcl[a], bcl[a + 1]));
+    T out[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      if (b == 0) sx[q] += vfx.v[q] - fl.v[q];
+      if (b == P) sx[q] += fr.v[q] - vfx.v[q];
+      if (a == 0) sy[q] += vfy.v[q] - fd.v[q];
+      if (a == P) sy[q] += fu.v[q] - vfy.v[q];
+      const T rHx = -hwa * sx[q], rHy = -hwb * sy[q];
+      const T rLx = -hwa * (fr.v[q] - fl.v[q]);
+      const T rLy = -hwb * (fu.v[q] - fd.v[q]);
+      uL[q] = vu.v[q] + dtm * (rLx + rLy);
+      out[q] = (A.limiter == 0) ? vu.v[q] + dtm * (rHx + rHy) : uL[q];
+      rx[q] = rHx - rLx;
+      ry[q] = rHy - rLy;
+    }
+    if (A.limiter != 2) {  // high-order target or low-order update only: done
+#pragma unroll
+      for (int q = 0; q < NC; ++q)
+        I.uout[q * N + g] = (I.c0 == T(0)) ? out[q] : I.c0 * I.u0[q * N + g] + I.c1 * out[q];
+    }
+    lo = tmin(tmin(vu.v[0], tmin(s.bbx[ix], s.bbx[ix + 1])), tmin(s.bby[iy], s.bby[iy + G::NX]));
+    hi = tmax(tmax(vu.v[0], tmax(s.bbx[ix], s.bbx[ix + 1])), tmax(s.bby[iy], s.bby[iy + G::NX]));
     if constexpr (LAW::kEntropy) {
-      K = tmin(sig, Kh);
-      if (b > 0) K = tmin(K, s.sig[node - 1]);
-      if (b < P) K = tmin(K, s.sig[node + 1]);
-      if (a > 0) K = tmin(K, s.sig[node - n]);
-      if (a < P) K = tmin(K, s.sig[node + n]);
+      const int sl = (col == 0) ? G::hW + row : G::slot(row, col - 1);
+      const int sr = (col == G::NX - 1) ? G::hE + row : G::slot(row, col + 1);
+      const int sd = (row == 0) ? G::hS + col : G::slot(row - 1, col);
+      const int su = (row == G::NY - 1) ? G::hN + col : G::slot(row + 1, col);
+      K = tmin(tmin(s.sig[me], tmin(s.sig[sl], s.sig[sr])), tmin(s.sig[sd], s.sig[su]));
     }
   }
-  T fe[NC];
-  if (A.limiter == 2) {
-    __syncthreads();  // all reads of F_x, F_y done
-    if (act) {
-#pragma unroll
-      for (int f = 0; f < NC; ++f) { s.fx[f][node] = rx[f]; s.fy[f][node] = ry[f]; }
-    }
-    __syncthreads();
-    // ---------------- D: subcell fluxes and nodal alpha-tilde
-    T xp[NC], xm[NC], yp[NC], ym[NC];
-    T at = T(1);
-    int iters = 0, caps = 0;
-    if (act) {
-#pragma unroll
-      for (int f = 0; f < NC; ++f) {
-        T acc = T(0);
-#pragma unroll
-        for (int c = 0; c < P; ++c) if (c < b) acc += s.fx[f][a * n + c];
-        xm[f] = acc;
-        xp[f] = (b == P) ? T(0) : acc + s.fx[f][a * n + b];
-        acc = T(0);
-#pragma unroll
-        for (int c = 0; c < P; ++c) if (c < a) acc += s.fy[f][c * n + b];
-        ym[f] = acc;
-        yp[f] = (a == P) ? T(0) : acc + s.fy[f][a * n + b];
-      }
-      if (move) {
-        // Zalesak on field 0: contributions +r-bar_{m+}, -r-bar_{m-} per direction
-        const T c1 = xp[0], c2 = -xm[0], c3 = yp[0], c4 = -ym[0];
-        const T Pp = tmax(c1, T(0)) + tmax(c2, T(0)) + tmax(c3, T(0)) + tmax(c4, T(0));
-        const T Pm = tmin(c1, T(0)) + tmin(c2, T(0)) + tmin(c3, T(0)) + tmin(c4, T(0));
-        const T mdt = m / dt;
-        const T Qp = tmax(T(0), mdt * (hi - uL[0]));
-        const T Qm = tmin(T(0), mdt * (lo - uL[0]));
-        const T Rp = (Pp > T(0)) ? tmin(T(1), Qp / Pp) : T(1);
-        const T Rm = (Pm < T(0)) ? tmin(T(1), Qm / Pm) : T(1);
-        at = tmin(Rp, Rm);
-        if constexpr (LAW::kEntropy) {
-          const T sc = T(4) * dtm;  // gamma_d = 2d = 4
-          T cand[4][4];
-#pragma unroll
-          for (int f = 0; f < 4; ++f) {
-            cand[0][f] = sc * xp[f];
-            cand[1][f] = -sc * xm[f];
-            cand[2][f] = sc * yp[f];
-            cand[3][f] = -sc * ym[f];
-          }
-          at = entropy_limit<LAW>(uL, K, cand, at, lp, iters, caps);
-        }
-      }
-      s.alpha[node] = at;
-      if (I.dbg_lo) {
-        I.dbg_lo[g] = (double)lo;
-        I.dbg_hi[g] = (double)hi;
-        I.dbg_K[g] = (double)K;
-        I.dbg_alpha[g] = (double)at;
-      }
-    }
-    __syncthreads();
-    // ---------------- E: face coefficients and limited update
-    if (act) {
-      const T axp = (b < P) ? tmin(at, s.alpha[node + 1]) : T(0);
-      const T axm = (b > 0) ? tmin(at, s.alpha[node - 1]) : T(0);
-      const T ayp = (a < P) ? tmin(at, s.alpha[node + n]) : T(0);
-      const T aym = (a > 0) ? tmin(at, s.alpha[node - n]) : T(0);
-#pragma unroll
-      for (int f = 0; f < NC; ++f) fe[f] = uL[f] + dtm * (axp * xp[f] - axm * xm[f] + ayp * yp[f] - aym * ym[f]);
-    }
-    if (I.stats) {
-      T v = T(0), ev = T(0);
-      if (act && move) {
-        const T scale = tmax(fabs(lo), fabs(hi));
-        v = tmax(lo - fe[0], fe[0] - hi);
-        v = (v > T(0)) ? v / (scale > T(0) ? scale : T(1)) : T(0);
-        if constexpr (LAW::kEntropy) {
-          const T sg = LAW::sigma_of(fe, lp);
-          ev = tmax(T(0), T(1) - sg / K);
-          if (!(fe[0] > T(0))) ev = T(1);
-        }
-        if (caps) atomicAdd(&I.stats->rootfind_cap_hits, (unsigned long long)caps);
-        if (iters) atomicMax(&I.stats->rootfind_max_iters, (unsigned int)iters);
-      }
-      block_max_atomic(v, &I.stats->max_bound_violation);
-      block_max_atomic(ev, &I.stats->max_entropy_violation);
-    }
-  } else if (act) {
-#pragma unroll
-    for (int f = 0; f < NC; ++f) fe[f] = (A.limiter == 0) ? uH[f] : uL[f];
-  }
+  if (A.limiter != 2) return;  // uniform across the CTA
+  __syncthreads();  // all reads of F_x, F_y done
   if (act) {
-    if (!move) {
+    V vrx, vry;
 #pragma unroll
-      for (int f = 0; f < NC; ++f) fe[f] = u[f];
-    }
-#pragma unroll
-    for (int f = 0; f < NC; ++f) {
-      const T v = (I.c0 == T(0)) ? fe[f] : I.c0 * I.u0[f * N + g] + I.c1 * fe[f];
-      I.uout[f * N + g] = v;
-    }
+    for (int q = 0; q < NC; ++q) { vrx.v[q] = rx[q]; vry.v[q] = ry[q]; }
+    s.fx[me] = vrx;
+    s.fy[me] = vry;
   }
-}
-
-// CFL bound of Eq. cfl-low per node: m_i / (2 sum_{j != i} d-hat_ij); min-reduced into *out_bits
-// (positive doubles order like their bit patterns).
-template <int P, class LAW, typename T>
-__global__ void __launch_bounds__(256) k_dt(const StageLaunch<T> A, unsigned long long* out_bits) {
-  constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
-  using Aux = typename LAW::Aux;
-  const Instance<T>& I = A.inst;
-  const LawParams& lp = A.lp;
-  const long long Ne = (long long)I.nx * I.ny;
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double val = DBL_MAX;
-  if (g < Ne * NN) {
-    const long long e = g / NN;
-    const int node = (int)(g - e * NN), a = node / n, b = node - a * n;
-    const int ex = (int)(e % I.nx), ey = (int)(e / I.nx);
-    const long long N = I.N;
-    T u[NC], v[NC];
-    Aux ax, av;
-#pragma unroll
-    for (int f = 0; f < NC; ++f) u[f] = I.uin[f * N + g];
-    LAW::aux(u, ax, lp);
-    T lam[4];
-#pragma unroll
-    for (int side = 0; side < 4; ++side) {
-      const int k = side >> 1;
-      const bool lower = (side & 1) == 0;
-      const int idx = (k == 0) ? b : a;
-      const bool inside = lower ? (idx > 0) : (idx < P);
-      if (inside) {
-        const long long gn = g + (k == 0 ? (lower ? -1 : 1) : (lower ? -n : n));
-#pragma unroll
-        for (int f = 0; f < NC; ++f) v[f] = I.uin[f * N + gn];
-      } else {
-        neighbor_state<P, NC>(I, side, e, ex, ey, (k == 0) ? a : b, u, v);
-      }
-      LAW::aux(v, av, lp);
-      lam[side] = lower ? LAW::lam(k, v, av, u, ax, lp) : LAW::lam(k, u, ax, v, av, lp);
-    }
-    const double h = I.h;
-    const double wa = (double)A.tab.w[a], wb = (double)A.tab.w[b];
-    const double m = h * h * wa * wb;
-    const double sumd = 0.5 * h * wa * ((double)lam[0] + (double)lam[1]) + 0.5 * h * wb * ((double)lam[2] + (double)lam[3]);
-    if (sumd > 0.0) val = m / (2.0 * sumd);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) val = fmin(val, __shfl_xor_sync(0xffffffffu, val, o));
-  __shared__ double red[32];
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = val;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    val = (threadIdx.x < (blockDim.x + 31) / 32) ? red[threadIdx.x] : DBL_MAX;
+  // ---------------- D: subcell fluxes and nodal alpha-tilde
+  T xp[NC], xm[NC], yp[NC], ym[NC];
+  T at = T(1);
+  int iters = 0, caps = 0;
+  if (act) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) val = fmin(val, __shfl_xor_sync(0xffffffffu, val, o));
-    if (threadIdx.x == 0 && val < DBL_MAX) atomicMin(out_bits, (unsigned long long)__double_as_longlong(val));
+    for (int q = 0; q < NC; ++q) { xm[q] = T(0); ym[q] = T(0); }
+    const int lx = le * NN + a * n, ly = le * NN + b;
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+      if (c < b) {
+        const V r = s.fx[lx + c];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) xm[q] += r.v[q];
+      }
+      if (c < a) {
+        const V r = s.fy[ly + c * n];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) ym[q] += r.v[q];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      xp[q] = (b == P) ? T(0) : xm[q] + rx[q];
+      yp[q] = (a == P) ? T(0) : ym[q] + ry[q];
+    }
+    if (move) {
+      const T c1 = xp[0], c2 = -xm[0], c3 = yp[0], c4 = -ym[0];
+      const T Pp = tmax(c1, T(0)) + tmax(c2, T(0)) + tmax(c3, T(0)) + tmax(c4, T(0));
+      const T Pm = tmin(c1, T(0)) + tmin(c2, T(0)) + tmin(c3, T(0)) + tmin(c4, T(0));
+      const T mdt = m / dt;
+      const T Qp = tmax(T(0), mdt * (hi - uL[0]));
+      const T Qm = tmin(T(0), mdt * (lo - uL[0]));
+      const T Rp = (Pp > T(0)) ? tmin(T(1), fdiv(Qp, Pp)) : T(1);
+      const T Rm = (Pm < T(0)) ? tmin(T(1), fdiv(Qm, Pm)) : T(1);
+      at = tmin(Rp, Rm);
+      if constexpr (LAW::kEntropy) at = entropy_limit<LAW>(uL, K, xp, xm, yp, ym, T(4) * dtm, at, lp, iters, caps);
+    }
+    s.alpha[me] = at;
+    if (I.dbg_lo) {
+      I.dbg_lo[g] = (double)lo;
+      I.dbg_hi[g] = (double)hi;
+      I.dbg_K[g] = (double)K;
+      I.dbg_alpha[g] = (double)at;
+    }
+  }
+  T u0[NC];  // u^n for the RK combination; its latency overlaps the barrier
+  if (act && I.c0 != T(0)) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) u0[q] = I.u0[q * N + g];
+  }
+  __syncthreads();
+  // ---------------- E: face coefficients and limited update
+  T fe[NC];
+  if (act) {
+    const T axp = (b < P) ? tmin(at, s.alpha[me + 1]) : T(0);
+    const T axm = (b > 0) ? tmin(at, s.alpha[me - 1]) : T(0);
+    const T ayp = (a < P) ? tmin(at, s.alpha[me + n]) : T(0);
+    const T aym = (a > 0) ? tmin(at, s.alpha[me - n]) : T(0);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) fe[q] = uL[q] + dtm * (axp * xp[q] - axm * xm[q] + ayp * yp[q] - aym * ym[q]);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) I.uout[q * N + g] = (I.c0 == T(0)) ? fe[q] : I.c0 * u0[q] + I.c1 * fe[q];
+  }
+  if (I.stats) {
+    T v = T(0), ev = T(0);
+    if (act && move) {
+      const T scale = tmax(fabs(lo), fabs(hi));
+      v = tmax(lo - fe[0], fe[0] - hi);
+      v = (v > T(0)) ? v / (scale > T(0) ? scale : T(1)) : T(0);
+      if constexpr (LAW::kEntropy) {
+        const T sg = LAW::sigma_of(fe, lp);
+        ev = tmax(T(0), T(1) - sg / K);
+        if (!(fe[0] > T(0))) ev = T(1);
+      }
+      if (caps) atomicAdd(&I.stats->rootfind_cap_hits, (unsigned long long)caps);
+      if (iters) atomicMax(&I.stats->rootfind_max_iters, (unsigned int)iters);
+    }
+    warp_max_atomic(v, &I.stats->max_bound_violation);
+    warp_max_atomic(ev, &I.stats->max_entropy_violation);
   }
 }
 
-template <int P, class LAW, typename T>
-cudaError_t launch_stage_p(const StageLaunch<T>& a, cudaStream_t s) {
-  constexpr int EPB = epb_for(P);
-  constexpr size_t smem = stage_smem_bytes<P, LAW, T>();
+// CFL bound of Eq. cfl-low per node, m_i / (2 sum_{j != i} d-hat_ij) with d-hat = (h w / 2) lambda on
+// the node's four faces, min-reduced into *out_bits (positive doubles order like their bit patterns).
+// Same tile machinery as the stage kernel: node quantities once per node, lambda once per face.
+template <int P, int TX, int TY, class LAW, typename T>
+__global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
+k_dt(const StageLaunch<T> A, unsigned long long* out_bits) {
+  using G = TileGeom<P, TX, TY>;
+  using S = TileSmem<P, TX, TY, LAW, T>;
+  using V = Vec<T, LAW::NC>;
+  constexpr int n = P + 1, NN = n * n;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S& s = *reinterpret_cast<S*>(smem_raw);
+  const Instance<T>& I = A.inst;
+  const LawParamsT<T>& lp = A.lp;
+  const int t = threadIdx.x;
+  const int tiles_x = (I.nx + TX - 1) / TX;
+  const int tile_y = blockIdx.x / tiles_x, tile_x = blockIdx.x - tile_y * tiles_x;
+  int le, a, b;
+  long long g;
+  const bool act = load_tile<P, TX, TY, LAW>(s, A, tile_x, tile_y, le, a, b, g);
+  __syncthreads();
+  T* lamx = s.bbx;  // face lambdas reuse the bar-state arrays
+  T* lamy = s.bby;
+#pragma unroll 1
+  for (int f = t; f < G::NFX + G::NFY; f += G::THREADS) {
+    if (f < G::NFX) {
+      const int row = f / (G::NX + 1), c = f - row * (G::NX + 1);
+      const int L = (c == 0) ? G::hW + row : G::slot(row, c - 1);
+      const int R = (c == G::NX) ? G::hE + row : G::slot(row, c);
+      const V uL = s.u[L], uR = s.u[R];
+      lamx[f] = LAW::lam(0, uL.v, s.aux[L], uR.v, s.aux[R], lp);
+    } else {
+      const int fi = f - G::NFX;
+      const int r = fi / G::NX, col = fi - r * G::NX;
+      const int L = (r == 0) ? G::hS + col : G::slot(r - 1, col);
+      const int R = (r == G::NY) ? G::hN + col : G::slot(r, col);
+      const V uL = s.u[L], uR = s.u[R];
+      lamy[fi] = LAW::lam(1, uL.v, s.aux[L], uR.v, s.aux[R], lp);
+    }
+  }
+  __syncthreads();
+  // per-node bound in the stage precision; the min is exact in any precision, and one
+  // conversion per block hands it to the float64 accumulator
+  const T big = T(FLT_MAX);
+  T val = big;
+  if (act) {
+    const int row = (le / TX) * n + a, col = (le % TX) * n + b;
+    const int ix = row * (G::NX + 1) + col, iy = row * G::NX + col;
+    const T h = I.hT;
+    const T wa = s.w[a], wb = s.w[b];
+    const T sumd = T(0.5) * h * wa * (lamx[ix] + lamx[ix + 1]) + T(0.5) * h * wb * (lamy[iy] + lamy[iy + G::NX]);
+    if (sumd > T(0)) val = h * h * wa * wb / (T(2) * sumd);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) val = tmin(val, __shfl_xor_sync(0xffffffffu, val, o));
+  __shared__ T red[32];
+  if ((t & 31) == 0) red[t >> 5] = val;
+  __syncthreads();
+  if (t < 32) {
+    val = (t < G::THREADS / 32) ? red[t] : big;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) val = tmin(val, __shfl_xor_sync(0xffffffffu, val, o));
+    if (t == 0 && val < big) atomicMin(out_bits, (unsigned long long)__double_as_longlong((double)val));
+  }
+}
+
+template <int P, int TX, int TY, class LAW, typename T>
+cudaError_t launch_tile(const StageLaunch<T>& a, unsigned long long* dt_bits, cudaStream_t s) {
+  using G = TileGeom<P, TX, TY>;
+  constexpr size_t smem = sizeof(TileSmem<P, TX, TY, LAW, T>);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(k_stage<P, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = cudaFuncSetAttribute(k_stage<P, TX, TY, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(k_dt<P, TX, TY, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     attr_set = true;
   }
-  const long long Ne = (long long)a.inst.nx * a.inst.ny;
-  const long long blocks = (Ne + EPB - 1) / EPB;
-  if (blocks <= 0) return cudaSuccess;
-  k_stage<P, LAW, T><<<(unsigned)blocks, stage_threads(P), smem, s>>>(a);
+  const long long tiles = (long long)((a.inst.nx + TX - 1) / TX) * ((a.inst.ny + TY - 1) / TY);
+  if (tiles <= 0) return cudaSuccess;
+  if (dt_bits) k_dt<P, TX, TY, LAW, T><<<(unsigned)tiles, G::THREADS, smem, s>>>(a, dt_bits);
+  else k_stage<P, TX, TY, LAW, T><<<(unsigned)tiles, G::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
-
-template <int P, class LAW, typename T>
-cudaError_t launch_dt_p(const StageLaunch<T>& a, unsigned long long* bits, cudaStream_t s) {
-  constexpr int NN = (P + 1) * (P + 1);
-  const long long total = (long long)a.inst.nx * a.inst.ny * NN;
-  const long long blocks = (total + 255) / 256;
-  if (blocks <= 0) return cudaSuccess;
-  k_dt<P, LAW, T><<<(unsigned)blocks, 256, 0, s>>>(a, bits);
-  return cudaGetLastError();
-}
-
-#define SIDP_DISPATCH_P(FN, ...)                    \
-  switch (p) {                                      \
-    case 1: return FN<1, LAWT, T>(__VA_ARGS__);     \
-    case 2: return FN<2, LAWT, T>(__VA_ARGS__);     \
-    case 3: return FN<3, LAWT, T>(__VA_ARGS__);     \
-    case 4: return FN<4, LAWT, T>(__VA_ARGS__);     \
-    case 5: return FN<5, LAWT, T>(__VA_ARGS__);     \
-    case 6: return FN<6, LAWT, T>(__VA_ARGS__);     \
-    case 7: return FN<7, LAWT, T>(__VA_ARGS__);     \
-    default: return cudaErrorInvalidValue;          \
-  }
-
-// Instantiate the launchers of one law and precision in the including translation unit.
-#define SIDP_INSTANTIATE(LAWID, LAWTPL, TT)                                                          \
-  template <>                                                                                        \
-  cudaError_t launch_stage_law<LAWID, TT>(int p, const StageLaunch<TT>& a, cudaStream_t s) {        \
-    using T = TT;                                                                                    \
-    using LAWT = LAWTPL<TT>;                                                                         \
-    SIDP_DISPATCH_P(launch_stage_p, a, s)                                                            \
-  }                                                                                                  \
-  template <>                                                                                        \
-  cudaError_t launch_dt_law<LAWID, TT>(int p, const StageLaunch<TT>& a, unsigned long long* bits,   \
-                                       cudaStream_t s) {                                             \
-    using T = TT;                                                                                    \
-    using LAWT = LAWTPL<TT>;                                                                         \
-    SIDP_DISPATCH_P(launch_dt_p, a, bits, s)                                                         \
-  }
 
 }  // namespace sidp

@@ -19,23 +19,35 @@ namespace sidp {
 template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 
-// pow for positive x, precision-specific
+// Precision-specific arithmetic.  float64: IEEE operations (parity with the float64 oracle).
+// float32 (the mixed path): hardware approximations (MUFU-based reciprocal, reciprocal square
+// root and exp2/log2; a few ulp), whose effect is covered by the bound checks of the update.
 __device__ __forceinline__ double ppow(double x, double y) { return pow(x, y); }
 __device__ __forceinline__ float ppow(float x, float y) { return __powf(x, y); }
 __device__ __forceinline__ double psqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float psqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ float psqrt(float x) { return x * rsqrtf(x); }
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
+// x^(2 gamma/(gamma-1)): seven multiplications' worth when the exponent is 7 (gamma = 1.4) in float32
+__device__ __forceinline__ double pstar_pow(double x, const LawParamsT<double>& lp) { return pow(x, lp.inv_e); }
+__device__ __forceinline__ float pstar_pow(float x, const LawParamsT<float>& lp) {
+  if (lp.pow7) { const float x2 = x * x, x4 = x2 * x2; return x4 * x2 * x; }
+  return __powf(x, lp.inv_e);
+}
 
 template <typename T>
 struct LawAdvection {
   static constexpr int NC = 1;
   static constexpr bool kEntropy = false;
   struct Aux {};
-  __device__ static void aux(const T*, Aux&, const LawParams&) {}
-  __device__ static void flux(const T* u, const Aux&, int k, T* f, const LawParams& lp) {
-    f[0] = T(lp.beta[k]) * u[0];
+  __device__ static void aux(const T*, Aux&, const LawParamsT<T>&) {}
+  __device__ static void flux(const T* u, const Aux&, int k, T* f, const LawParamsT<T>& lp) {
+    f[0] = lp.beta[k] * u[0];
   }
-  __device__ static T lam(int k, const T*, const Aux&, const T*, const Aux&, const LawParams& lp) {
-    return fabs(T(lp.beta[k]));
+  __device__ static T lam(int k, const T*, const Aux&, const T*, const Aux&, const LawParamsT<T>& lp) {
+    return fabs(lp.beta[k]);
   }
 };
 
@@ -44,12 +56,12 @@ struct LawBurgers {
   static constexpr int NC = 1;
   static constexpr bool kEntropy = false;
   struct Aux {};
-  __device__ static void aux(const T*, Aux&, const LawParams&) {}
-  __device__ static void flux(const T* u, const Aux&, int, T* f, const LawParams&) {
+  __device__ static void aux(const T*, Aux&, const LawParamsT<T>&) {}
+  __device__ static void flux(const T* u, const Aux&, int, T* f, const LawParamsT<T>&) {
     f[0] = T(0.5) * u[0] * u[0];
   }
   // F.e_k = u^2/2 is convex; the extreme characteristic speeds are the end states'.
-  __device__ static T lam(int, const T* uL, const Aux&, const T* uR, const Aux&, const LawParams&) {
+  __device__ static T lam(int, const T* uL, const Aux&, const T* uR, const Aux&, const LawParamsT<T>&) {
     return tmax(fabs(uL[0]), fabs(uR[0]));
   }
 };
@@ -58,23 +70,25 @@ template <typename T>
 struct LawEuler {
   static constexpr int NC = 4;
   static constexpr bool kEntropy = true;
-  struct Aux {
+  struct alignas(8 * sizeof(T) >= 32 ? 32 : 8 * sizeof(T)) Aux {
     T v[2];   // velocity
     T p;      // pressure
     T a;      // sound speed
-    T pm;     // p^{-(gamma-1)/(2 gamma)}
+    T ip;     // 1 / p
+    T apm;    // a p^{-(gamma-1)/(2 gamma)}
+    T pad[2]; // 8 values: two 16-byte (float) loads
   };
-  __device__ static void aux(const T* u, Aux& x, const LawParams& lp) {
-    const T g = T(lp.gamma);
-    const T rinv = T(1) / u[0];
+  __device__ static void aux(const T* u, Aux& x, const LawParamsT<T>& lp) {
+    const T rinv = frcp(u[0]);
     x.v[0] = u[1] * rinv;
     x.v[1] = u[2] * rinv;
-    x.p = (g - T(1)) * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * rinv);  // Eq. euler-eos
-    x.a = psqrt(g * x.p * rinv);
-    x.pm = ppow(x.p, -(g - T(1)) / (T(2) * g));
+    x.p = lp.gm1 * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * rinv);  // Eq. euler-eos
+    x.a = psqrt(lp.gamma * x.p * rinv);
+    x.ip = frcp(x.p);
+    x.apm = x.a * ppow(x.p, lp.neg_e);
   }
   // Eq. euler-flux along e_k: (m_k, m_k v_x + p d_{0k}, m_k v_y + p d_{1k}, (rho E + p) v_k)
-  __device__ static void flux(const T* u, const Aux& x, int k, T* f, const LawParams&) {
+  __device__ static void flux(const T* u, const Aux& x, int k, T* f, const LawParamsT<T>&) {
     const T mk = u[1 + k];
     f[0] = mk;
     f[1] = mk * x.v[0] + (k == 0 ? x.p : T(0));
@@ -83,37 +97,29 @@ struct LawEuler {
   }
   // Guermond-Popov two-rarefaction bound (guaranteed for 1 < gamma <= 5/3): the two-rarefaction
   // pressure bounds the star pressure from above, and the extreme speeds grow with it.
-  __device__ static T lam(int k, const T*, const Aux& L, const T*, const Aux& R, const LawParams& lp) {
-    const T g = T(lp.gamma);
-    const T e = (g - T(1)) / (T(2) * g);
-    const T num = tmax(L.a + R.a - T(0.5) * (g - T(1)) * (R.v[k] - L.v[k]), T(0));
-    const T den = L.a * L.pm + R.a * R.pm;
-    const T ps = ppow(num / den, T(1) / e);
-    const T c = (g + T(1)) / (T(2) * g);
-    const T lL = L.v[k] - L.a * psqrt(T(1) + c * tmax(ps - L.p, T(0)) / L.p);
-    const T lR = R.v[k] + R.a * psqrt(T(1) + c * tmax(ps - R.p, T(0)) / R.p);
+  __device__ static T lam(int k, const T*, const Aux& L, const T*, const Aux& R, const LawParamsT<T>& lp) {
+    const T num = tmax(L.a + R.a - lp.half_gm1 * (R.v[k] - L.v[k]), T(0));
+    const T ps = pstar_pow(fdiv(num, L.apm + R.apm), lp);
+    const T lL = L.v[k] - L.a * psqrt(T(1) + lp.c_gp * tmax(ps - L.p, T(0)) * L.ip);
+    const T lR = R.v[k] + R.a * psqrt(T(1) + lp.c_gp * tmax(ps - R.p, T(0)) * R.ip);
     return tmax(fabs(lL), fabs(lR));
   }
   // sigma = rho e rho^-gamma; s = log(sigma)/(gamma-1) (Sec. 4.3)
-  __device__ static T sigma(const T* u, const Aux& x, const LawParams& lp) {
-    const T g = T(lp.gamma);
-    return x.p / (g - T(1)) * ppow(u[0], -g);
+  __device__ static T sigma(const T* u, const Aux& x, const LawParamsT<T>& lp) {
+    return x.p * lp.inv_gm1 * ppow(u[0], -lp.gamma);
   }
-  __device__ static T sigma_of(const T* u, const LawParams& lp) {
-    const T g = T(lp.gamma);
-    const T rhoe = u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) / u[0];
-    return rhoe * ppow(u[0], -g);
+  __device__ static T sigma_of(const T* u, const LawParamsT<T>& lp) {
+    const T rhoe = u[3] - T(0.5) * fdiv(u[1] * u[1] + u[2] * u[2], u[0]);
+    return rhoe * ppow(u[0], -lp.gamma);
   }
   // psi_K(u) = rho e - K rho^gamma and its gradient in conserved variables
-  __device__ static T psi(const T* u, T K, const LawParams& lp) {
-    const T g = T(lp.gamma);
-    return u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) / u[0] - K * ppow(u[0], g);
+  __device__ static T psi(const T* u, T K, const LawParamsT<T>& lp) {
+    return u[3] - T(0.5) * fdiv(u[1] * u[1] + u[2] * u[2], u[0]) - K * ppow(u[0], lp.gamma);
   }
-  __device__ static T psi_grad_dot(const T* u, T K, const T* w, const LawParams& lp) {
-    const T g = T(lp.gamma);
-    const T rinv = T(1) / u[0];
+  __device__ static T psi_grad_dot(const T* u, T K, const T* w, const LawParamsT<T>& lp) {
+    const T rinv = frcp(u[0]);
     const T vx = u[1] * rinv, vy = u[2] * rinv;
-    const T drho = T(0.5) * (vx * vx + vy * vy) - g * K * ppow(u[0], g - T(1));
+    const T drho = T(0.5) * (vx * vx + vy * vy) - lp.gamma * K * ppow(u[0], lp.gm1);
     return drho * w[0] - vx * w[1] - vy * w[2] + w[3];
   }
 };

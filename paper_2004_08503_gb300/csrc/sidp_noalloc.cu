@@ -22,7 +22,7 @@
 #include <cmath>
 #include <mutex>
 
-#include "../../include/sidp.h"
+#include "sidp.h"
 #include "sidp_laws.cuh"
 #include "sidp_internal.h"
 
@@ -55,7 +55,7 @@ __device__ __forceinline__ void static_neighbor(const T* u, long long N, int nx,
 template <int P, class LAW, typename T>
 __global__ void __launch_bounds__(kStaticThreads)
 k_dt_static(const T* __restrict__ u, long long N, int nx, int ny, int4 bc4, double h, Tables<T> tab,
-            LawParams lp, double* partials) {
+            LawParamsT<T> lp, double* partials) {
   constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
   using Aux = typename LAW::Aux;
   const int bc[4] = {bc4.x, bc4.y, bc4.z, bc4.w};
@@ -70,7 +70,7 @@ k_dt_static(const T* __restrict__ u, long long N, int nx, int ny, int4 bc4, doub
 #pragma unroll
     for (int f = 0; f < NC; ++f) uu[f] = u[f * N + g];
     LAW::aux(uu, ax, lp);
-    double lam[4];
+    T lam[4];
 #pragma unroll
     for (int side = 0; side < 4; ++side) {
       const int k = side >> 1;
@@ -84,11 +84,12 @@ k_dt_static(const T* __restrict__ u, long long N, int nx, int ny, int4 bc4, doub
         static_neighbor<P, NC>(u, N, nx, ny, bc, side, e, ex, ey, (k == 0) ? a : b, uu, v);
       }
       LAW::aux(v, av, lp);
-      lam[side] = (double)(lower ? LAW::lam(k, v, av, uu, ax, lp) : LAW::lam(k, uu, ax, v, av, lp));
+      lam[side] = lower ? LAW::lam(k, v, av, uu, ax, lp) : LAW::lam(k, uu, ax, v, av, lp);
     }
-    const double wa = (double)tab.w[a], wb = (double)tab.w[b];
-    const double sumd = 0.5 * h * wa * (lam[0] + lam[1]) + 0.5 * h * wb * (lam[2] + lam[3]);
-    if (sumd > 0.0) val = h * h * wa * wb / (2.0 * sumd);
+    // per-node bound in the stage precision, like the context's time-step kernel
+    const T hT = T(h), wa = tab.w[a], wb = tab.w[b];
+    const T sumd = T(0.5) * hT * wa * (lam[0] + lam[1]) + T(0.5) * hT * wb * (lam[2] + lam[3]);
+    if (sumd > T(0)) val = (double)(hT * hT * wa * wb / (T(2) * sumd));
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) val = fmin(val, __shfl_xor_sync(0xffffffffu, val, o));
@@ -123,7 +124,7 @@ cudaError_t launch_static(const sidp_config* cfg, const void* d_state, long long
   double xi[kMaxN], w[kMaxN], D[kMaxN * kMaxN];
   gll_tables(P, xi, w, D);
   for (int i = 0; i <= P; ++i) tab.w[i] = T(w[i]);
-  LawParams lp{cfg->gamma, {cfg->adv_beta[0], cfg->adv_beta[1]}};
+  const LawParamsT<T> lp = make_law_params<T>(cfg->gamma, cfg->adv_beta);
   const long long blocks = (N + kStaticThreads - 1) / kStaticThreads;
   const int4 bc4 = make_int4(cfg->bc[0], cfg->bc[1], cfg->bc[2], cfg->bc[3]);
   k_dt_static<P, LAW, T><<<(unsigned)blocks, kStaticThreads, 0, s>>>(static_cast<const T*>(d_state), N, cfg->nx,

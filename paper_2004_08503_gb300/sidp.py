@@ -65,6 +65,7 @@ _SIGS = {
     "sidp_stage": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
     "sidp_step": (ctypes.c_int, [_P, ctypes.c_int]),
     "sidp_set_graph": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sidp_get_tile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "sidp_set_stats": (ctypes.c_int, [_P, ctypes.c_int]),
     "sidp_set_debug": (ctypes.c_int, [_P, ctypes.c_int]),
     "sidp_get_bounds": (ctypes.c_int, [_P, _D, _D, _D, _D]),
@@ -212,6 +213,12 @@ def sidp_stage(ctx, k, dt):
 
 def sidp_step(ctx, nsteps=1):
     _check(load().sidp_step(ctx, nsteps), ctx)
+
+
+def sidp_get_tile(ctx):
+    tx, ty = ctypes.c_int(), ctypes.c_int()
+    _check(load().sidp_get_tile(ctx, ctypes.byref(tx), ctypes.byref(ty)), ctx)
+    return tx.value, ty.value
 
 
 def sidp_set_graph(ctx, on):

@@ -37,7 +37,8 @@ def test_static_dt_matches_context_dt_twice(precision):
         sidp.sidp_compute_dt_static(sv.cfg, dptr, out.data_ptr(), None)
         torch.cuda.synchronize()
         got = float(out.item())
-        assert ref > 0 and abs(got - ref) <= 1e-13 * ref, (got, ref)
+        tol = 1e-13 if precision == "fp64" else 1e-6  # float32 rounding in the mixed path
+        assert ref > 0 and abs(got - ref) <= tol * ref, (got, ref)
         sv.close()
 
 
