@@ -64,8 +64,9 @@ struct TileSmem {
   V fby[G::NFY];
   typename LAW::Aux aux[G::NS];
   T sig[LAW::kEntropy ? G::NS : 1];
-  T bbx[G::NFX];
-  T bby[G::NFY];
+  // per face: bar state of field 0 and, for Euler, min(sigma_L, sigma_R)
+  Vec<T, LAW::kEntropy ? 2 : 1> bbx[G::NFX];
+  Vec<T, LAW::kEntropy ? 2 : 1> bby[G::NFY];
   T alpha[G::NT];
   T D[G::NN];
   T w[G::n];
@@ -101,26 +102,29 @@ __device__ __forceinline__ void neighbor_trace(const Instance<T>& I, int side, i
   }
 }
 
-// Node quantities of a slot: state, aux, fluxes and (Euler) sigma.
-template <class LAW, typename T, class S>
+// Node quantities of a slot: state, aux and -- unless LEAN (time-step kernel) -- fluxes and sigma.
+template <class LAW, bool LEAN, typename T, class S>
 __device__ __forceinline__ void fill_slot(S& s, int slot, const T* uu, const LawParamsT<T>& lp) {
   constexpr int NC = LAW::NC;
   typename LAW::Aux ax;
   LAW::aux(uu, ax, lp);
-  Vec<T, NC> vu, vx, vy;
+  Vec<T, NC> vu;
 #pragma unroll
   for (int f = 0; f < NC; ++f) vu.v[f] = uu[f];
-  LAW::flux(uu, ax, 0, vx.v, lp);
-  LAW::flux(uu, ax, 1, vy.v, lp);
   s.u[slot] = vu;
-  s.fx[slot] = vx;
-  s.fy[slot] = vy;
   s.aux[slot] = ax;
-  if constexpr (LAW::kEntropy) s.sig[slot] = LAW::sigma(uu, ax, lp);
+  if constexpr (!LEAN) {
+    Vec<T, NC> vx, vy;
+    LAW::flux(uu, ax, 0, vx.v, lp);
+    LAW::flux(uu, ax, 1, vy.v, lp);
+    s.fx[slot] = vx;
+    s.fy[slot] = vy;
+    if constexpr (LAW::kEntropy) s.sig[slot] = LAW::sigma(uu, ax, lp);
+  }
 }
 
 // Phase A: node slots and the halo.  Returns true for threads that own an active mesh node.
-template <int P, int TX, int TY, class LAW, typename T, class S>
+template <int P, int TX, int TY, class LAW, bool LEAN, typename T, class S>
 __device__ __forceinline__ bool load_tile(S& s, const StageLaunch<T>& A, int tile_x, int tile_y, int& le, int& a,
                                           int& b, long long& g) {
   using G = TileGeom<P, TX, TY>;
@@ -152,7 +156,7 @@ __device__ __forceinline__ bool load_tile(S& s, const StageLaunch<T>& A, int til
 #pragma unroll
       for (int f = 0; f < NC; ++f) uu[f] = I.uin[f * I.N + ((long long)ey0 * I.nx + ex0) * NN];
     }
-    fill_slot<LAW>(s, t, uu, A.lp);
+    fill_slot<LAW, LEAN>(s, t, uu, A.lp);
   }
   for (int h = t; h < G::NH; h += G::THREADS) {
     T uu[NC];
@@ -170,7 +174,7 @@ __device__ __forceinline__ bool load_tile(S& s, const StageLaunch<T>& A, int til
 #pragma unroll
       for (int f = 0; f < NC; ++f) uu[f] = I.uin[f * I.N + ((long long)ey0 * I.nx + ex0) * NN];
     }
-    fill_slot<LAW>(s, G::NT + h, uu, A.lp);
+    fill_slot<LAW, LEAN>(s, G::NT + h, uu, A.lp);
   }
   return act;
 }
@@ -266,11 +270,31 @@ __device__ __forceinline__ void warp_max_atomic(T v, unsigned long long* dst) {
   if ((threadIdx.x & 31) == 0 && d > 0.0) atomicMax(dst, (unsigned long long)__double_as_longlong(d));
 }
 
+// Slots of the four neighbours of node slot t = (le, a, b) at tile position (row, col):
+// within the element, across an element face inside the tile, or in the halo.
+template <int P, int TX, int TY>
+struct Nbr {
+  using G = TileGeom<P, TX, TY>;
+  static constexpr int n = P + 1, NN = n * n;
+  __device__ __forceinline__ static int left(int t, int b, int row, int col) {
+    return (col == 0) ? G::hW + row : t - ((b == 0) ? NN - P : 1);
+  }
+  __device__ __forceinline__ static int right(int t, int b, int row, int col) {
+    return (col == G::NX - 1) ? G::hE + row : t + ((b == P) ? NN - P : 1);
+  }
+  __device__ __forceinline__ static int down(int t, int a, int row, int col) {
+    return (row == 0) ? G::hS + col : t - ((a == 0) ? TX * NN - P * n : n);
+  }
+  __device__ __forceinline__ static int up(int t, int a, int row, int col) {
+    return (row == G::NY - 1) ? G::hN + col : t + ((a == P) ? TX * NN - P * n : n);
+  }
+};
+
 // Face along +e_k between the left/lower slot L (read from shared memory) and a right/upper state
 // given in registers; writes the face flux and the bar state of field 0 at index fi.
 template <class LAW, typename T, class S>
 __device__ __forceinline__ void face_eval_r(S& s, int k, int L, const Vec<T, LAW::NC>& uR, const Vec<T, LAW::NC>& FR,
-                                            const typename LAW::Aux& aR, int fi, const LawParamsT<T>& lp) {
+                                            const typename LAW::Aux& aR, T sR, int fi, const LawParamsT<T>& lp) {
   using V = Vec<T, LAW::NC>;
   constexpr int NC = LAW::NC;
   const V uL = s.u[L];
@@ -280,46 +304,12 @@ __device__ __forceinline__ void face_eval_r(S& s, int k, int L, const Vec<T, LAW
   V fb;
 #pragma unroll
   for (int q = 0; q < NC; ++q) fb.v[q] = T(0.5) * (FL.v[q] + FR.v[q]) - T(0.5) * lam * (uR.v[q] - uL.v[q]);
-  const T bar = (lam > T(0)) ? T(0.5) * (uL.v[0] + uR.v[0]) - fdiv(FR.v[0] - FL.v[0], T(2) * lam)
-                             : T(0.5) * (uL.v[0] + uR.v[0]);
-  if (k == 0) { s.fbx[fi] = fb; s.bbx[fi] = bar; }
-  else { s.fby[fi] = fb; s.bby[fi] = bar; }
-}
-
-// One face of the tile's node grid: x faces f < NFX ([row][c], c = 0..NX), then y faces ([r][col]).
-template <int P, int TX, int TY, class LAW, typename T, class S>
-__device__ __forceinline__ void face_update(S& s, int f, const LawParamsT<T>& lp) {
-  using G = TileGeom<P, TX, TY>;
-  using V = Vec<T, LAW::NC>;
-  constexpr int NC = LAW::NC;
-  int L, R, k, fi;
-  if (f < G::NFX) {
-    const int row = f / (G::NX + 1), c = f - row * (G::NX + 1);
-    L = (c == 0) ? G::hW + row : G::slot(row, c - 1);
-    R = (c == G::NX) ? G::hE + row : G::slot(row, c);
-    k = 0;
-    fi = f;
-  } else {
-    fi = f - G::NFX;
-    const int r = fi / G::NX, col = fi - r * G::NX;  // consecutive threads: consecutive columns
-    L = (r == 0) ? G::hS + col : G::slot(r - 1, col);
-    R = (r == G::NY) ? G::hN + col : G::slot(r, col);
-    k = 1;
-  }
-  const V* Fs = k ? s.fy : s.fx;
-  const V uL = s.u[L], uR = s.u[R];
-  const V FL = Fs[L], FR = Fs[R];
-  const typename LAW::Aux aL = s.aux[L], aR = s.aux[R];
-  const T lam = LAW::lam(k, uL.v, aL, uR.v, aR, lp);
-  V fb;
-#pragma unroll
-  for (int q = 0; q < NC; ++q) fb.v[q] = T(0.5) * (FL.v[q] + FR.v[q]) - T(0.5) * lam * (uR.v[q] - uL.v[q]);
-  const T bar = (lam > T(0)) ? T(0.5) * (uL.v[0] + uR.v[0]) - fdiv(FR.v[0] - FL.v[0], T(2) * lam)
-                             : T(0.5) * (uL.v[0] + uR.v[0]);
-  V* fbs = k ? s.fby : s.fbx;
-  T* bbs = k ? s.bby : s.bbx;
-  fbs[fi] = fb;
-  bbs[fi] = bar;
+  Vec<T, LAW::kEntropy ? 2 : 1> bb;
+  bb.v[0] = (lam > T(0)) ? T(0.5) * (uL.v[0] + uR.v[0]) - fdiv(FR.v[0] - FL.v[0], T(2) * lam)
+                         : T(0.5) * (uL.v[0] + uR.v[0]);
+  if constexpr (LAW::kEntropy) bb.v[1] = tmin(s.sig[L], sR);
+  if (k == 0) { s.fbx[fi] = fb; s.bbx[fi] = bb; }
+  else { s.fby[fi] = fb; s.bby[fi] = bb; }
 }
 
 template <int P, int TX, int TY, class LAW, typename T>
@@ -340,7 +330,7 @@ k_stage(const StageLaunch<T> A) {
   // ---------------- A
   int le, a, b;
   long long g;
-  const bool act = load_tile<P, TX, TY, LAW>(s, A, tile_x, tile_y, le, a, b, g);
+  const bool act = load_tile<P, TX, TY, LAW, false>(s, A, tile_x, tile_y, le, a, b, g);
   __syncthreads();
 
   // ---------------- B: every face once.  Each node slot's thread evaluates the x face on its left
@@ -350,20 +340,19 @@ k_stage(const StageLaunch<T> A) {
     const int row = (le / TX) * n + a, col = (le % TX) * n + b;
     const V uR = s.u[t];
     const typename LAW::Aux aR = s.aux[t];
-    face_eval_r<LAW>(s, 0, (col == 0) ? G::hW + row : t - ((b == 0) ? NN - P : 1), uR, s.fx[t], aR,
-                     row * (G::NX + 1) + col, lp);
-    face_eval_r<LAW>(s, 1, (row == 0) ? G::hS + col : t - ((a == 0) ? TX * NN - P * n : n), uR, s.fy[t], aR,
-                     row * G::NX + col, lp);
+    const T sR = LAW::kEntropy ? s.sig[t] : T(0);
+    face_eval_r<LAW>(s, 0, Nbr<P, TX, TY>::left(t, b, row, col), uR, s.fx[t], aR, sR, row * (G::NX + 1) + col, lp);
+    face_eval_r<LAW>(s, 1, Nbr<P, TX, TY>::down(t, a, row, col), uR, s.fy[t], aR, sR, row * G::NX + col, lp);
   }
   for (int e2 = t; e2 < G::NY + G::NX; e2 += G::THREADS) {
     if (e2 < G::NY) {  // east edge: slot (row, NX-1) | halo E
       const int row = e2;
       const int L = G::slot(row, G::NX - 1), R = G::hE + row;
-      face_eval_r<LAW>(s, 0, L, s.u[R], s.fx[R], s.aux[R], row * (G::NX + 1) + G::NX, lp);
+      face_eval_r<LAW>(s, 0, L, s.u[R], s.fx[R], s.aux[R], LAW::kEntropy ? s.sig[R] : T(0), row * (G::NX + 1) + G::NX, lp);
     } else {  // north edge: slot (NY-1, col) | halo N
       const int col = e2 - G::NY;
       const int L = G::slot(G::NY - 1, col), R = G::hN + col;
-      face_eval_r<LAW>(s, 1, L, s.u[R], s.fy[R], s.aux[R], G::NY * G::NX + col, lp);
+      face_eval_r<LAW>(s, 1, L, s.u[R], s.fy[R], s.aux[R], LAW::kEntropy ? s.sig[R] : T(0), G::NY * G::NX + col, lp);
     }
   }
   __syncthreads();
@@ -417,15 +406,11 @@ k_stage(const StageLaunch<T> A) {
       for (int q = 0; q < NC; ++q)
         I.uout[q * N + g] = (I.c0 == T(0)) ? out[q] : I.c0 * I.u0[q * N + g] + I.c1 * out[q];
     }
-    lo = tmin(tmin(vu.v[0], tmin(s.bbx[ix], s.bbx[ix + 1])), tmin(s.bby[iy], s.bby[iy + G::NX]));
-    hi = tmax(tmax(vu.v[0], tmax(s.bbx[ix], s.bbx[ix + 1])), tmax(s.bby[iy], s.bby[iy + G::NX]));
-    if constexpr (LAW::kEntropy) {
-      const int sl = (col == 0) ? G::hW + row : G::slot(row, col - 1);
-      const int sr = (col == G::NX - 1) ? G::hE + row : G::slot(row, col + 1);
-      const int sd = (row == 0) ? G::hS + col : G::slot(row - 1, col);
-      const int su = (row == G::NY - 1) ? G::hN + col : G::slot(row + 1, col);
-      K = tmin(tmin(s.sig[me], tmin(s.sig[sl], s.sig[sr])), tmin(s.sig[sd], s.sig[su]));
-    }
+    const auto bl = s.bbx[ix], br = s.bbx[ix + 1], bd = s.bby[iy], bu = s.bby[iy + G::NX];
+    lo = tmin(tmin(vu.v[0], tmin(bl.v[0], br.v[0])), tmin(bd.v[0], bu.v[0]));
+    hi = tmax(tmax(vu.v[0], tmax(bl.v[0], br.v[0])), tmax(bd.v[0], bu.v[0]));
+    // K_i = min sigma over the node and its four neighbours = min over its four faces' minima
+    if constexpr (LAW::kEntropy) K = tmin(tmin(bl.v[1], br.v[1]), tmin(bd.v[1], bu.v[1]));
   }
   if (A.limiter != 2) return;  // uniform across the CTA
   __syncthreads();  // all reads of F_x, F_y done
@@ -539,25 +524,29 @@ k_dt(const StageLaunch<T> A, unsigned long long* out_bits) {
   const int tile_y = blockIdx.x / tiles_x, tile_x = blockIdx.x - tile_y * tiles_x;
   int le, a, b;
   long long g;
-  const bool act = load_tile<P, TX, TY, LAW>(s, A, tile_x, tile_y, le, a, b, g);
+  const bool act = load_tile<P, TX, TY, LAW, true>(s, A, tile_x, tile_y, le, a, b, g);
   __syncthreads();
-  T* lamx = s.bbx;  // face lambdas reuse the bar-state arrays
-  T* lamy = s.bby;
-#pragma unroll 1
-  for (int f = t; f < G::NFX + G::NFY; f += G::THREADS) {
-    if (f < G::NFX) {
-      const int row = f / (G::NX + 1), c = f - row * (G::NX + 1);
-      const int L = (c == 0) ? G::hW + row : G::slot(row, c - 1);
-      const int R = (c == G::NX) ? G::hE + row : G::slot(row, c);
+  T* lamx = reinterpret_cast<T*>(s.bbx);  // face lambdas reuse the bar-state arrays
+  T* lamy = reinterpret_cast<T*>(s.bby);
+  if (t < G::NT) {
+    const int row = (le / TX) * n + a, col = (le % TX) * n + b;
+    const V uR = s.u[t];
+    const typename LAW::Aux aR = s.aux[t];
+    const int L = Nbr<P, TX, TY>::left(t, b, row, col), D = Nbr<P, TX, TY>::down(t, a, row, col);
+    const V uL = s.u[L], uD = s.u[D];
+    lamx[row * (G::NX + 1) + col] = LAW::lam(0, uL.v, s.aux[L], uR.v, aR, lp);
+    lamy[row * G::NX + col] = LAW::lam(1, uD.v, s.aux[D], uR.v, aR, lp);
+  }
+  for (int e2 = t; e2 < G::NY + G::NX; e2 += G::THREADS) {
+    if (e2 < G::NY) {
+      const int L = G::slot(e2, G::NX - 1), R = G::hE + e2;
       const V uL = s.u[L], uR = s.u[R];
-      lamx[f] = LAW::lam(0, uL.v, s.aux[L], uR.v, s.aux[R], lp);
+      lamx[e2 * (G::NX + 1) + G::NX] = LAW::lam(0, uL.v, s.aux[L], uR.v, s.aux[R], lp);
     } else {
-      const int fi = f - G::NFX;
-      const int r = fi / G::NX, col = fi - r * G::NX;
-      const int L = (r == 0) ? G::hS + col : G::slot(r - 1, col);
-      const int R = (r == G::NY) ? G::hN + col : G::slot(r, col);
+      const int col = e2 - G::NY;
+      const int L = G::slot(G::NY - 1, col), R = G::hN + col;
       const V uL = s.u[L], uR = s.u[R];
-      lamy[fi] = LAW::lam(1, uL.v, s.aux[L], uR.v, s.aux[R], lp);
+      lamy[G::NY * G::NX + col] = LAW::lam(1, uL.v, s.aux[L], uR.v, s.aux[R], lp);
     }
   }
   __syncthreads();

@@ -70,43 +70,48 @@ template <typename T>
 struct LawEuler {
   static constexpr int NC = 4;
   static constexpr bool kEntropy = true;
-  struct alignas(8 * sizeof(T) >= 32 ? 32 : 8 * sizeof(T)) Aux {
-    T v[2];   // velocity
-    T p;      // pressure
+  // Per-node quantities kept for the faces (16 bytes in float32): the normal velocity is
+  // m_k / rho, and the two-rarefaction bound needs p only through p*/p.
+  struct alignas(4 * sizeof(T) >= 16 ? 16 : 4 * sizeof(T)) Aux {
+    T rinv;   // 1 / rho
     T a;      // sound speed
-    T ip;     // 1 / p
     T apm;    // a p^{-(gamma-1)/(2 gamma)}
-    T pad[2]; // 8 values: two 16-byte (float) loads
+    T ip;     // 1 / p
   };
+  // Pressure (Eq. euler-eos), aux, and both flux components (Eq. euler-flux) of one node.
+  __device__ static T pressure(const T* u, T rinv, const LawParamsT<T>& lp) {
+    return lp.gm1 * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * rinv);
+  }
   __device__ static void aux(const T* u, Aux& x, const LawParamsT<T>& lp) {
-    const T rinv = frcp(u[0]);
-    x.v[0] = u[1] * rinv;
-    x.v[1] = u[2] * rinv;
-    x.p = lp.gm1 * (u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) * rinv);  // Eq. euler-eos
-    x.a = psqrt(lp.gamma * x.p * rinv);
-    x.ip = frcp(x.p);
-    x.apm = x.a * ppow(x.p, lp.neg_e);
+    x.rinv = frcp(u[0]);
+    const T p = pressure(u, x.rinv, lp);
+    x.a = psqrt(lp.gamma * p * x.rinv);
+    x.ip = frcp(p);
+    x.apm = x.a * ppow(p, lp.neg_e);
   }
   // Eq. euler-flux along e_k: (m_k, m_k v_x + p d_{0k}, m_k v_y + p d_{1k}, (rho E + p) v_k)
-  __device__ static void flux(const T* u, const Aux& x, int k, T* f, const LawParamsT<T>&) {
+  __device__ static void flux(const T* u, const Aux& x, int k, T* f, const LawParamsT<T>& lp) {
+    const T p = pressure(u, x.rinv, lp);
     const T mk = u[1 + k];
+    const T vk = mk * x.rinv;
     f[0] = mk;
-    f[1] = mk * x.v[0] + (k == 0 ? x.p : T(0));
-    f[2] = mk * x.v[1] + (k == 1 ? x.p : T(0));
-    f[3] = (u[3] + x.p) * x.v[k];
+    f[1] = u[1] * vk + (k == 0 ? p : T(0));
+    f[2] = u[2] * vk + (k == 1 ? p : T(0));
+    f[3] = (u[3] + p) * vk;
   }
   // Guermond-Popov two-rarefaction bound (guaranteed for 1 < gamma <= 5/3): the two-rarefaction
-  // pressure bounds the star pressure from above, and the extreme speeds grow with it.
-  __device__ static T lam(int k, const T*, const Aux& L, const T*, const Aux& R, const LawParamsT<T>& lp) {
-    const T num = tmax(L.a + R.a - lp.half_gm1 * (R.v[k] - L.v[k]), T(0));
+  // pressure p* bounds the star pressure from above, and the extreme speeds grow with it.
+  __device__ static T lam(int k, const T* uL, const Aux& L, const T* uR, const Aux& R, const LawParamsT<T>& lp) {
+    const T vL = uL[1 + k] * L.rinv, vR = uR[1 + k] * R.rinv;
+    const T num = tmax(L.a + R.a - lp.half_gm1 * (vR - vL), T(0));
     const T ps = pstar_pow(fdiv(num, L.apm + R.apm), lp);
-    const T lL = L.v[k] - L.a * psqrt(T(1) + lp.c_gp * tmax(ps - L.p, T(0)) * L.ip);
-    const T lR = R.v[k] + R.a * psqrt(T(1) + lp.c_gp * tmax(ps - R.p, T(0)) * R.ip);
+    const T lL = vL - L.a * psqrt(T(1) + lp.c_gp * tmax(ps * L.ip - T(1), T(0)));
+    const T lR = vR + R.a * psqrt(T(1) + lp.c_gp * tmax(ps * R.ip - T(1), T(0)));
     return tmax(fabs(lL), fabs(lR));
   }
   // sigma = rho e rho^-gamma; s = log(sigma)/(gamma-1) (Sec. 4.3)
   __device__ static T sigma(const T* u, const Aux& x, const LawParamsT<T>& lp) {
-    return x.p * lp.inv_gm1 * ppow(u[0], -lp.gamma);
+    return pressure(u, x.rinv, lp) * lp.inv_gm1 * ppow(u[0], -lp.gamma);
   }
   __device__ static T sigma_of(const T* u, const LawParamsT<T>& lp) {
     const T rhoe = u[3] - T(0.5) * fdiv(u[1] * u[1] + u[2] * u[2], u[0]);
