@@ -176,10 +176,12 @@ const char* sidp_status_str(sidp_status s);
 const char* sidp_last_error(const sidp_ctx* ctx);
 
 /* ---------------------------------------------------------------- batches
- * Many independent problems (each its own mesh, p, law, BCs, dt) advanced together: one
- * launch per RK stage covers every instance (a task table of (instance, element tile)
- * entries, grouped by p), and a whole step is captured in one CUDA graph.  All configs
- * of a batch must share law and precision. */
+ * Many independent problems (each its own mesh size, degree p, domain, periodic/outflow sides
+ * and time step) advanced together.  Work is a task table of (instance, element tile) entries
+ * grouped by p: each RK stage is one launch per degree group covering every tile of every
+ * instance of that degree, and a whole step (per-instance dt included) is one CUDA graph.  All
+ * configs of a batch share law, precision, limiter and law parameters.  Instance i's state is
+ * exchanged as float64 [nc][N_i] like a single context's. */
 sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int count, void* cuda_stream);
 sidp_status sidp_batch_destroy(sidp_batch* b);
 sidp_status sidp_batch_sizes(const sidp_batch* b, int i, long long* n_nodes, int* nc);
@@ -189,6 +191,7 @@ sidp_status sidp_batch_set_state(sidp_batch* b, int i, const double* u);
 sidp_status sidp_batch_get_state(sidp_batch* b, int i, double* u);
 sidp_status sidp_batch_step(sidp_batch* b, int nsteps);
 sidp_status sidp_batch_get_diag(sidp_batch* b, int i, sidp_diag* out);
+sidp_status sidp_batch_set_stats(sidp_batch* b, int on);   /* per-stage bound statistics (default on) */
 sidp_status sidp_batch_synchronize(sidp_batch* b);
 const char* sidp_batch_last_error(const sidp_batch* b);
 

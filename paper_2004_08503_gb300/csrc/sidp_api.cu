@@ -270,6 +270,22 @@ void tune_table_store() {
 
 cudaError_t run_stage(sidp_ctx* c, int k);
 cudaError_t run_dt(sidp_ctx* c, bool adv);
+}  // namespace
+
+namespace sidp {
+int tuned_tile(int law, int p, int mixed) {
+  if (const char* f = std::getenv("SIDP_TILE")) {
+    const int t = std::atoi(f);
+    if (t >= 0 && t < kNumTiles) return t;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_table_init();
+  if (law < 1 || law > 3 || p < 1 || p > kMaxP || mixed < 0 || mixed > 1) return -1;
+  return g_tune[law][p][mixed];
+}
+}  // namespace sidp
+
+namespace {
 
 cudaError_t autotune(sidp_ctx* c) {
   if (c->tuned) return cudaSuccess;
@@ -318,7 +334,10 @@ void drop_graph(sidp_ctx* c) {
   c->graph = nullptr;
 }
 
-sidp_status validate(const sidp_config* cfg, std::string& msg) {
+}  // namespace
+
+namespace sidp {
+sidp_status validate_config(const sidp_config* cfg, std::string& msg) {
   if (!cfg) { msg = "null config"; return SIDP_ERR_ARG; }
   if (cfg->law != SIDP_LAW_BURGERS2D && cfg->law != SIDP_LAW_EULER2D && cfg->law != SIDP_LAW_ADVECTION2D) { msg = "unknown law"; return SIDP_ERR_ARG; }
   if (cfg->p < 1 || cfg->p > kMaxP) { msg = "p must be in 1..7"; return SIDP_ERR_ARG; }
@@ -336,6 +355,9 @@ sidp_status validate(const sidp_config* cfg, std::string& msg) {
   if (!std::isfinite(cfg->adv_beta[0]) || !std::isfinite(cfg->adv_beta[1])) { msg = "non-finite advection velocity"; return SIDP_ERR_ARG; }
   return SIDP_OK;
 }
+}  // namespace sidp
+
+namespace {
 
 template <typename T>
 sidp_status upload(sidp_ctx* c, void* dst, const double* src, long long count) {
@@ -370,7 +392,7 @@ sidp_status sidp_create(sidp_ctx** out, const sidp_config* cfg, void* cuda_strea
   if (!out) return fail(nullptr, SIDP_ERR_ARG, "null output pointer");
   *out = nullptr;
   std::string msg;
-  sidp_status st = validate(cfg, msg);
+  sidp_status st = validate_config(cfg, msg);
   if (st != SIDP_OK) return fail(nullptr, st, msg);
   sidp_ctx* c = new sidp_ctx();
   c->cfg = *cfg;

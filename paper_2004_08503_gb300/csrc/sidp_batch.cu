@@ -1,23 +1,462 @@
-// Batched execution of independent problems (placeholder until the batched scheduler lands).
-#include "sidp.h"
+// Batched execution of independent problems (sidp_batch_*).
+//
+// Every instance owns a slice of three shared state buffers (u^n, u^(1), u^(2); each slice is the
+// instance's [nc][N_i] field-major state in library node order) and its own time step.  Work is
+// a task table of (instance, element tile) entries grouped by polynomial degree: each degree
+// group is one launch of the tile kernel templated on that degree, over all tiles of all its
+// instances.  A step is
+//     dt launches (one per degree group) -> per-instance finalisation -> 3 x stage launches per group
+// and is captured once in a CUDA graph that later steps replay.
+//
+// Trade-off: one launch per degree group rather than one launch that switches on p inside: a
+// single kernel holding every degree's code path would carry the register and shared-memory
+// footprint of the largest degree for all tasks.  With the graph, the extra launches cost
+// little next to the per-stage work.
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
 
-struct sidp_batch {
-  int unused;
+#include "sidp.h"
+#include "sidp_internal.h"
+
+using namespace sidp;
+
+namespace {
+
+__global__ void k_batch_finalize(unsigned long long* bits, const double* cfl, double* dt, float* dtf, double* clock,
+                                 int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double mn = __longlong_as_double((long long)bits[i]);
+  const double v = (mn < DBL_MAX) ? cfl[i] * mn : 0.0;
+  dt[i] = v;
+  dtf[i] = (float)v;
+  clock[i] += v;
+  bits[i] = (unsigned long long)__double_as_longlong(DBL_MAX);
+}
+
+struct Group {
+  int p = 0;
+  int tile = 0;
+  int2* d_tasks = nullptr;
+  int ntasks = 0;
 };
 
+thread_local std::string g_batch_err;
+
+}  // namespace
+
+struct sidp_batch {
+  std::vector<sidp_config> cfgs;
+  int n = 0, law = 0, nc = 1, limiter = 2;
+  bool mixed = false;
+  size_t esize = 8;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<long long> N, off;  // nodes and value offset of each instance
+  long long total_vals = 0;
+  void* d_u[3] = {nullptr, nullptr, nullptr};
+  void* d_inst[4] = {nullptr, nullptr, nullptr, nullptr};  // instance tables: dt, stage 1, 2, 3
+  double* d_dt = nullptr;
+  float* d_dtf = nullptr;
+  double* d_clock = nullptr;
+  double* d_cfl = nullptr;
+  unsigned long long* d_bits = nullptr;
+  StageStats* d_stats = nullptr;
+  std::vector<Group> groups;
+  cudaGraphExec_t graph = nullptr;
+  bool warm = false;
+  bool stats_on = true;
+  long long steps = 0;
+  std::string err;
+};
+
+namespace {
+
+sidp_status bfail(sidp_batch* b, sidp_status s, const std::string& m) {
+  if (b) b->err = m;
+  g_batch_err = m;
+  return s;
+}
+
+#define BCUDA(b, expr)                                                                               \
+  do {                                                                                               \
+    cudaError_t _e = (expr);                                                                         \
+    if (_e != cudaSuccess) return bfail(b, SIDP_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+template <typename T>
+cudaError_t build_tables(sidp_batch* b) {
+  std::vector<Instance<T>> tab[4];
+  for (int k = 0; k < 4; ++k) tab[k].resize(b->n);
+  T* u[3] = {static_cast<T*>(b->d_u[0]), static_cast<T*>(b->d_u[1]), static_cast<T*>(b->d_u[2])};
+  const T* dtT;
+  if constexpr (sizeof(T) == 4) dtT = reinterpret_cast<const T*>(b->d_dtf);
+  else dtT = reinterpret_cast<const T*>(b->d_dt);
+  for (int i = 0; i < b->n; ++i) {
+    const sidp_config& c = b->cfgs[i];
+    Instance<T> I;
+    std::memset(&I, 0, sizeof(I));
+    I.N = b->N[i];
+    I.nx = c.nx;
+    I.ny = c.ny;
+    for (int s = 0; s < 4; ++s) I.bc[s] = c.bc[s];
+    I.h = (c.x1 - c.x0) / c.nx;
+    I.hT = T(I.h);
+    I.dt = b->d_dt + i;
+    I.dtT = dtT + i;
+    I.stats = b->stats_on ? b->d_stats + i : nullptr;
+    const long long o = b->off[i];
+    // dt launch reads u^n
+    Instance<T> d = I;
+    d.uin = u[0] + o;
+    tab[0][i] = d;
+    Instance<T> s1 = I;
+    s1.uin = u[0] + o; s1.u0 = u[0] + o; s1.uout = u[1] + o; s1.c0 = T(0); s1.c1 = T(1);
+    tab[1][i] = s1;
+    Instance<T> s2 = I;
+    s2.uin = u[1] + o; s2.u0 = u[0] + o; s2.uout = u[2] + o; s2.c0 = T(0.75); s2.c1 = T(0.25);
+    tab[2][i] = s2;
+    Instance<T> s3 = I;
+    s3.uin = u[2] + o; s3.u0 = u[0] + o; s3.uout = u[0] + o; s3.c0 = T(1.0 / 3.0); s3.c1 = T(2.0 / 3.0);
+    tab[3][i] = s3;
+  }
+  for (int k = 0; k < 4; ++k) {
+    cudaError_t e = cudaSuccess;
+    if (!b->d_inst[k]) e = cudaMalloc(&b->d_inst[k], sizeof(Instance<T>) * b->n);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(b->d_inst[k], tab[k].data(), sizeof(Instance<T>) * b->n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <int LAW, typename T>
+cudaError_t launch_batch_law(int p, int tile, const BatchLaunch<T>& bl, bool dt, cudaStream_t s) {
+  switch (p) {
+    case 1: return launch_batch_p<LAW, T, 1>(tile, bl, dt, s);
+    case 2: return launch_batch_p<LAW, T, 2>(tile, bl, dt, s);
+    case 3: return launch_batch_p<LAW, T, 3>(tile, bl, dt, s);
+    case 4: return launch_batch_p<LAW, T, 4>(tile, bl, dt, s);
+    case 5: return launch_batch_p<LAW, T, 5>(tile, bl, dt, s);
+    case 6: return launch_batch_p<LAW, T, 6>(tile, bl, dt, s);
+    case 7: return launch_batch_p<LAW, T, 7>(tile, bl, dt, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// k = 0: time-step launch; k = 1..3: SSP-RK3 stage k (Sec. 5).
+template <typename T>
+cudaError_t launch_groups(sidp_batch* b, int k) {
+  for (const Group& gr : b->groups) {
+    BatchLaunch<T> bl;
+    std::memset(&bl, 0, sizeof(bl));
+    bl.insts = static_cast<const Instance<T>*>(b->d_inst[k]);
+    bl.tasks = gr.d_tasks;
+    bl.ntasks = gr.ntasks;
+    double xi[kMaxN], w[kMaxN], D[kMaxN * kMaxN];
+    gll_tables(gr.p, xi, w, D);
+    const int nn = gr.p + 1;
+    for (int i = 0; i < nn; ++i) bl.tab.w[i] = T(w[i]);
+    for (int i = 0; i < nn * nn; ++i) bl.tab.D[i] = T(D[i]);
+    bl.lp = make_law_params<T>(b->cfgs[0].gamma, b->cfgs[0].adv_beta);
+    bl.limiter = b->limiter;
+    bl.bits = b->d_bits;
+    cudaError_t e;
+    switch (b->law) {
+      case LAW_BURGERS: e = launch_batch_law<LAW_BURGERS, T>(gr.p, gr.tile, bl, k == 0, b->stream); break;
+      case LAW_EULER: e = launch_batch_law<LAW_EULER, T>(gr.p, gr.tile, bl, k == 0, b->stream); break;
+      default: e = launch_batch_law<LAW_ADVECTION, T>(gr.p, gr.tile, bl, k == 0, b->stream); break;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  if (k == 0) {
+    k_batch_finalize<<<(b->n + 127) / 128, 128, 0, b->stream>>>(b->d_bits, b->d_cfl, b->d_dt, b->d_dtf, b->d_clock, b->n);
+    return cudaGetLastError();
+  }
+  return cudaSuccess;
+}
+
+cudaError_t run_batch_step(sidp_batch* b) {
+  for (int k = 0; k <= 3; ++k) {
+    cudaError_t e = b->mixed ? launch_groups<float>(b, k) : launch_groups<double>(b, k);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
 extern "C" {
-sidp_status sidp_batch_create(sidp_batch** out, const sidp_config*, int, void*) {
-  if (out) *out = nullptr;
-  return SIDP_ERR_ARG;
+
+sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int count, void* cuda_stream) {
+  if (!out) return bfail(nullptr, SIDP_ERR_ARG, "null output pointer");
+  *out = nullptr;
+  if (!cfgs || count < 1) return bfail(nullptr, SIDP_ERR_ARG, "empty batch");
+  for (int i = 0; i < count; ++i) {
+    std::string msg;
+    if (validate_config(&cfgs[i], msg) != SIDP_OK) return bfail(nullptr, SIDP_ERR_ARG, "instance " + std::to_string(i) + ": " + msg);
+    if (cfgs[i].law != cfgs[0].law || cfgs[i].precision != cfgs[0].precision || cfgs[i].limiter != cfgs[0].limiter ||
+        cfgs[i].gamma != cfgs[0].gamma || cfgs[i].adv_beta[0] != cfgs[0].adv_beta[0] || cfgs[i].adv_beta[1] != cfgs[0].adv_beta[1])
+      return bfail(nullptr, SIDP_ERR_ARG, "all instances of a batch share law, precision, limiter and law parameters");
+    for (int s = 0; s < 4; ++s)
+      if (cfgs[i].bc[s] == SIDP_BC_EXACT_STATE) return bfail(nullptr, SIDP_ERR_ARG, "exact-state sides are not supported in batches");
+  }
+  sidp_batch* b = new sidp_batch();
+  b->cfgs.assign(cfgs, cfgs + count);
+  b->n = count;
+  b->law = cfgs[0].law;
+  b->nc = (b->law == SIDP_LAW_EULER2D) ? 4 : 1;
+  b->limiter = cfgs[0].limiter;
+  b->mixed = cfgs[0].precision == SIDP_MIXED;
+  b->esize = b->mixed ? 4 : 8;
+  auto bail = [&](sidp_status s, const std::string& m) {
+    g_batch_err = m;
+    sidp_batch_destroy(b);
+    return s;
+  };
+  b->N.resize(count);
+  b->off.resize(count);
+  long long tot = 0;
+  std::map<int, std::vector<int2>> tasks;
+  for (int i = 0; i < count; ++i) {
+    const sidp_config& c = cfgs[i];
+    const int nn = (c.p + 1) * (c.p + 1);
+    b->N[i] = (long long)c.nx * c.ny * nn;
+    b->off[i] = tot;
+    tot += b->nc * b->N[i];
+    int tile = tuned_tile(c.law, c.p, b->mixed ? 1 : 0);
+    if (tile < 0) tile = 0;
+    const TileShape ts = kTiles[c.p][tile];
+    const long long ntiles = (long long)((c.nx + ts.tx - 1) / ts.tx) * ((c.ny + ts.ty - 1) / ts.ty);
+    for (long long t = 0; t < ntiles; ++t) tasks[c.p].push_back(make_int2(i, (int)t));
+  }
+  b->total_vals = tot;
+  cudaError_t e;
+  if (cuda_stream) {
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if ((e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking)) != cudaSuccess) return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
+    b->own_stream = true;
+  }
+  for (int k = 0; k < 3; ++k)
+    if (cudaMalloc(&b->d_u[k], tot * b->esize) != cudaSuccess) return bail(SIDP_ERR_OOM, "state allocation failed");
+  if (cudaMalloc(&b->d_dt, count * sizeof(double)) != cudaSuccess || cudaMalloc(&b->d_dtf, count * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&b->d_clock, count * sizeof(double)) != cudaSuccess || cudaMalloc(&b->d_cfl, count * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&b->d_bits, count * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMalloc(&b->d_stats, count * sizeof(StageStats)) != cudaSuccess)
+    return bail(SIDP_ERR_OOM, "scratch allocation failed");
+  std::vector<double> cfl(count), zero(count, 0.0);
+  std::vector<unsigned long long> big(count, 0x7fefffffffffffffULL);
+  std::vector<StageStats> zs(count);
+  std::memset(zs.data(), 0, zs.size() * sizeof(StageStats));
+  for (int i = 0; i < count; ++i) cfl[i] = cfgs[i].cfl;
+  if ((e = cudaMemcpy(b->d_cfl, cfl.data(), count * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_clock, zero.data(), count * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_dt, zero.data(), count * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_bits, big.data(), count * sizeof(unsigned long long), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(b->d_stats, zs.data(), count * sizeof(StageStats), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(b->d_u[0], 0, tot * b->esize)) != cudaSuccess)
+    return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
+  if ((e = b->mixed ? build_tables<float>(b) : build_tables<double>(b)) != cudaSuccess) return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
+  for (auto& kv : tasks) {
+    Group g;
+    g.p = kv.first;
+    g.tile = tuned_tile(b->law, g.p, b->mixed ? 1 : 0);
+    if (g.tile < 0) g.tile = 0;
+    g.ntasks = (int)kv.second.size();
+    if (cudaMalloc(&g.d_tasks, sizeof(int2) * g.ntasks) != cudaSuccess) return bail(SIDP_ERR_OOM, "task table allocation failed");
+    b->groups.push_back(g);
+    if ((e = cudaMemcpy(g.d_tasks, kv.second.data(), sizeof(int2) * g.ntasks, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
+  }
+  *out = b;
+  return SIDP_OK;
 }
-sidp_status sidp_batch_destroy(sidp_batch*) { return SIDP_OK; }
-sidp_status sidp_batch_sizes(const sidp_batch*, int, long long*, int*) { return SIDP_ERR_ARG; }
-sidp_status sidp_batch_total_nodes(const sidp_batch*, long long*) { return SIDP_ERR_ARG; }
-sidp_status sidp_batch_node_coords(const sidp_batch*, int, double*, double*) { return SIDP_ERR_ARG; }
-sidp_status sidp_batch_set_state(sidp_batch*, int, const double*) { return SIDP_ERR_ARG; }
-sidp_status sidp_batch_get_state(sidp_batch*, int, double*) { return SIDP_ERR_ARG; }
-sidp_status sidp_batch_step(sidp_batch*, int) { return SIDP_ERR_ARG; }
-sidp_status sidp_batch_get_diag(sidp_batch*, int, sidp_diag*) { return SIDP_ERR_ARG; }
-sidp_status sidp_batch_synchronize(sidp_batch*) { return SIDP_ERR_ARG; }
-const char* sidp_batch_last_error(const sidp_batch*) { return "batched execution not built yet"; }
+
+sidp_status sidp_batch_destroy(sidp_batch* b) {
+  if (!b) return SIDP_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (int k = 0; k < 3; ++k) cudaFree(b->d_u[k]);
+  for (int k = 0; k < 4; ++k) cudaFree(b->d_inst[k]);
+  for (auto& g : b->groups) cudaFree(g.d_tasks);
+  cudaFree(b->d_dt);
+  cudaFree(b->d_dtf);
+  cudaFree(b->d_clock);
+  cudaFree(b->d_cfl);
+  cudaFree(b->d_bits);
+  cudaFree(b->d_stats);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return SIDP_OK;
 }
+
+sidp_status sidp_batch_sizes(const sidp_batch* b, int i, long long* n_nodes, int* nc) {
+  if (!b || i < 0 || i >= b->n) return bfail(nullptr, SIDP_ERR_ARG, "bad batch or index");
+  if (n_nodes) *n_nodes = b->N[i];
+  if (nc) *nc = b->nc;
+  return SIDP_OK;
+}
+
+sidp_status sidp_batch_total_nodes(const sidp_batch* b, long long* n_nodes) {
+  if (!b || !n_nodes) return bfail(nullptr, SIDP_ERR_ARG, "null argument");
+  long long t = 0;
+  for (long long v : b->N) t += v;
+  *n_nodes = t;
+  return SIDP_OK;
+}
+
+sidp_status sidp_batch_node_coords(const sidp_batch* b, int i, double* x, double* y) {
+  if (!b || i < 0 || i >= b->n || !x || !y) return bfail(nullptr, SIDP_ERR_ARG, "bad argument");
+  const sidp_config& c = b->cfgs[i];
+  double xi[kMaxN], w[kMaxN], D[kMaxN * kMaxN];
+  gll_tables(c.p, xi, w, D);
+  const int n = c.p + 1, NN = n * n;
+  const double h = (c.x1 - c.x0) / c.nx;
+  for (long long e = 0; e < (long long)c.nx * c.ny; ++e) {
+    const long long ex = e % c.nx, ey = e / c.nx;
+    for (int a = 0; a < n; ++a)
+      for (int bb = 0; bb < n; ++bb) {
+        x[e * NN + a * n + bb] = c.x0 + ((double)ex + xi[bb]) * h;
+        y[e * NN + a * n + bb] = c.y0 + ((double)ey + xi[a]) * h;
+      }
+  }
+  return SIDP_OK;
+}
+
+sidp_status sidp_batch_set_state(sidp_batch* b, int i, const double* u) {
+  if (!b || i < 0 || i >= b->n || !u) return bfail(b, SIDP_ERR_ARG, "bad argument");
+  const long long N = b->N[i], cnt = b->nc * N;
+  for (long long j = 0; j < cnt; ++j)
+    if (!std::isfinite(u[j])) return bfail(b, SIDP_ERR_NONFINITE, "state holds a non-finite value");
+  if (b->law == SIDP_LAW_EULER2D) {
+    const double g = b->cfgs[i].gamma;
+    for (long long j = 0; j < N; ++j) {
+      const double r = u[j], p = (g - 1.0) * (u[3 * N + j] - 0.5 * (u[N + j] * u[N + j] + u[2 * N + j] * u[2 * N + j]) / r);
+      if (!(r > 0) || !(p > 0)) return bfail(b, SIDP_ERR_BOUNDS, "Euler state with rho <= 0 or p <= 0");
+    }
+  }
+  char* dst = static_cast<char*>(b->d_u[0]) + b->off[i] * b->esize;
+  if (b->mixed) {
+    std::vector<float> tmp(cnt);
+    for (long long j = 0; j < cnt; ++j) tmp[j] = (float)u[j];
+    BCUDA(b, cudaMemcpyAsync(dst, tmp.data(), cnt * sizeof(float), cudaMemcpyHostToDevice, b->stream));
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+  } else {
+    BCUDA(b, cudaMemcpyAsync(dst, u, cnt * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+  }
+  return SIDP_OK;
+}
+
+sidp_status sidp_batch_get_state(sidp_batch* b, int i, double* u) {
+  if (!b || i < 0 || i >= b->n || !u) return bfail(b, SIDP_ERR_ARG, "bad argument");
+  const long long cnt = b->nc * b->N[i];
+  const char* src = static_cast<const char*>(b->d_u[0]) + b->off[i] * b->esize;
+  if (b->mixed) {
+    std::vector<float> tmp(cnt);
+    BCUDA(b, cudaMemcpyAsync(tmp.data(), src, cnt * sizeof(float), cudaMemcpyDeviceToHost, b->stream));
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+    for (long long j = 0; j < cnt; ++j) u[j] = tmp[j];
+  } else {
+    BCUDA(b, cudaMemcpyAsync(u, src, cnt * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    BCUDA(b, cudaStreamSynchronize(b->stream));
+  }
+  return SIDP_OK;
+}
+
+sidp_status sidp_batch_step(sidp_batch* b, int nsteps) {
+  if (!b || nsteps < 0) return bfail(b, SIDP_ERR_ARG, "bad argument");
+  int done = 0;
+  if (!b->warm && nsteps > 0) {  // first step eagerly: kernel attributes are set outside capture
+    BCUDA(b, run_batch_step(b));
+    b->warm = true;
+    ++done;
+  }
+  if (done < nsteps && !b->graph) {
+    cudaGraph_t g = nullptr;
+    BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = run_batch_step(b);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return bfail(b, SIDP_ERR_CUDA, std::string("graph capture failed: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { b->graph = nullptr; return bfail(b, SIDP_ERR_CUDA, cudaGetErrorString(e)); }
+  }
+  for (; done < nsteps; ++done) BCUDA(b, cudaGraphLaunch(b->graph, b->stream));
+  b->steps += nsteps;
+  return SIDP_OK;
+}
+
+sidp_status sidp_batch_get_diag(sidp_batch* b, int i, sidp_diag* out) {
+  if (!b || i < 0 || i >= b->n || !out) return bfail(b, SIDP_ERR_ARG, "bad argument");
+  std::memset(out, 0, sizeof(*out));
+  const sidp_config& c = b->cfgs[i];
+  const long long N = b->N[i];
+  std::vector<double> u(b->nc * N);
+  sidp_status st = sidp_batch_get_state(b, i, u.data());
+  if (st != SIDP_OK) return st;
+  double xi[kMaxN], w[kMaxN], D[kMaxN * kMaxN];
+  gll_tables(c.p, xi, w, D);
+  const int n = c.p + 1, NN = n * n;
+  const double h = (c.x1 - c.x0) / c.nx;
+  for (int f = 0; f < 4; ++f) { out->umin[f] = f < b->nc ? DBL_MAX : 0.0; out->umax[f] = f < b->nc ? -DBL_MAX : 0.0; }
+  out->rho_min = out->p_min = (b->law == SIDP_LAW_EULER2D) ? DBL_MAX : 0.0;
+  for (long long j = 0; j < N; ++j) {
+    const int node = (int)(j % NN);
+    const double m = h * h * w[node / n] * w[node % n];
+    for (int f = 0; f < b->nc; ++f) {
+      const double v = u[f * N + j];
+      if (!std::isfinite(v)) { ++out->nonfinite; continue; }
+      out->mass[f] += m * v;
+      out->umin[f] = std::fmin(out->umin[f], v);
+      out->umax[f] = std::fmax(out->umax[f], v);
+    }
+    if (b->law == SIDP_LAW_EULER2D) {
+      const double r = u[j], p = (c.gamma - 1.0) * (u[3 * N + j] - 0.5 * (u[N + j] * u[N + j] + u[2 * N + j] * u[2 * N + j]) / r);
+      out->rho_min = std::fmin(out->rho_min, r);
+      out->p_min = std::fmin(out->p_min, p);
+    }
+  }
+  StageStats ss;
+  double sc[2];
+  BCUDA(b, cudaMemcpy(&ss, b->d_stats + i, sizeof(ss), cudaMemcpyDeviceToHost));
+  BCUDA(b, cudaMemcpy(&sc[0], b->d_clock + i, sizeof(double), cudaMemcpyDeviceToHost));
+  BCUDA(b, cudaMemcpy(&sc[1], b->d_dt + i, sizeof(double), cudaMemcpyDeviceToHost));
+  out->t = sc[0];
+  out->last_dt = sc[1];
+  out->steps = b->steps;
+  std::memcpy(&out->max_bound_violation, &ss.max_bound_violation, sizeof(double));
+  std::memcpy(&out->max_entropy_violation, &ss.max_entropy_violation, sizeof(double));
+  out->rootfind_max_iters = (int)ss.rootfind_max_iters;
+  out->rootfind_cap_hits = (long long)ss.rootfind_cap_hits;
+  if (out->nonfinite) return bfail(b, SIDP_ERR_NONFINITE, "state holds non-finite values");
+  return SIDP_OK;
+}
+
+sidp_status sidp_batch_set_stats(sidp_batch* b, int on) {
+  if (!b) return bfail(nullptr, SIDP_ERR_ARG, "null batch");
+  if ((on != 0) == b->stats_on) return SIDP_OK;
+  BCUDA(b, cudaStreamSynchronize(b->stream));
+  b->stats_on = on != 0;
+  if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+  BCUDA(b, b->mixed ? build_tables<float>(b) : build_tables<double>(b));
+  return SIDP_OK;
+}
+
+sidp_status sidp_batch_synchronize(sidp_batch* b) {
+  if (!b) return bfail(nullptr, SIDP_ERR_ARG, "null batch");
+  BCUDA(b, cudaStreamSynchronize(b->stream));
+  return SIDP_OK;
+}
+
+const char* sidp_batch_last_error(const sidp_batch* b) { return b ? b->err.c_str() : g_batch_err.c_str(); }
+
+}  // extern "C"

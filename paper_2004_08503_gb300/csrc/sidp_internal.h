@@ -1,7 +1,9 @@
 // Internal declarations shared by the host API and the kernel translation units.
 #pragma once
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
+#include "sidp.h"
 
 namespace sidp {
 
@@ -97,6 +99,19 @@ struct Instance {
   StageStats* stats; // null = off
 };
 
+// A launch over many instances: CTA i runs tasks[i] = (instance index, tile index); all tasks
+// share degree, tile shape, law, precision and limiter.
+template <typename T>
+struct BatchLaunch {
+  const Instance<T>* insts;  // device array, one per instance
+  const int2* tasks;         // device array of (instance, linear tile index)
+  int ntasks;
+  Tables<T> tab;
+  LawParamsT<T> lp;
+  int limiter;
+  unsigned long long* bits;  // per-instance time-step accumulators (dt launches)
+};
+
 template <typename T>
 struct StageLaunch {
   Instance<T> inst;
@@ -104,6 +119,10 @@ struct StageLaunch {
   LawParamsT<T> lp;
   int limiter;
 };
+
+// Host-side helpers shared by the single-instance and batched entry points.
+int tuned_tile(int law, int p, int mixed);  // autotuned tile index, or -1 when not tuned yet
+sidp_status validate_config(const sidp_config* cfg, std::string& msg);
 
 // Host tables (float64), computed once.
 void gll_tables(int p, double* xi, double* w, double* D);
@@ -116,8 +135,11 @@ namespace sidp {
 // the inst_<law>_<precision>*.cu translation units.
 template <int LAW, typename T, int P>
 cudaError_t launch_p(int tile, const StageLaunch<T>& a, unsigned long long* dt_bits, cudaStream_t s);
+template <int LAW, typename T, int P>
+cudaError_t launch_batch_p(int tile, const BatchLaunch<T>& b, bool dt, cudaStream_t s);
 #define SIDP_DECLARE_P(LAWID, TT, P) \
-  template <> cudaError_t launch_p<LAWID, TT, P>(int, const StageLaunch<TT>&, unsigned long long*, cudaStream_t);
+  template <> cudaError_t launch_p<LAWID, TT, P>(int, const StageLaunch<TT>&, unsigned long long*, cudaStream_t); \
+  template <> cudaError_t launch_batch_p<LAWID, TT, P>(int, const BatchLaunch<TT>&, bool, cudaStream_t);
 #define SIDP_DECLARE(LAWID, TT) \
   SIDP_DECLARE_P(LAWID, TT, 1) SIDP_DECLARE_P(LAWID, TT, 2) SIDP_DECLARE_P(LAWID, TT, 3) SIDP_DECLARE_P(LAWID, TT, 4) \
   SIDP_DECLARE_P(LAWID, TT, 5) SIDP_DECLARE_P(LAWID, TT, 6) SIDP_DECLARE_P(LAWID, TT, 7)
@@ -140,6 +162,16 @@ SIDP_DECLARE(LAW_ADVECTION, float)
       case 1: return launch_tile<P, kTiles[P][1].tx, kTiles[P][1].ty, LAWTPL<TT>, TT>(a, bits, s);     \
       case 2: return launch_tile<P, kTiles[P][2].tx, kTiles[P][2].ty, LAWTPL<TT>, TT>(a, bits, s);     \
       case 3: return launch_tile<P, kTiles[P][3].tx, kTiles[P][3].ty, LAWTPL<TT>, TT>(a, bits, s);     \
+      default: return cudaErrorInvalidValue;                                                           \
+    }                                                                                                  \
+  }                                                                                                    \
+  template <>                                                                                          \
+  cudaError_t launch_batch_p<LAWID, TT, P>(int tile, const BatchLaunch<TT>& b, bool dt, cudaStream_t s) { \
+    switch (tile) {                                                                                    \
+      case 0: return launch_batch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT>(b, dt, s); \
+      case 1: return launch_batch_tile<P, kTiles[P][1].tx, kTiles[P][1].ty, LAWTPL<TT>, TT>(b, dt, s); \
+      case 2: return launch_batch_tile<P, kTiles[P][2].tx, kTiles[P][2].ty, LAWTPL<TT>, TT>(b, dt, s); \
+      case 3: return launch_batch_tile<P, kTiles[P][3].tx, kTiles[P][3].ty, LAWTPL<TT>, TT>(b, dt, s); \
       default: return cudaErrorInvalidValue;                                                           \
     }                                                                                                  \
   }

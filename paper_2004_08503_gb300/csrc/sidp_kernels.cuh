@@ -125,15 +125,14 @@ __device__ __forceinline__ void fill_slot(S& s, int slot, const T* uu, const Law
 
 // Phase A: node slots and the halo.  Returns true for threads that own an active mesh node.
 template <int P, int TX, int TY, class LAW, bool LEAN, typename T, class S>
-__device__ __forceinline__ bool load_tile(S& s, const StageLaunch<T>& A, int tile_x, int tile_y, int& le, int& a,
-                                          int& b, long long& g) {
+__device__ __forceinline__ bool load_tile(S& s, const Instance<T>& I, const Tables<T>& tab, const LawParamsT<T>& lp,
+                                          int tile_x, int tile_y, int& le, int& a, int& b, long long& g) {
   using G = TileGeom<P, TX, TY>;
   constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
-  const Instance<T>& I = A.inst;
   const int t = threadIdx.x;
   const int ex0 = tile_x * TX, ey0 = tile_y * TY;
-  if (t < NN) s.D[t] = A.tab.D[t];
-  if (t < n) s.w[t] = A.tab.w[t];
+  if (t < NN) s.D[t] = tab.D[t];
+  if (t < n) s.w[t] = tab.w[t];
   bool act = false;
   le = 0; a = 0; b = 0; g = 0;
   if (t < G::NT) {
@@ -156,7 +155,7 @@ __device__ __forceinline__ bool load_tile(S& s, const StageLaunch<T>& A, int til
 #pragma unroll
       for (int f = 0; f < NC; ++f) uu[f] = I.uin[f * I.N + ((long long)ey0 * I.nx + ex0) * NN];
     }
-    fill_slot<LAW, LEAN>(s, t, uu, A.lp);
+    fill_slot<LAW, LEAN>(s, t, uu, lp);
   }
   for (int h = t; h < G::NH; h += G::THREADS) {
     T uu[NC];
@@ -174,7 +173,7 @@ __device__ __forceinline__ bool load_tile(S& s, const StageLaunch<T>& A, int til
 #pragma unroll
       for (int f = 0; f < NC; ++f) uu[f] = I.uin[f * I.N + ((long long)ey0 * I.nx + ex0) * NN];
     }
-    fill_slot<LAW, LEAN>(s, G::NT + h, uu, A.lp);
+    fill_slot<LAW, LEAN>(s, G::NT + h, uu, lp);
   }
   return act;
 }
@@ -312,25 +311,19 @@ __device__ __forceinline__ void face_eval_r(S& s, int k, int L, const Vec<T, LAW
   else { s.fby[fi] = fb; s.bby[fi] = bb; }
 }
 
+// The whole stage for one tile of one problem instance.
 template <int P, int TX, int TY, class LAW, typename T>
-__global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
-k_stage(const StageLaunch<T> A) {
+__device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const Instance<T>& I, const Tables<T>& tab,
+                                           const LawParamsT<T>& lp, int limiter, int tile_x, int tile_y) {
   using G = TileGeom<P, TX, TY>;
-  using S = TileSmem<P, TX, TY, LAW, T>;
   using V = Vec<T, LAW::NC>;
   constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  S& s = *reinterpret_cast<S*>(smem_raw);
-  const Instance<T>& I = A.inst;
-  const LawParamsT<T>& lp = A.lp;
   const int t = threadIdx.x;
-  const int tiles_x = (I.nx + TX - 1) / TX;
-  const int tile_y = blockIdx.x / tiles_x, tile_x = blockIdx.x - tile_y * tiles_x;
 
   // ---------------- A
   int le, a, b;
   long long g;
-  const bool act = load_tile<P, TX, TY, LAW, false>(s, A, tile_x, tile_y, le, a, b, g);
+  const bool act = load_tile<P, TX, TY, LAW, false>(s, I, tab, lp, tile_x, tile_y, le, a, b, g);
   __syncthreads();
 
   // ---------------- B: every face once.  Each node slot's thread evaluates the x face on its left
@@ -397,11 +390,11 @@ k_stage(const StageLaunch<T> A) {
       const T rLx = -hwa * (fr.v[q] - fl.v[q]);
       const T rLy = -hwb * (fu.v[q] - fd.v[q]);
       uL[q] = vu.v[q] + dtm * (rLx + rLy);
-      out[q] = (A.limiter == 0) ? vu.v[q] + dtm * (rHx + rHy) : uL[q];
+      out[q] = (limiter == 0) ? vu.v[q] + dtm * (rHx + rHy) : uL[q];
       rx[q] = rHx - rLx;
       ry[q] = rHy - rLy;
     }
-    if (A.limiter != 2) {  // high-order target or low-order update only: done
+    if (limiter != 2) {  // high-order target or low-order update only: done
 #pragma unroll
       for (int q = 0; q < NC; ++q)
         I.uout[q * N + g] = (I.c0 == T(0)) ? out[q] : I.c0 * I.u0[q * N + g] + I.c1 * out[q];
@@ -412,7 +405,7 @@ k_stage(const StageLaunch<T> A) {
     // K_i = min sigma over the node and its four neighbours = min over its four faces' minima
     if constexpr (LAW::kEntropy) K = tmin(tmin(bl.v[1], br.v[1]), tmin(bd.v[1], bu.v[1]));
   }
-  if (A.limiter != 2) return;  // uniform across the CTA
+  if (limiter != 2) return;  // uniform across the CTA
   __syncthreads();  // all reads of F_x, F_y done
   if (act) {
     V vrx, vry;
@@ -505,26 +498,54 @@ k_stage(const StageLaunch<T> A) {
   }
 }
 
+template <int P, int TX, int TY, class LAW, typename T>
+__global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
+k_stage(const StageLaunch<T> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& s = *reinterpret_cast<TileSmem<P, TX, TY, LAW, T>*>(smem_raw);
+  const int tiles_x = (A.inst.nx + TX - 1) / TX;
+  const int tile_y = blockIdx.x / tiles_x, tile_x = blockIdx.x - tile_y * tiles_x;
+  stage_body<P, TX, TY, LAW, T>(s, A.inst, A.tab, A.lp, A.limiter, tile_x, tile_y);
+}
+
+// Copy the instance descriptor of this CTA's task into shared memory (all threads help).
+template <typename T>
+__device__ __forceinline__ void load_instance(Instance<T>& dst, const Instance<T>* src) {
+  static_assert(sizeof(Instance<T>) % 4 == 0, "instance size");
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(&dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(Instance<T>) / 4); i += blockDim.x) d[i] = s[i];
+  __syncthreads();
+}
+
+// Batched stage: CTA blockIdx.x runs task (instance, tile) of the task table; all tasks of one
+// launch share P, the tile shape, law and precision.
+template <int P, int TX, int TY, class LAW, typename T>
+__global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
+k_stage_batch(const BatchLaunch<T> B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& s = *reinterpret_cast<TileSmem<P, TX, TY, LAW, T>*>(smem_raw);
+  __shared__ Instance<T> sI;
+  const int2 task = B.tasks[blockIdx.x];
+  load_instance(sI, B.insts + task.x);
+  const int tiles_x = (sI.nx + TX - 1) / TX;
+  const int tile_y = task.y / tiles_x, tile_x = task.y - tile_y * tiles_x;
+  stage_body<P, TX, TY, LAW, T>(s, sI, B.tab, B.lp, B.limiter, tile_x, tile_y);
+}
+
 // CFL bound of Eq. cfl-low per node, m_i / (2 sum_{j != i} d-hat_ij) with d-hat = (h w / 2) lambda on
 // the node's four faces, min-reduced into *out_bits (positive doubles order like their bit patterns).
 // Same tile machinery as the stage kernel: node quantities once per node, lambda once per face.
 template <int P, int TX, int TY, class LAW, typename T>
-__global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
-k_dt(const StageLaunch<T> A, unsigned long long* out_bits) {
+__device__ __forceinline__ void dt_body(TileSmem<P, TX, TY, LAW, T>& s, const Instance<T>& I, const Tables<T>& tab,
+                                        const LawParamsT<T>& lp, int tile_x, int tile_y, unsigned long long* out_bits) {
   using G = TileGeom<P, TX, TY>;
-  using S = TileSmem<P, TX, TY, LAW, T>;
   using V = Vec<T, LAW::NC>;
-  constexpr int n = P + 1, NN = n * n;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  S& s = *reinterpret_cast<S*>(smem_raw);
-  const Instance<T>& I = A.inst;
-  const LawParamsT<T>& lp = A.lp;
+  constexpr int n = P + 1;
   const int t = threadIdx.x;
-  const int tiles_x = (I.nx + TX - 1) / TX;
-  const int tile_y = blockIdx.x / tiles_x, tile_x = blockIdx.x - tile_y * tiles_x;
   int le, a, b;
   long long g;
-  const bool act = load_tile<P, TX, TY, LAW, true>(s, A, tile_x, tile_y, le, a, b, g);
+  const bool act = load_tile<P, TX, TY, LAW, true>(s, I, tab, lp, tile_x, tile_y, le, a, b, g);
   __syncthreads();
   T* lamx = reinterpret_cast<T*>(s.bbx);  // face lambdas reuse the bar-state arrays
   T* lamy = reinterpret_cast<T*>(s.bby);
@@ -576,6 +597,29 @@ k_dt(const StageLaunch<T> A, unsigned long long* out_bits) {
 }
 
 template <int P, int TX, int TY, class LAW, typename T>
+__global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
+k_dt(const StageLaunch<T> A, unsigned long long* out_bits) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& s = *reinterpret_cast<TileSmem<P, TX, TY, LAW, T>*>(smem_raw);
+  const int tiles_x = (A.inst.nx + TX - 1) / TX;
+  const int tile_y = blockIdx.x / tiles_x, tile_x = blockIdx.x - tile_y * tiles_x;
+  dt_body<P, TX, TY, LAW, T>(s, A.inst, A.tab, A.lp, tile_x, tile_y, out_bits);
+}
+
+template <int P, int TX, int TY, class LAW, typename T>
+__global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
+k_dt_batch(const BatchLaunch<T> B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& s = *reinterpret_cast<TileSmem<P, TX, TY, LAW, T>*>(smem_raw);
+  __shared__ Instance<T> sI;
+  const int2 task = B.tasks[blockIdx.x];
+  load_instance(sI, B.insts + task.x);
+  const int tiles_x = (sI.nx + TX - 1) / TX;
+  const int tile_y = task.y / tiles_x, tile_x = task.y - tile_y * tiles_x;
+  dt_body<P, TX, TY, LAW, T>(s, sI, B.tab, B.lp, tile_x, tile_y, B.bits + task.x);
+}
+
+template <int P, int TX, int TY, class LAW, typename T>
 cudaError_t launch_tile(const StageLaunch<T>& a, unsigned long long* dt_bits, cudaStream_t s) {
   using G = TileGeom<P, TX, TY>;
   constexpr size_t smem = sizeof(TileSmem<P, TX, TY, LAW, T>);
@@ -591,6 +635,24 @@ cudaError_t launch_tile(const StageLaunch<T>& a, unsigned long long* dt_bits, cu
   if (tiles <= 0) return cudaSuccess;
   if (dt_bits) k_dt<P, TX, TY, LAW, T><<<(unsigned)tiles, G::THREADS, smem, s>>>(a, dt_bits);
   else k_stage<P, TX, TY, LAW, T><<<(unsigned)tiles, G::THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int P, int TX, int TY, class LAW, typename T>
+cudaError_t launch_batch_tile(const BatchLaunch<T>& B, bool dt, cudaStream_t s) {
+  using G = TileGeom<P, TX, TY>;
+  constexpr size_t smem = sizeof(TileSmem<P, TX, TY, LAW, T>);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t err = cudaFuncSetAttribute(k_stage_batch<P, TX, TY, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(k_dt_batch<P, TX, TY, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    attr_set = true;
+  }
+  if (B.ntasks <= 0) return cudaSuccess;
+  if (dt) k_dt_batch<P, TX, TY, LAW, T><<<(unsigned)B.ntasks, G::THREADS, smem, s>>>(B);
+  else k_stage_batch<P, TX, TY, LAW, T><<<(unsigned)B.ntasks, G::THREADS, smem, s>>>(B);
   return cudaGetLastError();
 }
 

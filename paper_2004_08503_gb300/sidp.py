@@ -83,6 +83,7 @@ _SIGS = {
     "sidp_batch_step": (ctypes.c_int, [_P, ctypes.c_int]),
     "sidp_batch_get_diag": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(sidp_diag)]),
     "sidp_batch_synchronize": (ctypes.c_int, [_P]),
+    "sidp_batch_set_stats": (ctypes.c_int, [_P, ctypes.c_int]),
     "sidp_batch_last_error": (ctypes.c_char_p, [_P]),
 }
 
@@ -314,6 +315,10 @@ def sidp_batch_get_diag(b, i):
     d = sidp_diag()
     _bcheck(load().sidp_batch_get_diag(b, i, ctypes.byref(d)), b)
     return _diag_dict(d)
+
+
+def sidp_batch_set_stats(b, on):
+    _bcheck(load().sidp_batch_set_stats(b, int(on)), b)
 
 
 def sidp_batch_synchronize(b):
