@@ -110,6 +110,20 @@ def make_solver(precision, stream):
                        domain=(0.0, 1.0, 0.0, 1.0), bc=("outflow",) * 4, cfl=0.5, gamma=1.4, limiter="subcell")
 
 
+def max_over_ranks(torch, seconds, dist, device):
+    """Slowest rank's time (the job's time); identity on one process."""
+    if not dist:
+        return seconds
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units processed by all ranks divided by the job's time (weak scaling: each rank its own copy)."""
+    return units_per_rank * world / seconds
+
+
 def time_steps(torch, sv, stream, steps, warmup, dist=None, clocks_gpu=None):
     """Graph-replayed steps; returns (max-over-ranks seconds, clock summary)."""
     sv.step(warmup)
@@ -129,11 +143,7 @@ def time_steps(torch, sv, stream, steps, warmup, dist=None, clocks_gpu=None):
     torch.cuda.synchronize()
     if clk:
         clk.__exit__()
-    sec = ev0.elapsed_time(ev1) / 1e3
-    if dist:
-        t = torch.tensor([sec], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec = float(t.item())
+    sec = max_over_ranks(torch, ev0.elapsed_time(ev1) / 1e3, dist, "cuda")
     return sec, (clk.summary() if clk else None)
 
 
@@ -251,14 +261,74 @@ def run_e2e(torch, sidp, sv, U, stream, args, dist, world, nodes):
         sidp.sidp_download_state(sv.ctx, 0, host_out.data_ptr())
     ev1.record(stream)
     ev1.synchronize()
-    e_sec = ev0.elapsed_time(ev1) / 1e3
-    if dist:
-        t = torch.tensor([e_sec], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_sec = float(t.item())
-    return {"value": world * nodes * 3 * e_steps / e_sec, "unit": UNIT,
+    e_sec = max_over_ranks(torch, ev0.elapsed_time(ev1) / 1e3, dist, "cuda")
+    return {"value": whole_job_rate(nodes * 3 * e_steps, world, e_sec), "unit": UNIT,
             "h2d_bytes_per_step": int(host_in.numel() * 4), "d2h_bytes_per_step": int(host_out.numel() * 4),
             "steps": e_steps}
+
+
+def run_batched(torch, sidp, stream, steps, warmup, seed=0, count=512):
+    """Batched workload: `count` independent Euler problems, elements per side from {8,16,32,64}
+    and p from {2..7} (seeded), seeded four-quadrant data, mixed precision, outflow sides."""
+    from paper_2004_08503_gb300 import inputs
+    shapes = inputs.batch_shapes(seed, count)
+    cfgs = [sidp.make_config(law="euler", p=p, nx=nel, ny=nel, precision="mixed", bc=("outflow",) * 4)
+            for nel, p in shapes]
+    b = sidp.sidp_batch_create(cfgs, stream)
+    for i in range(count):
+        x, y = sidp.sidp_batch_node_coords(b, i)
+        sidp.sidp_batch_set_state(b, i, inputs.four_quadrant(x, y, seed * 100003 + i))
+    sidp.sidp_batch_set_stats(b, False)
+    nodes = sidp.sidp_batch_total_nodes(b)
+    sidp.sidp_batch_step(b, warmup)
+    sidp.sidp_batch_synchronize(b)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sidp.sidp_batch_step(b, steps)
+    e1.record(stream)
+    e1.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    sidp.sidp_batch_set_stats(b, True)
+    sidp.sidp_batch_step(b, 2)
+    worst = {"rho_min": 1e300, "p_min": 1e300, "max_bound_violation": 0.0, "max_entropy_violation": 0.0}
+    for i in range(0, count, max(1, count // 32)):
+        d = sidp.sidp_batch_get_diag(b, i)
+        worst["rho_min"] = min(worst["rho_min"], d["rho_min"])
+        worst["p_min"] = min(worst["p_min"], d["p_min"])
+        worst["max_bound_violation"] = max(worst["max_bound_violation"], d["max_bound_violation"])
+        worst["max_entropy_violation"] = max(worst["max_entropy_violation"], d["max_entropy_violation"])
+    sidp.sidp_batch_destroy(b)
+    return {"value": nodes * 3 * steps / sec, "unit": UNIT, "instances": count, "nodes": nodes, "steps": steps,
+            "ms_per_step": 1e3 * sec / steps, "launches_per_step": "4 per (p, tile) group + 1",
+            "invariants_sampled": worst, "workload": f"{count} Euler instances, elements per side in {{8,16,32,64}}, "
+            f"p in {{2..7}} (seed {seed}), four-quadrant data, mixed precision, one CUDA graph per step"}
+
+
+def run_accuracy(sidp, stream, stages=200):
+    """Mixed (float32) against float64 after `stages` RK stages on the two mixed-precision
+    configurations (256x256 p=3 and 128x128 p=7, seeded four-quadrant data, outflow).  The float64
+    path is the one the parity tests hold to the FP64 oracle (1e-12 per step)."""
+    from paper_2004_08503_gb300 import inputs
+    out = []
+    for nel, p in ((256, 3), (128, 7)):
+        res = {}
+        for prec in ("fp64", "mixed"):
+            sv = sidp.Solver(stream=stream, law="euler", p=p, nx=nel, ny=nel, precision=prec, bc=("outflow",) * 4)
+            x, y = sv.node_coords()
+            sv.set_state(inputs.four_quadrant(x, y, 0))
+            sv.step(stages // 3)
+            res[prec] = (sv.get_state(0), sv.diag())
+            sv.close()
+        a, b = res["mixed"][0], res["fp64"][0]
+        w = np.abs(b).max(axis=1)
+        d = res["mixed"][1]
+        out.append({"config": f"{nel}x{nel} p={p}", "stages": 3 * (stages // 3),
+                    "linf_rel": (np.abs(a - b).max(axis=1) / w).tolist(),
+                    "l1_rel": (np.abs(a - b).mean(axis=1) / np.abs(b).mean(axis=1)).tolist(),
+                    "rho_min": d["rho_min"], "p_min": d["p_min"], "max_bound_violation": d["max_bound_violation"],
+                    "max_entropy_violation": d["max_entropy_violation"]})
+    return out
 
 
 def main():
@@ -273,6 +343,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the float64 leg (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--nel", type=int, default=NEL, help="elements per side (profiling runs only)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched leg")
+    ap.add_argument("--accuracy", action="store_true", help="also report mixed-vs-float64 errors (200 stages)")
     args = ap.parse_args()
     NEL = args.nel
     if args.impl == "reference":
@@ -303,7 +375,7 @@ def main():
     sv.set_stats(False)
     nodes = sv.N
     sec, clk = time_steps(torch, sv, stream, args.steps, args.warmup, dist, clocks_gpu=local)
-    value = world * nodes * 3 * args.steps / sec
+    value = whole_job_rate(nodes * 3 * args.steps, world, sec)
     # stage-kernel roofline: algorithmic bytes per launch = reads of u_in (and u^n in stages 2, 3)
     # plus the write of u_out, nc = 4 fields of s = 4 bytes per node
     kt = stage_kernel_times(torch, sv, stream, reps=20)
@@ -329,11 +401,16 @@ def main():
         sv64.set_state(U)
         sv64.set_stats(False)
         sec64, _ = time_steps(torch, sv64, stream, args.fp64_steps, 2, dist)
-        fp64_value = world * nodes * 3 * args.fp64_steps / sec64
+        fp64_value = whole_job_rate(nodes * 3 * args.fp64_steps, world, sec64)
         kt64 = stage_kernel_times(torch, sv64, stream, reps=2)
         sv64.close()
         fp64 = {"value": fp64_value, "unit": UNIT, "steps": args.fp64_steps,
                 "stage_ms": [1e3 * t for t in kt64], "speedup_mixed_over_fp64": value / fp64_value}
+
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(torch, sidp, stream, steps=max(10, args.steps // 4), warmup=2)
+    accuracy = run_accuracy(sidp, stream) if args.accuracy else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -350,7 +427,7 @@ def main():
                              "traffic": None, "kernel": "k_stage<3, LawEuler<float>, float>",
                              "stage_ms": [1e3 * t for t in kt], "peak_kind": peak_kind,
                              "whole_step_gbs": step_gbs, "whole_step_frac": step_gbs / hbm},
-                "fp64": fp64, "invariants": diag_stats,
+                "fp64": fp64, "batched": batched, "invariants": diag_stats, "accuracy": accuracy,
                 "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": 5 * args.steps}
         print(json.dumps(line), flush=True)

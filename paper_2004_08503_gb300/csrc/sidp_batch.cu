@@ -39,7 +39,7 @@ __global__ void k_batch_finalize(unsigned long long* bits, const double* cfl, do
 }
 
 struct Group {
-  int p = 0;
+  int p = 0;  // degree and tile shape shared by the group's tasks
   int tile = 0;
   int2* d_tasks = nullptr;
   int ntasks = 0;
@@ -221,18 +221,25 @@ sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int cou
   b->N.resize(count);
   b->off.resize(count);
   long long tot = 0;
-  std::map<int, std::vector<int2>> tasks;
+  // one tile shape per degree: the autotuned one when the tuner has run for this (law, p,
+  // precision), else the default (fitting the shape to each mesh to cut padding measured slower:
+  // more, smaller launches)
+  int ptile[kMaxP + 1];
+  for (int p = 1; p <= kMaxP; ++p) {
+    ptile[p] = tuned_tile(cfgs[0].law, p, cfgs[0].precision == SIDP_MIXED ? 1 : 0);
+    if (ptile[p] < 0) ptile[p] = 0;
+  }
+  std::map<std::pair<int, int>, std::vector<int2>> tasks;  // (p, tile) -> tasks
   for (int i = 0; i < count; ++i) {
     const sidp_config& c = cfgs[i];
     const int nn = (c.p + 1) * (c.p + 1);
     b->N[i] = (long long)c.nx * c.ny * nn;
     b->off[i] = tot;
     tot += b->nc * b->N[i];
-    int tile = tuned_tile(c.law, c.p, b->mixed ? 1 : 0);
-    if (tile < 0) tile = 0;
+    const int tile = ptile[c.p];
     const TileShape ts = kTiles[c.p][tile];
     const long long ntiles = (long long)((c.nx + ts.tx - 1) / ts.tx) * ((c.ny + ts.ty - 1) / ts.ty);
-    for (long long t = 0; t < ntiles; ++t) tasks[c.p].push_back(make_int2(i, (int)t));
+    for (long long t = 0; t < ntiles; ++t) tasks[{c.p, tile}].push_back(make_int2(i, (int)t));
   }
   b->total_vals = tot;
   cudaError_t e;
@@ -264,9 +271,8 @@ sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int cou
   if ((e = b->mixed ? build_tables<float>(b) : build_tables<double>(b)) != cudaSuccess) return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
   for (auto& kv : tasks) {
     Group g;
-    g.p = kv.first;
-    g.tile = tuned_tile(b->law, g.p, b->mixed ? 1 : 0);
-    if (g.tile < 0) g.tile = 0;
+    g.p = kv.first.first;
+    g.tile = kv.first.second;
     g.ntasks = (int)kv.second.size();
     if (cudaMalloc(&g.d_tasks, sizeof(int2) * g.ntasks) != cudaSuccess) return bail(SIDP_ERR_OOM, "task table allocation failed");
     b->groups.push_back(g);

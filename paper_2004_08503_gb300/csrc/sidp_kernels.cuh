@@ -32,8 +32,11 @@ namespace sidp {
 constexpr int kRootMaxIt = 60;
 
 template <typename T> struct Prec;
-template <> struct Prec<double> { static constexpr double root_tol = 1e-13; };
-template <> struct Prec<float> { static constexpr float root_tol = 2e-6f; };
+// root_tol: bracket width at which the entropy line search stops.  entropy_margin: the float32
+// path demands sigma >= K (1 + margin) so that evaluation error in float32 (a few ulp of rho e,
+// amplified where kinetic energy dominates) cannot leave the stored state below the bound.
+template <> struct Prec<double> { static constexpr double root_tol = 1e-13; static constexpr double entropy_margin = 0.0; };
+template <> struct Prec<float> { static constexpr float root_tol = 2e-6f; static constexpr float entropy_margin = 1e-6f; };
 
 template <typename T, int NC> struct alignas(NC == 4 ? 4 * sizeof(T) : sizeof(T)) Vec { T v[NC]; };
 
@@ -451,7 +454,8 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
       const T Rp = (Pp > T(0)) ? tmin(T(1), fdiv(Qp, Pp)) : T(1);
       const T Rm = (Pm < T(0)) ? tmin(T(1), fdiv(Qm, Pm)) : T(1);
       at = tmin(Rp, Rm);
-      if constexpr (LAW::kEntropy) at = entropy_limit<LAW>(uL, K, xp, xm, yp, ym, T(4) * dtm, at, lp, iters, caps);
+      if constexpr (LAW::kEntropy)
+        at = entropy_limit<LAW>(uL, K * (T(1) + Prec<T>::entropy_margin), xp, xm, yp, ym, T(4) * dtm, at, lp, iters, caps);
     }
     s.alpha[me] = at;
     if (I.dbg_lo) {

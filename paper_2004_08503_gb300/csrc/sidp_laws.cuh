@@ -109,18 +109,27 @@ struct LawEuler {
     const T lR = vR + R.a * psqrt(T(1) + lp.c_gp * tmax(ps * R.ip - T(1), T(0)));
     return tmax(fabs(lL), fabs(lR));
   }
+  // Internal energy rho e = rho E - |m|^2 / (2 rho).  Where kinetic energy dominates, the
+  // subtraction cancels; the float32 path therefore carries the rounding errors of |m|^2 and of
+  // the division (exact via fma) so that rho e keeps a relative error of a few ulp.
+  __device__ static T rhoe(const T* u) {
+    if constexpr (sizeof(T) == 8) {
+      return u[3] - T(0.5) * (u[1] * u[1] + u[2] * u[2]) / u[0];
+    } else {
+      const float a = u[1] * u[1], ea = fmaf(u[1], u[1], -a);
+      const float b = u[2] * u[2], eb = fmaf(u[2], u[2], -b);
+      const float s = a + b, bb = s - a, es = (a - (s - bb)) + (b - bb);
+      const float rinv = frcp(u[0]);
+      const float q = s * rinv;                                  // |m|^2 / rho, rounded
+      const float dq = (fmaf(-q, u[0], s) + (es + ea + eb)) * rinv;  // its correction
+      return (u[3] - 0.5f * q) - 0.5f * dq;
+    }
+  }
   // sigma = rho e rho^-gamma; s = log(sigma)/(gamma-1) (Sec. 4.3)
-  __device__ static T sigma(const T* u, const Aux& x, const LawParamsT<T>& lp) {
-    return pressure(u, x.rinv, lp) * lp.inv_gm1 * ppow(u[0], -lp.gamma);
-  }
-  __device__ static T sigma_of(const T* u, const LawParamsT<T>& lp) {
-    const T rhoe = u[3] - T(0.5) * fdiv(u[1] * u[1] + u[2] * u[2], u[0]);
-    return rhoe * ppow(u[0], -lp.gamma);
-  }
+  __device__ static T sigma(const T* u, const Aux&, const LawParamsT<T>& lp) { return rhoe(u) * ppow(u[0], -lp.gamma); }
+  __device__ static T sigma_of(const T* u, const LawParamsT<T>& lp) { return rhoe(u) * ppow(u[0], -lp.gamma); }
   // psi_K(u) = rho e - K rho^gamma and its gradient in conserved variables
-  __device__ static T psi(const T* u, T K, const LawParamsT<T>& lp) {
-    return u[3] - T(0.5) * fdiv(u[1] * u[1] + u[2] * u[2], u[0]) - K * ppow(u[0], lp.gamma);
-  }
+  __device__ static T psi(const T* u, T K, const LawParamsT<T>& lp) { return rhoe(u) - K * ppow(u[0], lp.gamma); }
   __device__ static T psi_grad_dot(const T* u, T K, const T* w, const LawParamsT<T>& lp) {
     const T rinv = frcp(u[0]);
     const T vx = u[1] * rinv, vy = u[2] * rinv;

@@ -1,0 +1,122 @@
+"""C-ABI behaviour on the GPU: error handling (host-side failures, no device faults), checkpoint /
+resume, statistics, and the mixed-precision form's invariants."""
+import numpy as np
+import pytest
+
+from oracle import laws, scheme
+from paper_2004_08503_gb300 import build, inputs, sidp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    sidp.load()
+
+
+def _euler(p=3, nel=8, precision="fp64", bc=("outflow",) * 4):
+    sv = sidp.Solver(law="euler", p=p, nx=nel, ny=nel, precision=precision, bc=bc)
+    x, y = sv.node_coords()
+    return sv, inputs.four_quadrant(x, y, 2)
+
+
+def test_invalid_states_are_rejected_on_the_host():
+    sv, U = _euler()
+    bad = U.copy()
+    bad[0, 5] = np.nan
+    with pytest.raises(sidp.SidpError) as e:
+        sv.set_state(bad)
+    assert e.value.status == 3  # SIDP_ERR_NONFINITE
+    bad = U.copy()
+    bad[0, 7] = -1.0
+    with pytest.raises(sidp.SidpError) as e:
+        sv.set_state(bad)
+    assert e.value.status == 4  # SIDP_ERR_BOUNDS
+    bad = U.copy()
+    bad[3, 9] = 0.0  # zero energy: negative pressure
+    with pytest.raises(sidp.SidpError) as e:
+        sv.set_state(bad)
+    assert e.value.status == 4
+
+
+def test_stage_order_and_arguments():
+    sv, U = _euler()
+    sv.set_state(U)
+    with pytest.raises(sidp.SidpError) as e:
+        sv.stage(2, 1e-4)
+    assert e.value.status == 6  # SIDP_ERR_STATE
+    with pytest.raises(sidp.SidpError):
+        sv.stage(1, float("nan"))
+    sv.stage(1, 1e-4)
+    with pytest.raises(sidp.SidpError) as e:
+        sv.step(1)  # a step in the middle of stages
+    assert e.value.status == 6
+    sv.stage(2, 1e-4)
+    sv.stage(3, 1e-4)
+    sv.step(1)
+
+
+def test_checkpoint_resume_is_bitwise():
+    """get_state / set_state round-trip: continuing from a checkpoint gives the same bits (FP64)."""
+    sv, U = _euler(p=4)
+    sv.set_state(U)
+    sv.step(3)
+    ck = sv.get_state(0)
+    sv.step(4)
+    a = sv.get_state(0)
+    sv2, _ = _euler(p=4)
+    sv2.set_state(ck)
+    sv2.step(4)
+    np.testing.assert_array_equal(a, sv2.get_state(0))
+
+
+def test_zero_wave_speed_gives_zero_dt_and_no_change():
+    sv = sidp.Solver(law="burgers", p=2, nx=3, ny=3)
+    sv.set_state(np.zeros((1, sv.N)))
+    assert sv.compute_dt() == 0.0
+    sv.step(2)
+    assert np.all(sv.get_state(0) == 0.0)
+
+
+def test_device_state_pointer_and_raw_transfer():
+    import torch
+    sv, U = _euler(precision="mixed")
+    sv.set_state(U)
+    ptr, dtype, stride = sidp.sidp_device_state(sv.ctx)
+    assert dtype == 1 and stride == sv.N and ptr
+    host = torch.from_numpy(U.astype(np.float32)).pin_memory()
+    out = torch.empty_like(host).pin_memory()
+    sidp.sidp_upload_state(sv.ctx, host.data_ptr())
+    sidp.sidp_download_state(sv.ctx, 0, out.data_ptr())
+    sv.synchronize()
+    np.testing.assert_array_equal(out.numpy(), host.numpy())
+
+
+@pytest.mark.parametrize("p,nel,kind", [(3, 32, "quad"), (7, 12, "quad"), (3, 48, "blast")])
+def test_mixed_precision_invariants_and_error(p, nel, kind):
+    """Mixed form: positive density and pressure, density bounds and the entropy minimum held to
+    1e-6 relative (measured in float64 on the stored state), and close to the FP64 form."""
+    res = {}
+    for prec in ("fp64", "mixed"):
+        sv = sidp.Solver(law="euler", p=p, nx=nel, ny=nel, precision=prec, bc=("outflow",) * 4)
+        x, y = sv.node_coords()
+        U = inputs.four_quadrant(x, y, 4) if kind == "quad" else inputs.blast(x, y)
+        sv.set_state(U)
+        sv.step(30)
+        res[prec] = (sv.get_state(0), sv.diag())
+    d = res["mixed"][1]
+    assert d["rho_min"] > 0 and d["p_min"] > 0 and d["nonfinite"] == 0
+    assert d["max_bound_violation"] <= 1e-6
+    assert d["max_entropy_violation"] <= 1e-6
+    assert d["rootfind_cap_hits"] == 0
+    a, b = res["mixed"][0], res["fp64"][0]
+    l1 = np.abs(a - b).mean(axis=1) / np.abs(b).mean(axis=1)
+    assert np.all(l1 < 1e-4), l1
+
+
+def test_diag_mass_matches_oracle_quadrature():
+    sv, U = _euler(p=5, nel=6)
+    sv.set_state(U)
+    pb = scheme.Problem(laws.Euler(1.4), 5, 6, 6, bc=("outflow",) * 4)
+    np.testing.assert_allclose(sv.diag()["mass"], pb.total_mass(U.reshape(4, pb.Ne, -1)), rtol=1e-14)
