@@ -197,69 +197,96 @@ __device__ __forceinline__ void candidate(int c, const T* xp, const T* xm, const
   }
 }
 
+// Largest t in [0, tmax_] with u^L + t w admissible ({rho > 0, psi_K >= target}), given that t = 0 is
+// and t = tmax_ is not.  psi_K is concave along the line, so the admissible t form [0, t*].  Bracket
+// [tL feasible, tR infeasible]: chord from the feasible end (stays feasible by concavity), tangent
+// from the infeasible end (stays infeasible), each classified by an actual evaluation, and a
+// bisection step whenever the bracket did not halve.  At most kRootMaxIt iterations (the feasible
+// end is returned and the cap counted).
+template <class LAW, typename T>
+__device__ T entropy_root(const T* uL, const T* w, T K, T psi0, T target, T tmax_, const LawParamsT<T>& lp,
+                          int& iters, int& caps) {
+  T tL = T(0), fL = psi0 - target, tR = tmax_;
+  if (w[0] < T(0)) tR = tmin(tR, fdiv(-uL[0], w[0]));
+  int it = 0;
+#pragma unroll 1
+  for (; it < kRootMaxIt; ++it) {
+    const T width = tR - tL;
+    if (!(width > Prec<T>::root_tol)) break;
+    T uR[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) uR[f] = uL[f] + tR * w[f];
+    if (uR[0] > T(0)) {
+      const T fR = LAW::psi(uR, K, lp) - target;
+      if (fR >= T(0)) { tL = tR; fL = fR; break; }
+      const T tc = tL + fdiv(fL * (tR - tL), fL - fR);  // chord root: feasible side
+      if (tc > tL && tc < tR) {
+        T uc[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) uc[f] = uL[f] + tc * w[f];
+        const T fc = (uc[0] > T(0)) ? LAW::psi(uc, K, lp) - target : T(-1);
+        if (uc[0] > T(0) && fc >= T(0)) { tL = tc; fL = fc; } else { tR = tc; }
+      }
+      const T dR = LAW::psi_grad_dot(uR, K, w, lp);  // tangent root from the old tR: infeasible side
+      if (dR < T(0)) {
+        const T tn = tR - fdiv(fR, dR);
+        if (tn > tL && tn < tR) {
+          T un[4];
+#pragma unroll
+          for (int f = 0; f < 4; ++f) un[f] = uL[f] + tn * w[f];
+          const T fn = (un[0] > T(0)) ? LAW::psi(un, K, lp) - target : T(-1);
+          if (un[0] > T(0) && fn >= T(0)) { tL = tn; fL = fn; } else { tR = tn; }
+        }
+      }
+    }
+    if (tR - tL > T(0.5) * width) {  // guarantee at least a halving
+      const T tm = T(0.5) * (tL + tR);
+      T um[4];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) um[f] = uL[f] + tm * w[f];
+      const T fm = (um[0] > T(0)) ? LAW::psi(um, K, lp) - target : T(-1);
+      if (um[0] > T(0) && fm >= T(0)) { tL = tm; fL = fm; } else { tR = tm; }
+    }
+  }
+  if (it > iters) iters = it;
+  if (it >= kRootMaxIt) ++caps;
+  return tL;
+}
+
+// Euler: largest t in [0, tcap] such that every candidate u^L + t w_c, w_c = gamma_d dt/m (+-r-bar),
+// has rho > 0 and psi_K >= min(0, psi_K(u^L)).  Along each candidate the admissible set is an
+// interval [0, t*], so the candidates are taken in turn with the running cap; all four are first
+// tested at tcap in one pass, and only those that fail there need a root search.
 template <class LAW, typename T>
 __device__ T entropy_limit(const T* uL, T K, const T* xp, const T* xm, const T* yp, const T* ym, T sc, T tcap,
                            const LawParamsT<T>& lp, int& iters, int& caps) {
+  if (!(tcap > T(0))) return tcap;
   const T psi0 = LAW::psi(uL, K, lp);
   const T target = tmin(psi0, T(0));
+  unsigned fail = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    T ut[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const T v = (c == 0) ? xp[f] : (c == 1) ? -xm[f] : (c == 2) ? yp[f] : -ym[f];
+      ut[f] = uL[f] + tcap * (sc * v);
+    }
+    if (!(ut[0] > T(0) && LAW::psi(ut, K, lp) >= target)) fail |= 1u << c;
+  }
   T t = tcap;
 #pragma unroll 1
-  for (int c = 0; c < 4; ++c) {
-    if (!(t > T(0))) break;
+  while (fail) {
+    const int c = __ffs(fail) - 1;
+    fail &= fail - 1;
     T w[4];
     candidate<LAW>(c, xp, xm, yp, ym, sc, w);
     T ut[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) ut[f] = uL[f] + t * w[f];
-    if (ut[0] > T(0) && LAW::psi(ut, K, lp) >= target) continue;
-    T tL = T(0), fL = psi0 - target, tR = t;
-    if (w[0] < T(0)) {
-      const T t0 = -uL[0] / w[0];
-      if (t0 < tR) tR = t0;
-    }
-    int it = 0;
-#pragma unroll 1
-    for (; it < kRootMaxIt; ++it) {
-      const T width = tR - tL;
-      if (!(width > Prec<T>::root_tol)) break;
-      T uR[4];
-#pragma unroll
-      for (int f = 0; f < 4; ++f) uR[f] = uL[f] + tR * w[f];
-      if (uR[0] > T(0)) {
-        const T fR = LAW::psi(uR, K, lp) - target;
-        if (fR >= T(0)) { tL = tR; fL = fR; break; }
-        const T tc = tL + fL * (tR - tL) / (fL - fR);  // chord root: feasible side
-        if (tc > tL && tc < tR) {
-          T uc[4];
-#pragma unroll
-          for (int f = 0; f < 4; ++f) uc[f] = uL[f] + tc * w[f];
-          const T fc = (uc[0] > T(0)) ? LAW::psi(uc, K, lp) - target : T(-1);
-          if (uc[0] > T(0) && fc >= T(0)) { tL = tc; fL = fc; } else { tR = tc; }
-        }
-        const T dR = LAW::psi_grad_dot(uR, K, w, lp);  // tangent root from the old tR: infeasible side
-        if (dR < T(0)) {
-          const T tn = tR - fR / dR;
-          if (tn > tL && tn < tR) {
-            T un[4];
-#pragma unroll
-            for (int f = 0; f < 4; ++f) un[f] = uL[f] + tn * w[f];
-            const T fn = (un[0] > T(0)) ? LAW::psi(un, K, lp) - target : T(-1);
-            if (un[0] > T(0) && fn >= T(0)) { tL = tn; fL = fn; } else { tR = tn; }
-          }
-        }
-      }
-      if (tR - tL > T(0.5) * width) {  // guarantee at least a halving
-        const T tm = T(0.5) * (tL + tR);
-        T um[4];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) um[f] = uL[f] + tm * w[f];
-        const T fm = (um[0] > T(0)) ? LAW::psi(um, K, lp) - target : T(-1);
-        if (um[0] > T(0) && fm >= T(0)) { tL = tm; fL = fm; } else { tR = tm; }
-      }
-    }
-    if (it > iters) iters = it;
-    if (it >= kRootMaxIt) ++caps;
-    t = tL;
+    if (t < tcap && ut[0] > T(0) && LAW::psi(ut, K, lp) >= target) continue;  // admissible at the reduced cap
+    t = entropy_root<LAW>(uL, w, K, psi0, target, t, lp, iters, caps);
+    if (!(t > T(0))) break;
   }
   return t;
 }
@@ -369,7 +396,7 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
     const T wa = s.w[a], wb = s.w[b];
     const T hwa = h * wa, hwb = h * wb;
     m = h * h * wa * wb;
-    dtm = move ? dt / m : T(0);
+    dtm = move ? fdiv(dt, m) : T(0);
     T sx[NC], sy[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) { sx[q] = T(0); sy[q] = T(0); }
@@ -448,7 +475,7 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
       const T c1 = xp[0], c2 = -xm[0], c3 = yp[0], c4 = -ym[0];
       const T Pp = tmax(c1, T(0)) + tmax(c2, T(0)) + tmax(c3, T(0)) + tmax(c4, T(0));
       const T Pm = tmin(c1, T(0)) + tmin(c2, T(0)) + tmin(c3, T(0)) + tmin(c4, T(0));
-      const T mdt = m / dt;
+      const T mdt = fdiv(m, dt);
       const T Qp = tmax(T(0), mdt * (hi - uL[0]));
       const T Qm = tmin(T(0), mdt * (lo - uL[0]));
       const T Rp = (Pp > T(0)) ? tmin(T(1), fdiv(Qp, Pp)) : T(1);
@@ -488,7 +515,7 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
     if (act && move) {
       const T scale = tmax(fabs(lo), fabs(hi));
       v = tmax(lo - fe[0], fe[0] - hi);
-      v = (v > T(0)) ? v / (scale > T(0) ? scale : T(1)) : T(0);
+      v = (v > T(0)) ? fdiv(v, scale > T(0) ? scale : T(1)) : T(0);
       if constexpr (LAW::kEntropy) {
         const T sg = LAW::sigma_of(fe, lp);
         ev = tmax(T(0), T(1) - sg / K);
@@ -585,7 +612,7 @@ __device__ __forceinline__ void dt_body(TileSmem<P, TX, TY, LAW, T>& s, const In
     const T h = I.hT;
     const T wa = s.w[a], wb = s.w[b];
     const T sumd = T(0.5) * h * wa * (lamx[ix] + lamx[ix + 1]) + T(0.5) * h * wb * (lamy[iy] + lamy[iy + G::NX]);
-    if (sumd > T(0)) val = h * h * wa * wb / (T(2) * sumd);
+    if (sumd > T(0)) val = fdiv(h * h * wa * wb, T(2) * sumd);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) val = tmin(val, __shfl_xor_sync(0xffffffffu, val, o));

@@ -16,8 +16,11 @@
 
 namespace sidp {
 
-template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
-template <typename T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
+// min / max as single instructions (inputs are finite: states are validated on entry)
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
 
 // Precision-specific arithmetic.  float64: IEEE operations (parity with the float64 oracle).
 // float32 (the mixed path): hardware approximations (MUFU-based reciprocal, reciprocal square
