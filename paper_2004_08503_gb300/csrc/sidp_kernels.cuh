@@ -261,8 +261,8 @@ template <class LAW, typename T>
 __device__ T entropy_limit(const T* uL, T K, const T* xp, const T* xm, const T* yp, const T* ym, T sc, T tcap,
                            const LawParamsT<T>& lp, int& iters, int& caps) {
   if (!(tcap > T(0))) return tcap;
-  const T psi0 = LAW::psi(uL, K, lp);
-  const T target = tmin(psi0, T(0));
+  // target = min(0, psi_K(u^L)); the precise psi is needed only when u^L is not certainly inside
+  const T target = LAW::psi_certainly_ge(uL, K, T(0), lp) ? T(0) : tmin(LAW::psi(uL, K, lp), T(0));
   unsigned fail = 0;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
@@ -272,8 +272,11 @@ __device__ T entropy_limit(const T* uL, T K, const T* xp, const T* xm, const T* 
       const T v = (c == 0) ? xp[f] : (c == 1) ? -xm[f] : (c == 2) ? yp[f] : -ym[f];
       ut[f] = uL[f] + tcap * (sc * v);
     }
-    if (!(ut[0] > T(0) && LAW::psi(ut, K, lp) >= target)) fail |= 1u << c;
+    if (!(ut[0] > T(0) && (LAW::psi_certainly_ge(ut, K, target, lp) || LAW::psi(ut, K, lp) >= target)))
+      fail |= 1u << c;
   }
+  if (!fail) return tcap;
+  const T psi0 = LAW::psi(uL, K, lp);
   T t = tcap;
 #pragma unroll 1
   while (fail) {
@@ -381,6 +384,9 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
   __syncthreads();
 
   // ---------------- C: residuals, low-order state, bounds
+  // Every tile slot is computed (slots outside a ragged mesh edge hold valid ghost data); only
+  // global-memory traffic is restricted to active nodes.  slot is false only for padding threads.
+  const bool slot = (G::NT == G::THREADS) || (t < G::NT);
   const T dt = *I.dtT;
   const bool move = (dt > T(0)) && (dt < T(FLT_MAX));
   const T h = I.hT;
@@ -390,7 +396,7 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
   const long long N = I.N;
   T uL[NC], rx[NC], ry[NC];
   T lo = T(0), hi = T(0), K = T(0), m = T(1), dtm = T(0);
-  if (act) {
+  if (slot) {
     const V vu = s.u[me], vfx = s.fx[me], vfy = s.fy[me];
     const V fl = s.fbx[ix], fr = s.fbx[ix + 1], fd = s.fby[iy], fu = s.fby[iy + G::NX];
     const T wa = s.w[a], wb = s.w[b];
@@ -424,7 +430,7 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
       rx[q] = rHx - rLx;
       ry[q] = rHy - rLy;
     }
-    if (limiter != 2) {  // high-order target or low-order update only: done
+    if (limiter != 2 && act) {  // high-order target or low-order update only: done
 #pragma unroll
       for (int q = 0; q < NC; ++q)
         I.uout[q * N + g] = (I.c0 == T(0)) ? out[q] : I.c0 * I.u0[q * N + g] + I.c1 * out[q];
@@ -437,7 +443,7 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
   }
   if (limiter != 2) return;  // uniform across the CTA
   __syncthreads();  // all reads of F_x, F_y done
-  if (act) {
+  if (slot) {
     V vrx, vry;
 #pragma unroll
     for (int q = 0; q < NC; ++q) { vrx.v[q] = rx[q]; vry.v[q] = ry[q]; }
@@ -449,7 +455,7 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
   T xp[NC], xm[NC], yp[NC], ym[NC];
   T at = T(1);
   int iters = 0, caps = 0;
-  if (act) {
+  if (slot) {
 #pragma unroll
     for (int q = 0; q < NC; ++q) { xm[q] = T(0); ym[q] = T(0); }
     const int lx = le * NN + a * n, ly = le * NN + b;
@@ -485,7 +491,7 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
         at = entropy_limit<LAW>(uL, K * (T(1) + Prec<T>::entropy_margin), xp, xm, yp, ym, T(4) * dtm, at, lp, iters, caps);
     }
     s.alpha[me] = at;
-    if (I.dbg_lo) {
+    if (I.dbg_lo && act) {
       I.dbg_lo[g] = (double)lo;
       I.dbg_hi[g] = (double)hi;
       I.dbg_K[g] = (double)K;
@@ -500,15 +506,17 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
   __syncthreads();
   // ---------------- E: face coefficients and limited update
   T fe[NC];
-  if (act) {
+  if (slot) {
     const T axp = (b < P) ? tmin(at, s.alpha[me + 1]) : T(0);
     const T axm = (b > 0) ? tmin(at, s.alpha[me - 1]) : T(0);
     const T ayp = (a < P) ? tmin(at, s.alpha[me + n]) : T(0);
     const T aym = (a > 0) ? tmin(at, s.alpha[me - n]) : T(0);
 #pragma unroll
     for (int q = 0; q < NC; ++q) fe[q] = uL[q] + dtm * (axp * xp[q] - axm * xm[q] + ayp * yp[q] - aym * ym[q]);
+    if (act) {
 #pragma unroll
-    for (int q = 0; q < NC; ++q) I.uout[q * N + g] = (I.c0 == T(0)) ? fe[q] : I.c0 * u0[q] + I.c1 * fe[q];
+      for (int q = 0; q < NC; ++q) I.uout[q * N + g] = (I.c0 == T(0)) ? fe[q] : I.c0 * u0[q] + I.c1 * fe[q];
+    }
   }
   if (I.stats) {
     T v = T(0), ev = T(0);

@@ -133,6 +133,22 @@ struct LawEuler {
   __device__ static T sigma_of(const T* u, const LawParamsT<T>& lp) { return rhoe(u) * ppow(u[0], -lp.gamma); }
   // psi_K(u) = rho e - K rho^gamma and its gradient in conserved variables
   __device__ static T psi(const T* u, T K, const LawParamsT<T>& lp) { return rhoe(u) - K * ppow(u[0], lp.gamma); }
+  // True when psi_K(u) >= target is certain from a cheap float32 evaluation: the few roundings
+  // of rho E, |m|^2/(2 rho) and K rho^gamma stay below 1e-6 of their magnitudes (a bound with a
+  // wide margin over the ~10 ulp they can reach), so psi >= psi_fast - err.  False means
+  // "undecided" (the caller evaluates psi precisely).  The float64 path always evaluates psi.
+  __device__ static bool psi_certainly_ge(const T* u, T K, T target, const LawParamsT<T>& lp) {
+    if constexpr (sizeof(T) == 8) {
+      return false;
+    } else {
+      const float rinv = frcp(u[0]);
+      const float ke = 0.5f * fmaf(u[1], u[1], u[2] * u[2]) * rinv;
+      const float rg = K * ppow(u[0], lp.gamma);
+      const float pf = (u[3] - ke) - rg;
+      const float err = 1e-6f * (fabsf(u[3]) + ke + rg);
+      return pf - err >= target;
+    }
+  }
   __device__ static T psi_grad_dot(const T* u, T K, const T* w, const LawParamsT<T>& lp) {
     const T rinv = frcp(u[0]);
     const T vx = u[1] * rinv, vy = u[2] * rinv;
