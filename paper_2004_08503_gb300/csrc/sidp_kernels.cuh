@@ -442,41 +442,67 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
     if constexpr (LAW::kEntropy) K = tmin(tmin(bl.v[1], br.v[1]), tmin(bd.v[1], bu.v[1]));
   }
   if (limiter != 2) return;  // uniform across the CTA
-  __syncthreads();  // all reads of F_x, F_y done
-  if (slot) {
-    V vrx, vry;
-#pragma unroll
-    for (int q = 0; q < NC; ++q) { vrx.v[q] = rx[q]; vry.v[q] = ry[q]; }
-    s.fx[me] = vrx;
-    s.fy[me] = vry;
-  }
-  __syncthreads();
   // ---------------- D: subcell fluxes and nodal alpha-tilde
   T xp[NC], xm[NC], yp[NC], ym[NC];
   T at = T(1);
   int iters = 0, caps = 0;
-  if (slot) {
-#pragma unroll
-    for (int q = 0; q < NC; ++q) { xm[q] = T(0); ym[q] = T(0); }
-    const int lx = le * NN + a * n, ly = le * NN + b;
-#pragma unroll
-    for (int c = 0; c < P; ++c) {
-      if (c < b) {
-        const V r = s.fx[lx + c];
-#pragma unroll
-        for (int q = 0; q < NC; ++q) xm[q] += r.v[q];
-      }
-      if (c < a) {
-        const V r = s.fy[ly + c * n];
-#pragma unroll
-        for (int q = 0; q < NC; ++q) ym[q] += r.v[q];
-      }
-    }
+  if constexpr (32 % NN == 0) {
+    // An element's nodes sit in NN consecutive lanes of one warp: the line prefix sums
+    // r-bar = sum_{c <= b} r_c are warp scans (x lines: n consecutive lanes; y lines: stride n).
+    // r-bar at face b-1/2 is taken from the neighbouring lane's inclusive sum, so both nodes of a
+    // face use the same value.
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      xp[q] = (b == P) ? T(0) : xm[q] + rx[q];
-      yp[q] = (a == P) ? T(0) : ym[q] + ry[q];
+      T vx = rx[q], vy = ry[q];
+#pragma unroll
+      for (int d = 1; d < n; d <<= 1) {
+        const T ox = __shfl_up_sync(0xffffffffu, vx, d, n);
+        const T oy = __shfl_up_sync(0xffffffffu, vy, d * n, NN);
+        if (b >= d) vx += ox;
+        if (a >= d) vy += oy;
+      }
+      const T px = __shfl_up_sync(0xffffffffu, vx, 1, n);
+      const T py = __shfl_up_sync(0xffffffffu, vy, n, NN);
+      xm[q] = (b > 0) ? px : T(0);
+      ym[q] = (a > 0) ? py : T(0);
+      xp[q] = (b == P) ? T(0) : vx;
+      yp[q] = (a == P) ? T(0) : vy;
     }
+  } else {
+    __syncthreads();  // all reads of F_x, F_y done
+    if (slot) {
+      V vrx, vry;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) { vrx.v[q] = rx[q]; vry.v[q] = ry[q]; }
+      s.fx[me] = vrx;
+      s.fy[me] = vry;
+    }
+    __syncthreads();
+    if (slot) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) { xm[q] = T(0); ym[q] = T(0); }
+      const int lx = le * NN + a * n, ly = le * NN + b;
+#pragma unroll
+      for (int c = 0; c < P; ++c) {
+        if (c < b) {
+          const V r = s.fx[lx + c];
+#pragma unroll
+          for (int q = 0; q < NC; ++q) xm[q] += r.v[q];
+        }
+        if (c < a) {
+          const V r = s.fy[ly + c * n];
+#pragma unroll
+          for (int q = 0; q < NC; ++q) ym[q] += r.v[q];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        xp[q] = (b == P) ? T(0) : xm[q] + rx[q];
+        yp[q] = (a == P) ? T(0) : ym[q] + ry[q];
+      }
+    }
+  }
+  if (slot) {
     if (move) {
       const T c1 = xp[0], c2 = -xm[0], c3 = yp[0], c4 = -ym[0];
       const T Pp = tmax(c1, T(0)) + tmax(c2, T(0)) + tmax(c3, T(0)) + tmax(c4, T(0));
