@@ -35,9 +35,11 @@ class Problem:
     """Mesh, law, reference operators and boundary data of one simulation."""
 
     def __init__(self, law, p, nx, ny, domain=(0.0, 1.0, 0.0, 1.0), bc=("periodic",) * 4,
-                 ghost=None, cfl=0.5, limiter="subcell", sparsify=True):
+                 ghost=None, cfl=0.5, limiter="subcell", sparsify=True, smoothness=None):
         """sparsify=False swaps D-hat for the dense D in the low-order operator: the
-        unsparsified graph-viscosity method the paper compares against (Sec. 3.4)."""
+        unsparsified graph-viscosity method the paper compares against (Sec. 3.4).
+        smoothness: None, or dict(gmin, gmax[, s0, kappa]) enabling the subcell-resolution
+        smoothness indicator of Sec. 4.4 (relaxed bounds of the limited field)."""
         x0, x1, y0, y1 = map(float, domain)
         h = (x1 - x0) / nx
         if abs((y1 - y0) / ny - h) > 1e-14 * max(1.0, abs(h)):
@@ -51,6 +53,12 @@ class Problem:
                 raise ValueError(self.bc[s])
         self.ghost = ghost or {}
         self.cfl, self.limiter = float(cfl), limiter
+        self.smoothness = None
+        if smoothness is not None:
+            si = dict(smoothness)
+            si.setdefault("s0", np.log10(float(p) ** -4))  # Sec. 4.4: s0 ~ log10(p^-4)
+            si.setdefault("kappa", 1.0)
+            self.smoothness = si
         n = self.n
         self.xi, self.w = _gll.gll(self.p)
         D = _gll.diff_matrix(self.p)
@@ -307,6 +315,37 @@ class Problem:
         ym = rbar[1][:, :, :, 0:n].swapaxes(2, 3).reshape(nc, ne, n * n)
         return xp, xm, yp, ym
 
+    def smoothness_factor(self, U, elems):
+        """epsilon_K of Sec. 4.4 for each element, from the limited field of the stage input.
+
+        u_K is expanded in the tensor Legendre basis on the element (solving the nodal
+        interpolation V c = u exactly, V_ij = L_j(x_i) on [0,1]); u-hat_K drops every mode of
+        degree p in either variable; the norms are the exact L2 norms of the polynomials
+        (||L_k||^2 = 1/(2k+1) on [0,1]); s_K = log10(||u - u-hat||^2 / ||u||^2).
+        reading: the printed middle branch 1/2 - 1/2 sin(pi (s_K - s0)/(2 kappa)) is 1 at the lower
+        end and 0 at the upper end, contradicting the outer branches (0 below, 1 above); the
+        continuous form 1/2 + 1/2 sin(...) (Persson-Peraire) is used.
+        """
+        from numpy.polynomial import legendre as npleg
+        n, p = self.n, self.p
+        Lv = np.stack([npleg.legval(2.0 * self.xi - 1.0, np.eye(n)[k]) for k in range(n)], axis=1)  # V[i,k]
+        Vinv = np.linalg.inv(Lv)
+        u = U[0, elems].reshape(len(elems), n, n)  # [e, a, b]
+        c = np.einsum("ja,kb,eab->ejk", Vinv, Vinv, u)  # c[e, j (y degree), k (x degree)]
+        norms = 1.0 / (2.0 * np.arange(n) + 1.0)
+        wgt = norms[:, None] * norms[None, :]
+        tot = np.sum(c * c * wgt, axis=(1, 2))
+        mask = np.zeros((n, n), bool)
+        mask[p, :] = True
+        mask[:, p] = True
+        top = np.sum(c * c * wgt * mask, axis=(1, 2))
+        with np.errstate(divide="ignore", invalid="ignore"):
+            sK = np.where(tot > 0, np.log10(np.maximum(top, 1e-300) / tot), -np.inf)
+        s0, kap = self.smoothness["s0"], self.smoothness["kappa"]
+        eps = np.where(sK < s0 - kap, 0.0,
+                       np.where(sK > s0 + kap, 1.0, 0.5 + 0.5 * np.sin(np.pi * (sK - s0) / (2.0 * kap))))
+        return eps, sK
+
     def zalesak(self, uL, lo, hi, rbar, dt, field=0):
         """Nodal alpha-tilde from the sums of positive and negative parts of the adjacent
         subcell fluxes (Sec. 4.1.3), Zalesak-style.
@@ -379,6 +418,11 @@ class Problem:
             r = rH - rL
             rbar = self.subcell_fluxes(r)
             lo, hi, K = self.bounds(U, bars, elems)
+            if self.smoothness is not None:
+                # Eq. relaxed-bounds: eps_K u^min + (1 - eps_K) g^min (and likewise the maximum)
+                eps, _ = self.smoothness_factor(U, elems)
+                lo = eps[:, None] * lo + (1.0 - eps[:, None]) * self.smoothness["gmin"]
+                hi = eps[:, None] * hi + (1.0 - eps[:, None]) * self.smoothness["gmax"]
             at = self.zalesak(uL, lo, hi, rbar, dt)
             if self.law.name == "euler":
                 at = self.entropy_limit(uL, K, rbar, dt, at)
