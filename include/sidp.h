@@ -63,6 +63,11 @@ typedef struct {
   double gamma;     /* Euler ratio of specific heats, 1 < gamma <= 5/3 (wave-speed bound valid)  */
   double adv_beta[2]; /* advection velocity                                                      */
   int limiter;      /* sidp_limiter: HO target only, LO IDP only, or subcell FCT/convex limiting */
+  int smoothness;   /* 1: the subcell-resolution smoothness indicator (Sec. 4.4) relaxes the bounds
+                       of the limited field: eps_K u^min + (1 - eps_K) g^min, likewise the maximum   */
+  double si_s0;     /* s0; 0 selects log10(p^-4) (Sec. 4.4)                                      */
+  double si_kappa;  /* kappa; <= 0 selects 1                                                     */
+  double si_gmin, si_gmax; /* global bounds g^min <= g^max of the limited field (scalar or rho)   */
 } sidp_config;
 
 typedef struct {

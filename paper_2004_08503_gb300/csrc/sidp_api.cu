@@ -161,6 +161,13 @@ void fill_launch(const sidp_ctx* c, StageLaunch<T>& L) {
   for (int i = 0; i < c->n; ++i) L.tab.w[i] = T(c->w[i]);
   for (int i = 0; i < c->n * c->n; ++i) L.tab.D[i] = T(c->D[i]);
   L.lp = make_law_params<T>(c->cfg.gamma, c->cfg.adv_beta);
+  {
+    double Vinv[kMaxN * kMaxN], nrm[kMaxN];
+    modal_tables(c->cfg.p, Vinv, nrm);
+    for (int i = 0; i < c->n * c->n; ++i) L.tab.Vinv[i] = T(Vinv[i]);
+    for (int i = 0; i < c->n; ++i) L.tab.nrm[i] = T(nrm[i]);
+    L.si = make_smoothness<T>(c->cfg);
+  }
   L.limiter = c->cfg.limiter;
   if (c->debug) {
     L.inst.dbg_lo = c->d_dbg;
@@ -353,6 +360,11 @@ sidp_status validate_config(const sidp_config* cfg, std::string& msg) {
   if (cfg->law == SIDP_LAW_EULER2D && !(cfg->gamma > 1.0 && cfg->gamma <= 5.0 / 3.0)) { msg = "gamma must be in (1, 5/3]"; return SIDP_ERR_ARG; }
   if (cfg->limiter < 0 || cfg->limiter > 2) { msg = "unknown limiter"; return SIDP_ERR_ARG; }
   if (!std::isfinite(cfg->adv_beta[0]) || !std::isfinite(cfg->adv_beta[1])) { msg = "non-finite advection velocity"; return SIDP_ERR_ARG; }
+  if (cfg->smoothness != 0 && cfg->smoothness != 1) { msg = "smoothness must be 0 or 1"; return SIDP_ERR_ARG; }
+  if (cfg->smoothness && (!std::isfinite(cfg->si_gmin) || !std::isfinite(cfg->si_gmax) || cfg->si_gmin > cfg->si_gmax ||
+                          !std::isfinite(cfg->si_s0) || !std::isfinite(cfg->si_kappa))) {
+    msg = "smoothness indicator needs finite s0, kappa and g_min <= g_max"; return SIDP_ERR_ARG;
+  }
   return SIDP_OK;
 }
 }  // namespace sidp

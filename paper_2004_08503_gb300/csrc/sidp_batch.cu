@@ -163,6 +163,15 @@ cudaError_t launch_groups(sidp_batch* b, int k) {
     for (int i = 0; i < nn; ++i) bl.tab.w[i] = T(w[i]);
     for (int i = 0; i < nn * nn; ++i) bl.tab.D[i] = T(D[i]);
     bl.lp = make_law_params<T>(b->cfgs[0].gamma, b->cfgs[0].adv_beta);
+    {
+      double Vinv[kMaxN * kMaxN], nrm[kMaxN];
+      modal_tables(gr.p, Vinv, nrm);
+      for (int i = 0; i < nn * nn; ++i) bl.tab.Vinv[i] = T(Vinv[i]);
+      for (int i = 0; i < nn; ++i) bl.tab.nrm[i] = T(nrm[i]);
+      sidp_config cp = b->cfgs[0];
+      cp.p = gr.p;  // s0 defaults per degree
+      bl.si = make_smoothness<T>(cp);
+    }
     bl.limiter = b->limiter;
     bl.bits = b->d_bits;
     cudaError_t e;
@@ -200,8 +209,10 @@ sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int cou
     std::string msg;
     if (validate_config(&cfgs[i], msg) != SIDP_OK) return bfail(nullptr, SIDP_ERR_ARG, "instance " + std::to_string(i) + ": " + msg);
     if (cfgs[i].law != cfgs[0].law || cfgs[i].precision != cfgs[0].precision || cfgs[i].limiter != cfgs[0].limiter ||
-        cfgs[i].gamma != cfgs[0].gamma || cfgs[i].adv_beta[0] != cfgs[0].adv_beta[0] || cfgs[i].adv_beta[1] != cfgs[0].adv_beta[1])
-      return bfail(nullptr, SIDP_ERR_ARG, "all instances of a batch share law, precision, limiter and law parameters");
+        cfgs[i].gamma != cfgs[0].gamma || cfgs[i].adv_beta[0] != cfgs[0].adv_beta[0] || cfgs[i].adv_beta[1] != cfgs[0].adv_beta[1] ||
+        cfgs[i].smoothness != cfgs[0].smoothness || cfgs[i].si_s0 != cfgs[0].si_s0 || cfgs[i].si_kappa != cfgs[0].si_kappa ||
+        cfgs[i].si_gmin != cfgs[0].si_gmin || cfgs[i].si_gmax != cfgs[0].si_gmax)
+      return bfail(nullptr, SIDP_ERR_ARG, "all instances of a batch share law, precision, limiter, law and smoothness parameters");
     for (int s = 0; s < 4; ++s)
       if (cfgs[i].bc[s] == SIDP_BC_EXACT_STATE) return bfail(nullptr, SIDP_ERR_ARG, "exact-state sides are not supported in batches");
   }

@@ -1,5 +1,6 @@
 // Internal declarations shared by the host API and the kernel translation units.
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <cuda_runtime.h>
@@ -65,6 +66,15 @@ template <typename T>
 struct Tables {
   T w[kMaxN];             // Gauss-Lobatto weights on [0,1]
   T D[kMaxN * kMaxN];     // (D_1D)_{ij} = w_i phi_j'(xi_i), row-major
+  T Vinv[kMaxN * kMaxN];  // nodal -> Legendre modal coefficients, row k = degree
+  T nrm[kMaxN];           // squared L2 norm of L_k(2x-1) on [0,1]
+};
+
+// Smoothness indicator of Sec. 4.4 (off when on == 0): relaxed bounds of the limited field.
+template <typename T>
+struct SmoothnessT {
+  int on;
+  T s0, kappa, gmin, gmax;
 };
 
 // Per-stage statistics, reduced with atomics (non-negative floats stored as bit patterns).
@@ -109,6 +119,7 @@ struct BatchLaunch {
   Tables<T> tab;
   LawParamsT<T> lp;
   int limiter;
+  SmoothnessT<T> si;
   unsigned long long* bits;  // per-instance time-step accumulators (dt launches)
 };
 
@@ -118,7 +129,19 @@ struct StageLaunch {
   Tables<T> tab;
   LawParamsT<T> lp;
   int limiter;
+  SmoothnessT<T> si;
 };
+
+template <typename T>
+inline SmoothnessT<T> make_smoothness(const sidp_config& c) {
+  SmoothnessT<T> s{};
+  s.on = c.smoothness ? 1 : 0;
+  s.s0 = T(c.si_s0 != 0.0 ? c.si_s0 : -4.0 * std::log10((double)c.p));
+  s.kappa = T(c.si_kappa > 0.0 ? c.si_kappa : 1.0);
+  s.gmin = T(c.si_gmin);
+  s.gmax = T(c.si_gmax);
+  return s;
+}
 
 // Host-side helpers shared by the single-instance and batched entry points.
 int tuned_tile(int law, int p, int mixed);  // autotuned tile index, or -1 when not tuned yet
@@ -126,6 +149,7 @@ sidp_status validate_config(const sidp_config* cfg, std::string& msg);
 
 // Host tables (float64), computed once.
 void gll_tables(int p, double* xi, double* w, double* D);
+void modal_tables(int p, double* Vinv, double* nrm);
 
 }  // namespace sidp
 

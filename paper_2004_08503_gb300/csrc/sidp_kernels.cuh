@@ -73,6 +73,9 @@ struct TileSmem {
   T alpha[G::NT];
   T D[G::NN];
   T w[G::n];
+  T Vinv[G::NN];  // smoothness indicator: nodal -> modal transform
+  T nrm[G::n];
+  T eps[G::NE];   // smoothness factor epsilon_K per element of the tile
 };
 
 // Trace of the neighbouring element across `side` (0 W, 1 E, 2 S, 3 N) of element (ex, ey) at
@@ -134,8 +137,8 @@ __device__ __forceinline__ bool load_tile(S& s, const Instance<T>& I, const Tabl
   constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
   const int t = threadIdx.x;
   const int ex0 = tile_x * TX, ey0 = tile_y * TY;
-  if (t < NN) s.D[t] = tab.D[t];
-  if (t < n) s.w[t] = tab.w[t];
+  if (t < NN) { s.D[t] = tab.D[t]; s.Vinv[t] = tab.Vinv[t]; }
+  if (t < n) { s.w[t] = tab.w[t]; s.nrm[t] = tab.nrm[t]; }
   bool act = false;
   le = 0; a = 0; b = 0; g = 0;
   if (t < G::NT) {
@@ -347,7 +350,8 @@ __device__ __forceinline__ void face_eval_r(S& s, int k, int L, const Vec<T, LAW
 // The whole stage for one tile of one problem instance.
 template <int P, int TX, int TY, class LAW, typename T>
 __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const Instance<T>& I, const Tables<T>& tab,
-                                           const LawParamsT<T>& lp, int limiter, int tile_x, int tile_y) {
+                                           const LawParamsT<T>& lp, int limiter, const SmoothnessT<T>& si, int tile_x,
+                                           int tile_y) {
   using G = TileGeom<P, TX, TY>;
   using V = Vec<T, LAW::NC>;
   constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
@@ -382,6 +386,48 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
     }
   }
   __syncthreads();
+
+  // ---------------- smoothness indicator (Sec. 4.4), when enabled: epsilon_K per element from the
+  // Legendre coefficients of the limited field (separable nodal -> modal transform), s_K =
+  // log10(||u - u-hat||^2 / ||u||^2) with u-hat dropping the modes of degree p in either variable
+  const bool slot0 = (G::NT == G::THREADS) || (t < G::NT);
+  if (si.on && limiter == 2) {
+    const int base = le * NN;
+    if (slot0) {
+      T c1 = T(0);
+#pragma unroll
+      for (int c = 0; c < n; ++c) c1 += s.Vinv[b * n + c] * s.u[base + a * n + c].v[0];
+      s.alpha[t] = c1;
+    }
+    __syncthreads();
+    T wgt = T(0);
+    if (slot0) {
+      T cc = T(0);
+#pragma unroll
+      for (int c = 0; c < n; ++c) cc += s.Vinv[a * n + c] * s.alpha[base + c * n + b];
+      wgt = cc * cc * s.nrm[a] * s.nrm[b];
+    }
+    __syncthreads();
+    if (slot0) s.alpha[t] = wgt;
+    __syncthreads();
+    if (slot0 && a == 0 && b == 0) {
+      T tot = T(0), top = T(0);
+      for (int i = 0; i < NN; ++i) {
+        const T v = s.alpha[base + i];
+        tot += v;
+        if (i / n == P || i % n == P) top += v;
+      }
+      T e = T(0);
+      if (tot > T(0) && top > T(0)) {
+        const T sk = plog10(top / tot);
+        e = (sk < si.s0 - si.kappa) ? T(0)
+          : (sk > si.s0 + si.kappa) ? T(1)
+          : T(0.5) + T(0.5) * psin(T(3.14159265358979323846) * (sk - si.s0) / (T(2) * si.kappa));
+      }
+      s.eps[le] = e;
+    }
+    __syncthreads();
+  }
 
   // ---------------- C: residuals, low-order state, bounds
   // Every tile slot is computed (slots outside a ragged mesh edge hold valid ghost data); only
@@ -438,6 +484,11 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
     const auto bl = s.bbx[ix], br = s.bbx[ix + 1], bd = s.bby[iy], bu = s.bby[iy + G::NX];
     lo = tmin(tmin(vu.v[0], tmin(bl.v[0], br.v[0])), tmin(bd.v[0], bu.v[0]));
     hi = tmax(tmax(vu.v[0], tmax(bl.v[0], br.v[0])), tmax(bd.v[0], bu.v[0]));
+    if (si.on) {  // Eq. relaxed-bounds
+      const T e = s.eps[le];
+      lo = e * lo + (T(1) - e) * si.gmin;
+      hi = e * hi + (T(1) - e) * si.gmax;
+    }
     // K_i = min sigma over the node and its four neighbours = min over its four faces' minima
     if constexpr (LAW::kEntropy) K = tmin(tmin(bl.v[1], br.v[1]), tmin(bd.v[1], bu.v[1]));
   }
@@ -570,7 +621,7 @@ k_stage(const StageLaunch<T> A) {
   auto& s = *reinterpret_cast<TileSmem<P, TX, TY, LAW, T>*>(smem_raw);
   const int tiles_x = (A.inst.nx + TX - 1) / TX;
   const int tile_y = blockIdx.x / tiles_x, tile_x = blockIdx.x - tile_y * tiles_x;
-  stage_body<P, TX, TY, LAW, T>(s, A.inst, A.tab, A.lp, A.limiter, tile_x, tile_y);
+  stage_body<P, TX, TY, LAW, T>(s, A.inst, A.tab, A.lp, A.limiter, A.si, tile_x, tile_y);
 }
 
 // Copy the instance descriptor of this CTA's task into shared memory (all threads help).
@@ -595,7 +646,7 @@ k_stage_batch(const BatchLaunch<T> B) {
   load_instance(sI, B.insts + task.x);
   const int tiles_x = (sI.nx + TX - 1) / TX;
   const int tile_y = task.y / tiles_x, tile_x = task.y - tile_y * tiles_x;
-  stage_body<P, TX, TY, LAW, T>(s, sI, B.tab, B.lp, B.limiter, tile_x, tile_y);
+  stage_body<P, TX, TY, LAW, T>(s, sI, B.tab, B.lp, B.limiter, B.si, tile_x, tile_y);
 }
 
 // CFL bound of Eq. cfl-low per node, m_i / (2 sum_{j != i} d-hat_ij) with d-hat = (h w / 2) lambda on

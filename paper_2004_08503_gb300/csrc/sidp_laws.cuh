@@ -32,6 +32,10 @@ __device__ __forceinline__ float psqrt(float x) { return x * rsqrtf(x); }
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ double plog10(double x) { return log10(x); }
+__device__ __forceinline__ float plog10(float x) { return log10f(x); }
+__device__ __forceinline__ double psin(double x) { return sin(x); }
+__device__ __forceinline__ float psin(float x) { return sinf(x); }
 __device__ __forceinline__ float frcp(float x) { return __fdividef(1.0f, x); }
 // x^(2 gamma/(gamma-1)): seven multiplications' worth when the exponent is 7 (gamma = 1.4) in float32
 __device__ __forceinline__ double pstar_pow(double x, const LawParamsT<double>& lp) { return pow(x, lp.inv_e); }

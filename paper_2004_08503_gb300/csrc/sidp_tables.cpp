@@ -77,4 +77,34 @@ void gll_tables(int p, double* xi, double* w, double* D) {
   }
 }
 
+// Nodal-to-modal transform of the Gauss-Lobatto interpolant: coefficients c_k of the Legendre
+// polynomials L_k(2x-1) on [0,1].  The discrete Gram matrix sum_i w_i L_j(x_i) L_k(x_i) is diagonal
+// on the Gauss-Lobatto nodes (exact quadrature up to degree 2p-1 for j != k), so
+// Vinv[k][i] = w_i L_k(x_i) / gamma_k with gamma_k = sum_i w_i L_k(x_i)^2.  nrm[k] = 1/(2k+1) is
+// the exact squared norm of L_k(2x-1) on [0,1].
+void modal_tables(int p, double* Vinv, double* nrm) {
+  const int n = p + 1;
+  double xi[kMaxN], w[kMaxN], D[kMaxN * kMaxN];
+  gll_tables(p, xi, w, D);
+  double L[kMaxN][kMaxN];  // L[k][i] = L_k(2 xi_i - 1)
+  for (int i = 0; i < n; ++i) {
+    const double x = 2.0 * xi[i] - 1.0;
+    double lm1 = 1.0, l = x;
+    L[0][i] = 1.0;
+    if (p >= 1) L[1][i] = x;
+    for (int k = 2; k <= p; ++k) {
+      const double ln = ((2.0 * k - 1.0) * x * l - (k - 1.0) * lm1) / k;
+      lm1 = l;
+      l = ln;
+      L[k][i] = l;
+    }
+  }
+  for (int k = 0; k < n; ++k) {
+    double g = 0.0;
+    for (int i = 0; i < n; ++i) g += w[i] * L[k][i] * L[k][i];
+    for (int i = 0; i < n; ++i) Vinv[k * n + i] = w[i] * L[k][i] / g;
+    nrm[k] = 1.0 / (2.0 * k + 1.0);
+  }
+}
+
 }  // namespace sidp

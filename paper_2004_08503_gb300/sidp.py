@@ -28,7 +28,8 @@ class sidp_config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("x0", ctypes.c_double), ("x1", ctypes.c_double),
                 ("y0", ctypes.c_double), ("y1", ctypes.c_double), ("bc", ctypes.c_int * 4),
                 ("cfl", ctypes.c_double), ("gamma", ctypes.c_double), ("adv_beta", ctypes.c_double * 2),
-                ("limiter", ctypes.c_int)]
+                ("limiter", ctypes.c_int), ("smoothness", ctypes.c_int), ("si_s0", ctypes.c_double),
+                ("si_kappa", ctypes.c_double), ("si_gmin", ctypes.c_double), ("si_gmax", ctypes.c_double)]
 
 
 class sidp_diag(ctypes.Structure):
@@ -128,7 +129,8 @@ def _stream_handle(stream):
 
 
 def make_config(law="euler", p=3, nx=8, ny=8, precision="fp64", domain=(0.0, 1.0, 0.0, 1.0),
-                bc=("periodic",) * 4, cfl=0.5, gamma=1.4, beta=(1.0, 0.0), limiter="subcell"):
+                bc=("periodic",) * 4, cfl=0.5, gamma=1.4, beta=(1.0, 0.0), limiter="subcell", smoothness=None):
+    """smoothness: None, or dict(gmin, gmax[, s0, kappa]) for the Sec. 4.4 indicator."""
     c = sidp_config()
     c.law, c.p, c.nx, c.ny = LAWS[law], p, nx, ny
     c.precision = PRECISIONS[precision]
@@ -138,6 +140,11 @@ def make_config(law="euler", p=3, nx=8, ny=8, precision="fp64", domain=(0.0, 1.0
     c.cfl, c.gamma = cfl, gamma
     c.adv_beta[0], c.adv_beta[1] = beta
     c.limiter = LIMITERS[limiter]
+    if smoothness is not None:
+        c.smoothness = 1
+        c.si_gmin, c.si_gmax = smoothness["gmin"], smoothness["gmax"]
+        c.si_s0 = smoothness.get("s0", 0.0)
+        c.si_kappa = smoothness.get("kappa", 0.0)
     return c
 
 

@@ -31,7 +31,10 @@ def _state(law, x, y, seed):
 
 
 @pytest.mark.parametrize("law,precision", [("euler", "fp64"), ("euler", "mixed"), ("burgers", "fp64")])
-def test_batch_equals_instances_alone(law, precision):
+def test_batch_equals_instances_alone(law, precision, monkeypatch):
+    # the same tile shape on both sides: different shapes are different instantiations whose
+    # float roundings may differ in the last bit (checked to a tolerance below)
+    monkeypatch.setenv("SIDP_TILE", "0")
     cfgs = _cfgs(law, precision)
     b = sidp.sidp_batch_create([sidp.make_config(**c) for c in cfgs])
     states = []
@@ -55,6 +58,24 @@ def test_batch_equals_instances_alone(law, precision):
         sv.close()
     assert sidp.sidp_batch_total_nodes(b) == sum(c["nx"] * c["ny"] * (c["p"] + 1) ** 2 for c in cfgs)
     sidp.sidp_batch_destroy(b)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("mixed", 2e-6)])
+def test_tile_shapes_agree(precision, tol, monkeypatch):
+    """Every tile-shape candidate gives the same update up to rounding."""
+    res = []
+    for t in range(4):
+        monkeypatch.setenv("SIDP_TILE", str(t))
+        sv = sidp.Solver(law="euler", p=3, nx=13, ny=9, precision=precision, domain=(0.0, 1.0, 0.0, 9.0 / 13.0),
+                         bc=("outflow",) * 4)
+        x, y = sv.node_coords()
+        sv.set_state(inputs.four_quadrant(x, y, 7))
+        sv.step(3)
+        res.append(sv.get_state(0))
+        sv.close()
+    for r in res[1:]:
+        err = np.max(np.abs(r - res[0]), axis=1) / np.max(np.abs(res[0]), axis=1)
+        assert np.all(err <= tol), err
 
 
 def test_batch_rejects_mixed_laws():

@@ -281,3 +281,35 @@ def test_sampled_full_size_blast_fp64():
     exp = pb.fe_stage(U, dt, elems=sample)
     err = np.max(np.abs(got[:, sample] - exp), axis=(1, 2)) / np.max(np.abs(exp), axis=(1, 2))
     assert np.all(err <= TOL), err
+
+
+@pytest.mark.parametrize("lawname,kind,p", [("burgers", "pulse", 3), ("burgers", "pulse", 5), ("advection", "tanh", 4),
+                                            ("advection", "sine", 2)])
+def test_smoothness_indicator_stage_parity(lawname, kind, p):
+    """Sec. 4.4 relaxed bounds: the GPU's epsilon_K, relaxed bounds and limited stage equal the oracle's."""
+    nx, ny = 5, 3
+    domain = (0.0, 1.0, 0.0, 0.6)
+    law = laws.Burgers() if lawname == "burgers" else laws.Advection((1.0, 0.5))
+    pb0 = scheme.Problem(law, p, nx, ny, domain=domain)
+    X, Y = pb0.node_coords()
+    if kind == "pulse":
+        U = inputs.burgers_pulse(X, Y)
+    elif kind == "tanh":
+        U = np.tanh((X - 0.45) / 0.04)[None] + 0.0 * Y[None]
+    else:
+        U = inputs.sine_advection(X, Y)
+    si = dict(gmin=float(U.min()), gmax=float(U.max()))
+    pb = scheme.Problem(law, p, nx, ny, domain=domain, smoothness=si)
+    eps, sK = pb.smoothness_factor(U, np.arange(pb.Ne))
+    sv = sidp.Solver(law=lawname, p=p, nx=nx, ny=ny, domain=domain, beta=(1.0, 0.5), smoothness=si)
+    sv.set_state(U.reshape(1, -1))
+    sv.set_debug(True)
+    dt = pb.compute_dt(U)
+    sv.stage(1, dt)
+    exp, info = pb.fe_stage(U, dt, full=True)
+    assert np.all(rel(sv.get_state(1), exp) <= TOL), rel(sv.get_state(1), exp)
+    bd = sv.bounds()
+    np.testing.assert_allclose(bd["lo"], info["lo"].ravel(), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(bd["hi"], info["hi"].ravel(), rtol=1e-12, atol=1e-13)
+    if kind == "tanh":
+        assert np.any((eps > 0) & (eps < 1)) or (np.any(eps == 0) and np.any(eps == 1))
