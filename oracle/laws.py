@@ -29,6 +29,22 @@ class Advection:
         return np.abs(self.bx * nx + self.by * ny) * np.ones_like(uL[0])
 
 
+class AdvectionVar:
+    """Linear advection u_t + div(beta(x) u) = 0 with the divergence-free affine velocity
+    beta = (bx0 + bxy y, by0 + byx x) (Sec. 3.3; solid body rotation of Sec. 5.4 is
+    bx0 = pi, bxy = -2 pi, by0 = -pi, byx = 2 pi).  Each component is constant along its own
+    direction, so beta.n is continuous across every face of a Cartesian mesh."""
+
+    nc = 1
+    name = "advection_var"
+
+    def __init__(self, bx0=0.0, bxy=0.0, by0=0.0, byx=0.0):
+        self.bx0, self.bxy, self.by0, self.byx = float(bx0), float(bxy), float(by0), float(byx)
+
+    def velocity(self, X, Y):
+        return self.bx0 + self.bxy * Y, self.by0 + self.byx * X
+
+
 class Burgers:
     """2D Burgers f(u) = u^2/2 (1,1) (Sec. 5.5, velocity vector (1,1))."""
 

@@ -92,6 +92,11 @@ class Problem:
         self.fnodes = {"W": a * n, "E": a * n + (n - 1), "S": a, "N": (n - 1) * n + a}
         self.fopp = {"W": self.fnodes["E"], "E": self.fnodes["W"], "S": self.fnodes["N"], "N": self.fnodes["S"]}
         self.fw = {s: self.w.copy() for s in SIDES}  # face quadrature weight at each face node
+        # variable-velocity advection (Sec. 3.3): beta at every node
+        self.var = law.name == "advection_var"
+        if self.var:
+            X, Y = self.node_coords()
+            self.BX, self.BY = law.velocity(X, Y)
 
     # ------------------------------------------------------------------ geometry
     def node_coords(self):
@@ -150,7 +155,7 @@ class Problem:
         elems = np.arange(self.Ne) if elems is None else np.asarray(elems)
         Ue = U[:, elems]
         h = self.h
-        Fx, Fy = self.law.flux(Ue)
+        Fx, Fy = self._flux(Ue, elems)
         r = np.zeros((2,) + Ue.shape)
         r[0] = -(h * Fx) @ self.DX.T
         r[1] = -(h * Fy) @ self.DY.T
@@ -159,12 +164,33 @@ class Problem:
             idx = self.fnodes[s]
             um = Ue[:, :, idx]
             up = self.neighbor_trace(U, s, elems)
+            if self.var:
+                bn = self.BX[elems][:, idx] * nvec[0] + self.BY[elems][:, idx] * nvec[1]
+                fhat = 0.5 * bn * (um + up) - 0.5 * np.abs(bn) * (up - um)
+                G = np.zeros_like(Ue)
+                G[:, :, idx] = h * (fhat - bn * um)
+                r[_DIR[s]] -= G @ self.B[s].T
+                continue
             fhat, _ = self.lf_flux(um, up, nvec)
             Fm = self.law.flux(um)
             G = np.zeros_like(Ue)
             G[:, :, idx] = h * (fhat - (Fm[0] * nvec[0] + Fm[1] * nvec[1]))  # scaled normal carries h
             r[_DIR[s]] -= G @ self.B[s].T
         return r
+
+    def _flux(self, Ue, elems):
+        """F at the nodes of `elems`; beta(x_i) u_i for variable-velocity advection."""
+        if self.var:
+            return self.BX[elems][None] * Ue, self.BY[elems][None] * Ue
+        return self.law.flux(Ue)
+
+    def _pair_viscosity_var(self, elems):
+        """Sec. 3.3 modified coefficients: d-hat_ij = max(|c-hat_ij . beta_i|, |c-hat_ji . beta_j|)."""
+        bxi, byi = self.BX[elems][:, self.pI], self.BY[elems][:, self.pI]
+        bxj, byj = self.BX[elems][:, self.pJ], self.BY[elems][:, self.pJ]
+        a = np.abs(self.p_cij[0] * bxi + self.p_cij[1] * byi)
+        b = np.abs(self.p_cji[0] * bxj + self.p_cji[1] * byj)
+        return np.maximum(a, b)
 
     def _pair_viscosity(self, Ue):
         """d_ij of Eq. (dij) on the in-element pairs (pI, pJ): (len(elems), npairs).
@@ -192,13 +218,13 @@ class Problem:
         elems = np.arange(self.Ne) if elems is None else np.asarray(elems)
         Ue = U[:, elems]
         h = self.h
-        Fx, Fy = self.law.flux(Ue)
+        Fx, Fy = self._flux(Ue, elems)
         r = np.zeros((2,) + Ue.shape)
         # volume: sum_j c_ij . F_j (c_ij = h (D-hat_{1,R}^T, D-hat_{2,R}^T)_ij)
         r[0] = Fx @ self.cX.T
         r[1] = Fy @ self.cY.T
-        # in-element graph viscosity, Eq. (dij)
-        dij = self._pair_viscosity(Ue)
+        # in-element graph viscosity, Eq. (dij) (Sec. 3.3 coefficients for variable velocity)
+        dij = self._pair_viscosity_var(elems) if self.var else self._pair_viscosity(Ue)
         ui, uj = Ue[:, :, self.pI], Ue[:, :, self.pJ]
         visc = dij[None] * (uj - ui)
         for k in (0, 1):
@@ -208,9 +234,13 @@ class Problem:
             r[k] += acc
         bars = None
         if want_bars:
-            FI = (Fx[:, :, self.pI], Fy[:, :, self.pI])
-            FJ = (Fx[:, :, self.pJ], Fy[:, :, self.pJ])
-            cdF = self.p_cij[0] * (FJ[0] - FI[0]) + self.p_cij[1] * (FJ[1] - FI[1])
+            if self.var:  # Sec. 3.3 modified bar states: (c-hat_ij . beta_j) (u_j - u_i)
+                cb = self.p_cij[0] * self.BX[elems][:, self.pJ] + self.p_cij[1] * self.BY[elems][:, self.pJ]
+                cdF = cb[None] * (uj - ui)
+            else:
+                FI = (Fx[:, :, self.pI], Fy[:, :, self.pI])
+                FJ = (Fx[:, :, self.pJ], Fy[:, :, self.pJ])
+                cdF = self.p_cij[0] * (FJ[0] - FI[0]) + self.p_cij[1] * (FJ[1] - FI[1])
             dsafe = np.where(dij > 0, dij, 1.0)
             ubar = 0.5 * (ui + uj) + np.where(dij > 0, cdF / (2.0 * dsafe), 0.0)
             bars = {"pairs": ubar, "faces": {}}
@@ -221,12 +251,17 @@ class Problem:
             idx = self.fnodes[s]
             um = Ue[:, :, idx]
             up = self.neighbor_trace(U, s, elems)
-            Fm, Fp = self.law.flux(um), self.law.flux(up)
-            lam = self.law.lam(um, up, nvec[0], nvec[1])
             wn = h * self.fw[s]  # |wn_ij|
             bcoef = -0.5 * wn  # b_ii^(face) = b_ij = -1/2 wn (times the normal)
-            FnI = Fm[0] * nvec[0] + Fm[1] * nvec[1]
-            FnJ = Fp[0] * nvec[0] + Fp[1] * nvec[1]
+            if self.var:  # beta.n is continuous across the face (Sec. 3.3 velocity class)
+                bn = self.BX[elems][:, idx] * nvec[0] + self.BY[elems][:, idx] * nvec[1]
+                FnI, FnJ = bn * um, bn * up
+                lam = np.abs(bn)
+            else:
+                Fm, Fp = self.law.flux(um), self.law.flux(up)
+                lam = self.law.lam(um, up, nvec[0], nvec[1])
+                FnI = Fm[0] * nvec[0] + Fm[1] * nvec[1]
+                FnJ = Fp[0] * nvec[0] + Fp[1] * nvec[1]
             dhat = 0.5 * lam * wn
             contrib = bcoef * (FnI + FnJ) + dhat * (up - um)
             G = np.zeros_like(Ue)
@@ -258,7 +293,9 @@ class Problem:
         form Eq. (convex-combination) needs dt <= m_i / (2 sum_{j != i} d-hat_ij), used here.
         """
         tot = self.sum_dhat(U)
-        return self.cfl * float(np.min(self.mass[None, :] / (2.0 * tot)))
+        # a node with sum d-hat = 0 (a stagnation point of a velocity field) puts no limit on dt
+        with np.errstate(divide="ignore"):
+            return self.cfl * float(np.min(self.mass[None, :] / (2.0 * tot)))
 
     # ------------------------------------------------------------------ limiting
     def bounds(self, U, bars, elems):

@@ -18,6 +18,11 @@ Recipes (all float64):
                      p = rho T, swirl u_theta = r sqrt(g A/((g-1) s^2)) exp(-r^2/(4 s^2))
   sod_x              Sod data (rho,v,p) = (1,0,1) | (1/8,0,1/10) split at x = xs, y-invariant
   sine_advection     sin(2 pi x), y-invariant
+  solid_body         Sec. 5.4 rotation data on [0,1]^2: disks of radius 0.15, r normalised by it;
+                     bump (1 + cos(pi r))/4 at (0.25,0.5), cone 1 - r at (0.5,0.25), slotted
+                     cylinder at (0.5,0.75): 1 where |x - 0.5| >= 0.025 or y >= 0.85, else 0;
+                     zero outside the disks.  Rotation velocity (2 pi (1/2 - y), 2 pi (x - 1/2)).
+  smooth_bump        cos(pi r/2)^6 on a disk of radius r0 around (xc, yc) (C^5), zero outside
   batch_shapes       seeded (elements per side, p) pairs of a batch of independent problems
 """
 import numpy as np
@@ -93,6 +98,27 @@ def sod_x(x, y, xs=0.0, gamma=GAMMA):
     rho = np.where(left, 1.0, 0.125)
     p = np.where(left, 1.0, 0.1)
     return _cons(rho, 0.0 * x, 0.0 * x, p, gamma)
+
+
+SOLID_BODY_VELOCITY = (np.pi, -2.0 * np.pi, -np.pi, 2.0 * np.pi)  # (bx0, bxy, by0, byx)
+
+
+def solid_body(x, y):
+    r0 = 0.15
+    u = np.zeros_like(x, dtype=float)
+    r = np.hypot(x - 0.25, y - 0.5) / r0
+    u = np.where(r <= 1.0, 0.25 * (1.0 + np.cos(np.pi * np.minimum(r, 1.0))), u)
+    r = np.hypot(x - 0.5, y - 0.25) / r0
+    u = np.where(r <= 1.0, 1.0 - r, u)
+    r = np.hypot(x - 0.5, y - 0.75) / r0
+    cyl = np.where((np.abs(x - 0.5) >= 0.025) | (y >= 0.85), 1.0, 0.0)
+    u = np.where(r <= 1.0, cyl, u)
+    return u[None]
+
+
+def smooth_bump(x, y, xc=0.5, yc=0.3, r0=0.2):
+    r = np.minimum(np.hypot(x - xc, y - yc) / r0, 1.0)
+    return (np.cos(0.5 * np.pi * r) ** 6)[None]
 
 
 def constant_state(x, y, prim=(0.7, 0.3, -0.2, 0.9), gamma=GAMMA):
