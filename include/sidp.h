@@ -43,14 +43,22 @@ typedef enum {
   SIDP_ERR_OOM = 7           /* device allocation failed                                */
 } sidp_status;
 
-typedef enum { SIDP_LAW_BURGERS2D = 1, SIDP_LAW_EULER2D = 2, SIDP_LAW_ADVECTION2D = 3 } sidp_law;
+typedef enum {
+  SIDP_LAW_BURGERS2D = 1,
+  SIDP_LAW_EULER2D = 2,
+  SIDP_LAW_ADVECTION2D = 3,
+  SIDP_LAW_ADVECTION_VAR2D = 4
+} sidp_law;
 typedef enum { SIDP_FP64 = 0, SIDP_MIXED = 1 } sidp_precision;
 typedef enum { SIDP_BC_PERIODIC = 0, SIDP_BC_OUTFLOW = 1, SIDP_BC_EXACT_STATE = 2 } sidp_bc;
 typedef enum { SIDP_LIMITER_NONE = 0, SIDP_LIMITER_LOW_ORDER = 1, SIDP_LIMITER_SUBCELL = 2 } sidp_limiter;
 
 typedef struct {
   int law;          /* sidp_law.  Burgers: f(u) = u^2/2 (1,1) (Sec. 5.5); Euler: Eq. euler-flux;
-                       advection: f(u) = beta u with constant beta (Sec. 3.3)                     */
+                       advection: f(u) = beta u with constant beta (Sec. 3.3); variable-velocity
+                       advection: f(u) = beta(x) u with beta = (adv_beta[0] + adv_grad[0] y,
+                       adv_beta[1] + adv_grad[1] x), divergence-free (Sec. 3.3; the solid body
+                       rotation of Sec. 5.4 is adv_beta = (pi, -pi), adv_grad = (-2 pi, 2 pi))    */
   int p;            /* polynomial degree, 1..7                                                   */
   int nx, ny;       /* elements per direction, >= 1                                              */
   int precision;    /* SIDP_FP64: everything in float64.  SIDP_MIXED: float32 state and stage
@@ -68,6 +76,7 @@ typedef struct {
   double si_s0;     /* s0; 0 selects log10(p^-4) (Sec. 4.4)                                      */
   double si_kappa;  /* kappa; <= 0 selects 1                                                     */
   double si_gmin, si_gmax; /* global bounds g^min <= g^max of the limited field (scalar or rho)   */
+  double adv_grad[2]; /* variable-velocity advection: d beta_x / dy and d beta_y / dx            */
 } sidp_config;
 
 typedef struct {
@@ -135,7 +144,8 @@ sidp_status sidp_compute_dt(sidp_ctx* ctx, double* dt);
  * d_state: device pointer to the [nc][N] state in the storage type of cfg->precision (float64 or
  * float32), library node order; d_dt: device pointer to one double that receives
  * cfl * min_i m_i / (2 sum_{j != i} d-hat_ij) (0 when no wave moves).  Asynchronous on
- * cuda_stream.  Periodic and outflow sides only.  Scratch lives in a fixed 512 KiB device array
+ * cuda_stream.  Periodic and outflow sides only; Burgers, Euler and constant-velocity advection
+ * only (the variable-velocity law is SIDP_ERR_ARG here).  Scratch lives in a fixed 512 KiB device array
  * shared by all calls: at most 65536 * 256 = 16,777,216 nodes (else SIDP_ERR_ARG), and calls that
  * overlap on the GPU race.  The first call on a device looks the array up (cudaGetSymbolAddress);
  * make it before any stream capture. */

@@ -379,8 +379,9 @@ class Problem:
         with np.errstate(divide="ignore", invalid="ignore"):
             sK = np.where(tot > 0, np.log10(np.maximum(top, 1e-300) / tot), -np.inf)
         s0, kap = self.smoothness["s0"], self.smoothness["kappa"]
-        eps = np.where(sK < s0 - kap, 0.0,
-                       np.where(sK > s0 + kap, 1.0, 0.5 + 0.5 * np.sin(np.pi * (sK - s0) / (2.0 * kap))))
+        with np.errstate(invalid="ignore"):  # sin(-inf) on all-zero elements, discarded by the branch
+            eps = np.where(sK < s0 - kap, 0.0,
+                           np.where(sK > s0 + kap, 1.0, 0.5 + 0.5 * np.sin(np.pi * (sK - s0) / (2.0 * kap))))
         return eps, sK
 
     def zalesak(self, uL, lo, hi, rbar, dt, field=0):

@@ -156,11 +156,13 @@ void fill_launch(const sidp_ctx* c, StageLaunch<T>& L) {
   }
   L.inst.h = c->h;
   L.inst.hT = T(c->h);
+  L.inst.x0 = T(c->cfg.x0);
+  L.inst.y0 = T(c->cfg.y0);
   L.inst.dt = c->d_scal;
   L.inst.dtT = dt_ptr<T>(c);
-  for (int i = 0; i < c->n; ++i) L.tab.w[i] = T(c->w[i]);
+  for (int i = 0; i < c->n; ++i) { L.tab.w[i] = T(c->w[i]); L.tab.xi[i] = T(c->xi[i]); }
   for (int i = 0; i < c->n * c->n; ++i) L.tab.D[i] = T(c->D[i]);
-  L.lp = make_law_params<T>(c->cfg.gamma, c->cfg.adv_beta);
+  L.lp = make_law_params<T>(c->cfg.gamma, c->cfg.adv_beta, c->cfg.adv_grad);
   {
     double Vinv[kMaxN * kMaxN], nrm[kMaxN];
     modal_tables(c->cfg.p, Vinv, nrm);
@@ -198,6 +200,7 @@ cudaError_t dispatch(int law, int p, int tile, const StageLaunch<T>& a, unsigned
     case LAW_BURGERS: return launch_law<LAW_BURGERS, T>(p, tile, a, bits, s);
     case LAW_EULER: return launch_law<LAW_EULER, T>(p, tile, a, bits, s);
     case LAW_ADVECTION: return launch_law<LAW_ADVECTION, T>(p, tile, a, bits, s);
+    case LAW_ADVECTION_VAR: return launch_law<LAW_ADVECTION_VAR, T>(p, tile, a, bits, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -244,7 +247,7 @@ cudaError_t run_step(sidp_ctx* c) {
 // forces a candidate, SIDP_AUTOTUNE=0 keeps the default; SIDP_TUNE_FILE=<path> loads and stores
 // the table ("law p precision tile" lines).
 std::mutex g_tune_mu;
-int g_tune[4][kMaxP + 1][2];
+int g_tune[LAW_ADVECTION_VAR + 1][kMaxP + 1][2];
 bool g_tune_init = false;
 
 void tune_table_init() {
@@ -346,7 +349,8 @@ void drop_graph(sidp_ctx* c) {
 namespace sidp {
 sidp_status validate_config(const sidp_config* cfg, std::string& msg) {
   if (!cfg) { msg = "null config"; return SIDP_ERR_ARG; }
-  if (cfg->law != SIDP_LAW_BURGERS2D && cfg->law != SIDP_LAW_EULER2D && cfg->law != SIDP_LAW_ADVECTION2D) { msg = "unknown law"; return SIDP_ERR_ARG; }
+  if (cfg->law != SIDP_LAW_BURGERS2D && cfg->law != SIDP_LAW_EULER2D && cfg->law != SIDP_LAW_ADVECTION2D &&
+      cfg->law != SIDP_LAW_ADVECTION_VAR2D) { msg = "unknown law"; return SIDP_ERR_ARG; }
   if (cfg->p < 1 || cfg->p > kMaxP) { msg = "p must be in 1..7"; return SIDP_ERR_ARG; }
   if (cfg->nx < 1 || cfg->ny < 1) { msg = "nx, ny must be >= 1"; return SIDP_ERR_ARG; }
   if (cfg->precision != SIDP_FP64 && cfg->precision != SIDP_MIXED) { msg = "unknown precision"; return SIDP_ERR_ARG; }
@@ -360,6 +364,9 @@ sidp_status validate_config(const sidp_config* cfg, std::string& msg) {
   if (cfg->law == SIDP_LAW_EULER2D && !(cfg->gamma > 1.0 && cfg->gamma <= 5.0 / 3.0)) { msg = "gamma must be in (1, 5/3]"; return SIDP_ERR_ARG; }
   if (cfg->limiter < 0 || cfg->limiter > 2) { msg = "unknown limiter"; return SIDP_ERR_ARG; }
   if (!std::isfinite(cfg->adv_beta[0]) || !std::isfinite(cfg->adv_beta[1])) { msg = "non-finite advection velocity"; return SIDP_ERR_ARG; }
+  if (cfg->law == SIDP_LAW_ADVECTION_VAR2D && (!std::isfinite(cfg->adv_grad[0]) || !std::isfinite(cfg->adv_grad[1]))) {
+    msg = "non-finite advection velocity gradient"; return SIDP_ERR_ARG;
+  }
   if (cfg->smoothness != 0 && cfg->smoothness != 1) { msg = "smoothness must be 0 or 1"; return SIDP_ERR_ARG; }
   if (cfg->smoothness && (!std::isfinite(cfg->si_gmin) || !std::isfinite(cfg->si_gmax) || cfg->si_gmin > cfg->si_gmax ||
                           !std::isfinite(cfg->si_s0) || !std::isfinite(cfg->si_kappa))) {

@@ -106,6 +106,8 @@ cudaError_t build_tables(sidp_batch* b) {
     for (int s = 0; s < 4; ++s) I.bc[s] = c.bc[s];
     I.h = (c.x1 - c.x0) / c.nx;
     I.hT = T(I.h);
+    I.x0 = T(c.x0);
+    I.y0 = T(c.y0);
     I.dt = b->d_dt + i;
     I.dtT = dtT + i;
     I.stats = b->stats_on ? b->d_stats + i : nullptr;
@@ -160,9 +162,9 @@ cudaError_t launch_groups(sidp_batch* b, int k) {
     double xi[kMaxN], w[kMaxN], D[kMaxN * kMaxN];
     gll_tables(gr.p, xi, w, D);
     const int nn = gr.p + 1;
-    for (int i = 0; i < nn; ++i) bl.tab.w[i] = T(w[i]);
+    for (int i = 0; i < nn; ++i) { bl.tab.w[i] = T(w[i]); bl.tab.xi[i] = T(xi[i]); }
     for (int i = 0; i < nn * nn; ++i) bl.tab.D[i] = T(D[i]);
-    bl.lp = make_law_params<T>(b->cfgs[0].gamma, b->cfgs[0].adv_beta);
+    bl.lp = make_law_params<T>(b->cfgs[0].gamma, b->cfgs[0].adv_beta, b->cfgs[0].adv_grad);
     {
       double Vinv[kMaxN * kMaxN], nrm[kMaxN];
       modal_tables(gr.p, Vinv, nrm);
@@ -178,6 +180,7 @@ cudaError_t launch_groups(sidp_batch* b, int k) {
     switch (b->law) {
       case LAW_BURGERS: e = launch_batch_law<LAW_BURGERS, T>(gr.p, gr.tile, bl, k == 0, b->stream); break;
       case LAW_EULER: e = launch_batch_law<LAW_EULER, T>(gr.p, gr.tile, bl, k == 0, b->stream); break;
+      case LAW_ADVECTION_VAR: e = launch_batch_law<LAW_ADVECTION_VAR, T>(gr.p, gr.tile, bl, k == 0, b->stream); break;
       default: e = launch_batch_law<LAW_ADVECTION, T>(gr.p, gr.tile, bl, k == 0, b->stream); break;
     }
     if (e != cudaSuccess) return e;
@@ -210,6 +213,8 @@ sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int cou
     if (validate_config(&cfgs[i], msg) != SIDP_OK) return bfail(nullptr, SIDP_ERR_ARG, "instance " + std::to_string(i) + ": " + msg);
     if (cfgs[i].law != cfgs[0].law || cfgs[i].precision != cfgs[0].precision || cfgs[i].limiter != cfgs[0].limiter ||
         cfgs[i].gamma != cfgs[0].gamma || cfgs[i].adv_beta[0] != cfgs[0].adv_beta[0] || cfgs[i].adv_beta[1] != cfgs[0].adv_beta[1] ||
+        (cfgs[0].law == SIDP_LAW_ADVECTION_VAR2D &&
+         (cfgs[i].adv_grad[0] != cfgs[0].adv_grad[0] || cfgs[i].adv_grad[1] != cfgs[0].adv_grad[1])) ||
         cfgs[i].smoothness != cfgs[0].smoothness || cfgs[i].si_s0 != cfgs[0].si_s0 || cfgs[i].si_kappa != cfgs[0].si_kappa ||
         cfgs[i].si_gmin != cfgs[0].si_gmin || cfgs[i].si_gmax != cfgs[0].si_gmax)
       return bfail(nullptr, SIDP_ERR_ARG, "all instances of a batch share law, precision, limiter, law and smoothness parameters");

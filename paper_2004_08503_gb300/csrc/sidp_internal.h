@@ -11,7 +11,7 @@ namespace sidp {
 constexpr int kMaxP = 7;
 constexpr int kMaxN = kMaxP + 1;
 
-enum Law { LAW_BURGERS = 1, LAW_EULER = 2, LAW_ADVECTION = 3 };
+enum Law { LAW_BURGERS = 1, LAW_EULER = 2, LAW_ADVECTION = 3, LAW_ADVECTION_VAR = 4 };
 
 // Physical parameters of a law.
 // Law constants in the stage precision T, computed once on the host (float kernels must not
@@ -25,12 +25,13 @@ struct LawParamsT {
   T c_gp;       // (gamma + 1) / (2 gamma)
   T neg_e;      // -(gamma - 1) / (2 gamma)
   T inv_e;      // 2 gamma / (gamma - 1): exponent of the two-rarefaction pressure
-  T beta[2];    // advection velocity
+  T beta[2];    // advection velocity (variable-velocity law: its constant part)
+  T bxy, byx;   // variable-velocity law: beta = (beta[0] + bxy y, beta[1] + byx x)
   int pow7;     // inv_e == 7 (gamma = 1.4): the float path multiplies instead of calling pow
 };
 
 template <typename T>
-inline LawParamsT<T> make_law_params(double gamma, const double* beta) {
+inline LawParamsT<T> make_law_params(double gamma, const double* beta, const double* grad = nullptr) {
   LawParamsT<T> p{};
   const double g = gamma > 1.0 ? gamma : 1.4;
   p.gamma = T(g);
@@ -42,6 +43,8 @@ inline LawParamsT<T> make_law_params(double gamma, const double* beta) {
   p.inv_e = T(2.0 * g / (g - 1.0));
   p.beta[0] = T(beta[0]);
   p.beta[1] = T(beta[1]);
+  p.bxy = grad ? T(grad[0]) : T(0);
+  p.byx = grad ? T(grad[1]) : T(0);
   p.pow7 = (2.0 * g / (g - 1.0) > 7.0 - 1e-12 && 2.0 * g / (g - 1.0) < 7.0 + 1e-12) ? 1 : 0;
   return p;
 }
@@ -66,6 +69,7 @@ template <typename T>
 struct Tables {
   T w[kMaxN];             // Gauss-Lobatto weights on [0,1]
   T D[kMaxN * kMaxN];     // (D_1D)_{ij} = w_i phi_j'(xi_i), row-major
+  T xi[kMaxN];            // Gauss-Lobatto points on [0,1] (node positions)
   T Vinv[kMaxN * kMaxN];  // nodal -> Legendre modal coefficients, row k = degree
   T nrm[kMaxN];           // squared L2 norm of L_k(2x-1) on [0,1]
 };
@@ -100,6 +104,7 @@ struct Instance {
   int bc[4];
   double h;
   T hT;              // h in the stage precision
+  T x0, y0;          // lower-left corner of the domain (node positions)
   T c0, c1;          // RK combination uout = c0 u0 + c1 FE(uin)
   // debug outputs (null = off), per node
   double* dbg_lo;
@@ -173,6 +178,8 @@ SIDP_DECLARE(LAW_EULER, double)
 SIDP_DECLARE(LAW_EULER, float)
 SIDP_DECLARE(LAW_ADVECTION, double)
 SIDP_DECLARE(LAW_ADVECTION, float)
+SIDP_DECLARE(LAW_ADVECTION_VAR, double)
+SIDP_DECLARE(LAW_ADVECTION_VAR, float)
 #undef SIDP_DECLARE
 #undef SIDP_DECLARE_P
 

@@ -109,11 +109,15 @@ __device__ __forceinline__ void neighbor_trace(const Instance<T>& I, int side, i
 }
 
 // Node quantities of a slot: state, aux and -- unless LEAN (time-step kernel) -- fluxes and sigma.
+template <class L, class = void> struct HasPosition { static constexpr bool value = false; };
+template <class L> struct HasPosition<L, decltype(void(L::kPosition))> { static constexpr bool value = L::kPosition; };
+
 template <class LAW, bool LEAN, typename T, class S>
-__device__ __forceinline__ void fill_slot(S& s, int slot, const T* uu, const LawParamsT<T>& lp) {
+__device__ __forceinline__ void fill_slot(S& s, int slot, const T* uu, T x, T y, const LawParamsT<T>& lp) {
   constexpr int NC = LAW::NC;
   typename LAW::Aux ax;
-  LAW::aux(uu, ax, lp);
+  if constexpr (HasPosition<LAW>::value) LAW::aux_at(uu, x, y, ax, lp);
+  else LAW::aux(uu, ax, lp);
   Vec<T, NC> vu;
 #pragma unroll
   for (int f = 0; f < NC; ++f) vu.v[f] = uu[f];
@@ -138,6 +142,7 @@ __device__ __forceinline__ bool load_tile(S& s, const Instance<T>& I, const Tabl
   const int t = threadIdx.x;
   const int ex0 = tile_x * TX, ey0 = tile_y * TY;
   if (t < NN) { s.D[t] = tab.D[t]; s.Vinv[t] = tab.Vinv[t]; }
+  const T hh = I.hT;
   if (t < n) { s.w[t] = tab.w[t]; s.nrm[t] = tab.nrm[t]; }
   bool act = false;
   le = 0; a = 0; b = 0; g = 0;
@@ -147,6 +152,9 @@ __device__ __forceinline__ bool load_tile(S& s, const Instance<T>& I, const Tabl
     a = node / n;
     b = node - a * n;
     const int ex = ex0 + le % TX, ey = ey0 + le / TX;
+    // node position (velocity laws); slots outside the mesh take the boundary face's position
+    const T px = I.x0 + hh * (ex < I.nx ? T(ex) + tab.xi[b] : T(I.nx));
+    const T py = I.y0 + hh * (ey < I.ny ? T(ey) + tab.xi[a] : T(I.ny));
     T uu[NC];
     if (ex < I.nx && ey < I.ny) {
       act = true;
@@ -161,7 +169,7 @@ __device__ __forceinline__ bool load_tile(S& s, const Instance<T>& I, const Tabl
 #pragma unroll
       for (int f = 0; f < NC; ++f) uu[f] = I.uin[f * I.N + ((long long)ey0 * I.nx + ex0) * NN];
     }
-    fill_slot<LAW, LEAN>(s, t, uu, lp);
+    fill_slot<LAW, LEAN>(s, t, uu, px, py, lp);
   }
   for (int h = t; h < G::NH; h += G::THREADS) {
     T uu[NC];
@@ -173,13 +181,22 @@ __device__ __forceinline__ bool load_tile(S& s, const Instance<T>& I, const Tabl
     int ex, ey, along;
     if (side < 2) { ex = (side == 0) ? ex0 : ex0 + TX - 1; ey = ey0 + pos / n; along = pos % n; }
     else { ey = (side == 2) ? ey0 : ey0 + TY - 1; ex = ex0 + pos / n; along = pos % n; }
+    // halo position: the face node's (the normal velocity component is constant across the face)
+    T px, py;
+    if (side < 2) {
+      px = I.x0 + hh * T(side == 0 ? ex0 : ex0 + TX);
+      py = I.y0 + hh * (T(ey) + tab.xi[along]);
+    } else {
+      px = I.x0 + hh * (T(ex) + tab.xi[along]);
+      py = I.y0 + hh * T(side == 2 ? ey0 : ey0 + TY);
+    }
     if (ex < I.nx && ey < I.ny) {
       neighbor_trace<P, NC>(I, side, ex, ey, along, uu);
     } else {
 #pragma unroll
       for (int f = 0; f < NC; ++f) uu[f] = I.uin[f * I.N + ((long long)ey0 * I.nx + ex0) * NN];
     }
-    fill_slot<LAW, LEAN>(s, G::NT + h, uu, lp);
+    fill_slot<LAW, LEAN>(s, G::NT + h, uu, px, py, lp);
   }
   return act;
 }

@@ -58,6 +58,28 @@ struct LawAdvection {
   }
 };
 
+// Linear advection with the divergence-free velocity beta = (b0x + bxy y, b0y + byx x) (Sec. 3.3):
+// each component is constant along its own direction, so beta.n is continuous across every face,
+// the discrete divergence sum_j c-hat_ij . beta_j vanishes, and the modified coefficients
+// d-hat_ij = max(|c-hat_ij . beta_i|, |c-hat_ji . beta_j|) and bar states of Sec. 3.3 equal the
+// face flux forms below.  The node's velocity is the law's per-node quantity (from its position).
+template <typename T>
+struct LawAdvectionVar {
+  static constexpr int NC = 1;
+  static constexpr bool kEntropy = false;
+  static constexpr bool kPosition = true;
+  struct Aux { T b[2]; };
+  __device__ static void aux_at(const T*, T x, T y, Aux& a, const LawParamsT<T>& lp) {
+    a.b[0] = lp.beta[0] + lp.bxy * y;
+    a.b[1] = lp.beta[1] + lp.byx * x;
+  }
+  __device__ static void aux(const T*, Aux&, const LawParamsT<T>&) {}
+  __device__ static void flux(const T* u, const Aux& a, int k, T* f, const LawParamsT<T>&) { f[0] = a.b[k] * u[0]; }
+  __device__ static T lam(int k, const T*, const Aux& L, const T*, const Aux& R, const LawParamsT<T>&) {
+    return tmax(fabs(L.b[k]), fabs(R.b[k]));
+  }
+};
+
 template <typename T>
 struct LawBurgers {
   static constexpr int NC = 1;

@@ -16,7 +16,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libsidp.so")
 HEADER = os.path.join(os.path.dirname(_PKG), "include", "sidp.h")
 
-LAWS = {"burgers": 1, "euler": 2, "advection": 3}
+LAWS = {"burgers": 1, "euler": 2, "advection": 3, "advection_var": 4}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 BCS = {"periodic": 0, "outflow": 1, "exact": 2}
 LIMITERS = {"none": 0, "lo": 1, "subcell": 2}
@@ -29,7 +29,8 @@ class sidp_config(ctypes.Structure):
                 ("y0", ctypes.c_double), ("y1", ctypes.c_double), ("bc", ctypes.c_int * 4),
                 ("cfl", ctypes.c_double), ("gamma", ctypes.c_double), ("adv_beta", ctypes.c_double * 2),
                 ("limiter", ctypes.c_int), ("smoothness", ctypes.c_int), ("si_s0", ctypes.c_double),
-                ("si_kappa", ctypes.c_double), ("si_gmin", ctypes.c_double), ("si_gmax", ctypes.c_double)]
+                ("si_kappa", ctypes.c_double), ("si_gmin", ctypes.c_double), ("si_gmax", ctypes.c_double),
+                ("adv_grad", ctypes.c_double * 2)]
 
 
 class sidp_diag(ctypes.Structure):
@@ -129,8 +130,10 @@ def _stream_handle(stream):
 
 
 def make_config(law="euler", p=3, nx=8, ny=8, precision="fp64", domain=(0.0, 1.0, 0.0, 1.0),
-                bc=("periodic",) * 4, cfl=0.5, gamma=1.4, beta=(1.0, 0.0), limiter="subcell", smoothness=None):
-    """smoothness: None, or dict(gmin, gmax[, s0, kappa]) for the Sec. 4.4 indicator."""
+                bc=("periodic",) * 4, cfl=0.5, gamma=1.4, beta=(1.0, 0.0), limiter="subcell", smoothness=None,
+                grad=(0.0, 0.0)):
+    """smoothness: None, or dict(gmin, gmax[, s0, kappa]) for the Sec. 4.4 indicator.
+    law "advection_var": velocity (beta[0] + grad[0] y, beta[1] + grad[1] x)."""
     c = sidp_config()
     c.law, c.p, c.nx, c.ny = LAWS[law], p, nx, ny
     c.precision = PRECISIONS[precision]
@@ -139,6 +142,7 @@ def make_config(law="euler", p=3, nx=8, ny=8, precision="fp64", domain=(0.0, 1.0
         c.bc[i] = BCS[b]
     c.cfl, c.gamma = cfl, gamma
     c.adv_beta[0], c.adv_beta[1] = beta
+    c.adv_grad[0], c.adv_grad[1] = grad
     c.limiter = LIMITERS[limiter]
     if smoothness is not None:
         c.smoothness = 1

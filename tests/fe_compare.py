@@ -1,0 +1,75 @@
+"""Comparison of a forward-Euler limited stage with the oracle's where Zalesak's ratio is 0/0.
+
+Sec. 4.1.3 limits node i by alpha_i = min(R+, R-), R+- = min(1, Q+-/P+-).  Where the low-order
+state sits on its bound (Q = 0 up to rounding) and the antidiffusive fluxes of that sign are
+rounding noise (P = 0 up to rounding), R is a 0/0 that rounding decides anywhere in [0, 1]: one
+ulp of input moves it.  alpha_i also limits the node's fluxes of the other sign and, through the
+face minimum, its neighbours' - genuine fluxes - so two correct evaluations of the method may
+differ there by much more than rounding (the oracle against itself under one-ulp input noise
+shows it).  Both results are valid: every candidate stays inside the bounds.
+
+The check: nodes where that rounding moves the update by more than `tol` (a binding ratio whose
+P is small beside the node's other fluxes, or a rounding-level 0/0), together with their
+subcell-face neighbours, must lie inside the (relaxed) bounds and differ from the oracle by
+no more than the node's full antidiffusive correction dt/m sum |r-bar|; every other node must
+match to `tol` (normwise).
+"""
+import numpy as np
+
+
+def zalesak_ill_conditioned(pb, info, dt, tol=1e-12, kappa=64.0, tau=1e-10):
+    """Nodes (Ne, n*n) whose limited update the rounding of the Zalesak ratio moves by more
+    than `tol` (relative to max|u|).
+
+    Rounding perturbs Q = m/dt (bound - u^L) by about kappa ulp m/dt max|u|, so a ratio R = Q/P
+    that binds (R < 1) moves by about that over P; through alpha_i it moves every flux the node
+    governs, at most dt/m (P+ + P-).  The relative change is kappa ulp (P+ + P-)/P.  The extreme
+    case is the 0/0 - Q and P of one sign both below the noise floor tau m/dt max|u| while the
+    other sign carries genuine flux - where R may take any value in [0, 1]."""
+    ulp = np.finfo(float).eps
+    xp, xm, yp, ym = pb._node_face_fluxes(info["rbar"])
+    c = np.stack([xp[0], -xm[0], yp[0], -ym[0]])
+    Pp = np.sum(np.maximum(c, 0.0), axis=0)
+    Pm = -np.sum(np.minimum(c, 0.0), axis=0)
+    uL = info["uL"][0]
+    scale = max(np.max(np.abs(uL)), 1e-300)
+    m = pb.mass[None, :]
+    eta = tau * m / dt * scale
+    Qp = m / dt * np.maximum(info["hi"] - uL, 0.0)
+    Qm = m / dt * np.maximum(uL - info["lo"], 0.0)
+    tot = Pp + Pm
+    lim = tol / (kappa * ulp)
+    flag = np.zeros(Pp.shape, bool)
+    for P, Q, other in ((Pp, Qp, Pm), (Pm, Qm, Pp)):
+        binding = (P > 0) & (Q < P * (1 + 1e-8))
+        flag |= binding & (tot > lim * P)
+        flag |= (P <= eta) & (Q <= eta) & (other > eta)
+    return flag
+
+
+def spread_faces(flag, n):
+    A = flag.reshape(-1, n, n)
+    out = A.copy()
+    out[:, :, 1:] |= A[:, :, :-1]
+    out[:, :, :-1] |= A[:, :, 1:]
+    out[:, 1:, :] |= A[:, :-1, :]
+    out[:, :-1, :] |= A[:, 1:, :]
+    return out.reshape(flag.shape)
+
+
+def scalar_fe_check(pb, U, dt, got, tol=1e-12, tau=1e-10):
+    """Compare a scalar forward-Euler limited stage `got` (any shape of nc*N values) with the
+    oracle's from the same input U.  Returns the fraction of nodes checked by validity."""
+    exp, info = pb.fe_stage(U, dt, full=True)
+    got = np.asarray(got).reshape(exp.shape)
+    scale = max(np.max(np.abs(exp)), 1e-300)
+    bad = spread_faces(zalesak_ill_conditioned(pb, info, dt, tol=tol, tau=tau), pb.n)
+    err = np.abs(got - exp)[0] / scale
+    assert np.all(err[~bad] <= tol), np.max(err[~bad])
+    xp, xm, yp, ym = pb._node_face_fluxes(info["rbar"])
+    corr = dt / pb.mass * (np.abs(xp) + np.abs(xm) + np.abs(yp) + np.abs(ym))[0] / scale
+    assert np.all(err[bad] <= corr[bad] + tol)
+    g = got[0]
+    slack = tol * scale
+    assert np.all(g[bad] >= info["lo"][bad] - slack) and np.all(g[bad] <= info["hi"][bad] + slack)
+    return float(bad.mean())
