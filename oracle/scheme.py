@@ -411,14 +411,18 @@ class Problem:
         arithmetic; the min keeps roundoff in u^L from zeroing the coefficient).  psi_K is concave,
         so along a candidate the admissible t form an interval [0, t*]; t* is found by bisection.
         """
-        law = self.law
         xp, xm, yp, ym = self._node_face_fluxes(rbar)
         scale = 4.0 * dt / self.mass[None, :]
+        return self.entropy_line_search(uL, K, [scale[None] * v for v in (xp, -xm, yp, -ym)], amax, iters)
+
+    def entropy_line_search(self, uL, K, dirs, amax, iters=80):
+        """Largest t in [0, amax] with u^L + t w in the entropy set for every direction w of `dirs`
+        (bisection on each line; the admissible t of a line form an interval since psi_K is concave)."""
+        law = self.law
         psi0 = law.psi(uL, K)
         target = np.minimum(0.0, psi0)
         t_all = amax.copy()
-        for v in (xp, -xm, yp, -ym):
-            wdir = scale[None] * v
+        for wdir in dirs:
 
             def ok(t):
                 u = uL + t[None] * wdir
@@ -436,6 +440,29 @@ class Problem:
             t_all = np.minimum(t_all, t)
         return t_all
 
+    def elementwise_alpha(self, uL, lo, hi, K, rn, dt):
+        """Elementwise limiting (Sec. 4.1.2 linear, Sec. 4.2.1 convex constraints).
+
+        alpha-tilde_i is the largest value in [0,1] for which u^L_i + alpha (dt/m_i) r_i, with the
+        nodal antidiffusive flux r_i = r^H_i - r^L_i (summed over dimensions), stays inside the
+        bounds of the limited field (Zalesak with the single flux r_i: R+- = min(1, Q+-/P+-),
+        P+ = max(0, r_i), P- = min(0, r_i), 1 where P = 0) and, for Euler, in the entropy set
+        (Eq. convex-provisional-elementwise, one candidate, no gamma_d factor).  Every node of the
+        element then takes alpha_K = min of alpha-tilde over the element.  Returns (Ne, 1).
+        """
+        m = self.mass[None, :]
+        r0 = rn[0]
+        Pp = np.maximum(r0, 0.0)
+        Pm = np.minimum(r0, 0.0)
+        Qp = np.maximum(0.0, m / dt * (hi - uL[0]))
+        Qm = np.minimum(0.0, m / dt * (lo - uL[0]))
+        Rp = np.where(Pp > 0, np.minimum(1.0, Qp / np.where(Pp > 0, Pp, 1.0)), 1.0)
+        Rm = np.where(Pm < 0, np.minimum(1.0, Qm / np.where(Pm < 0, Pm, -1.0)), 1.0)
+        at = np.minimum(Rp, Rm)
+        if self.law.name == "euler":
+            at = self.entropy_line_search(uL, K, [(dt / m)[None] * rn], at)
+        return at.min(axis=1, keepdims=True), at
+
     # ------------------------------------------------------------------ one stage
     def fe_stage(self, U, dt, elems=None, limiter=None, full=False):
         """Forward-Euler limited update u^{FE}(U) of Eq. (subcell-fct) / (convex-fct)."""
@@ -452,6 +479,16 @@ class Problem:
             out = uH
         elif limiter == "lo":
             out = uL
+        elif limiter == "elementwise":
+            lo, hi, K = self.bounds(U, bars, elems)
+            if self.smoothness is not None:
+                eps, _ = self.smoothness_factor(U, elems)
+                lo = eps[:, None] * lo + (1.0 - eps[:, None]) * self.smoothness["gmin"]
+                hi = eps[:, None] * hi + (1.0 - eps[:, None]) * self.smoothness["gmax"]
+            rn = (rH[0] + rH[1]) - (rL[0] + rL[1])
+            aK, at = self.elementwise_alpha(uL, lo, hi, K, rn, dt)
+            out = uL + dt / m * aK[None] * rn
+            info.update({"lo": lo, "hi": hi, "K": K, "alpha_tilde": at, "alpha_K": aK[:, 0], "rn": rn})
         elif limiter == "subcell":
             r = rH - rL
             rbar = self.subcell_fluxes(r)
