@@ -51,7 +51,16 @@ typedef enum {
 } sidp_law;
 typedef enum { SIDP_FP64 = 0, SIDP_MIXED = 1 } sidp_precision;
 typedef enum { SIDP_BC_PERIODIC = 0, SIDP_BC_OUTFLOW = 1, SIDP_BC_EXACT_STATE = 2 } sidp_bc;
-typedef enum { SIDP_LIMITER_NONE = 0, SIDP_LIMITER_LOW_ORDER = 1, SIDP_LIMITER_SUBCELL = 2 } sidp_limiter;
+/* NONE: the high-order DG-SEM target (Eq. dg-strong); LOW_ORDER: the sparse IDP method
+ * (Eq. dg-idp); SUBCELL: subcell flux correction with Zalesak (Sec. 4.1.3) and, for Euler, convex
+ * entropy limiting (Sec. 4.3); ELEMENTWISE: one coefficient per element (Sec. 4.1.2, 4.2.1), the
+ * comparison mode of Sec. 4.1.4.  The smoothness indicator applies to SUBCELL and ELEMENTWISE. */
+typedef enum {
+  SIDP_LIMITER_NONE = 0,
+  SIDP_LIMITER_LOW_ORDER = 1,
+  SIDP_LIMITER_SUBCELL = 2,
+  SIDP_LIMITER_ELEMENTWISE = 3
+} sidp_limiter;
 
 typedef struct {
   int law;          /* sidp_law.  Burgers: f(u) = u^2/2 (1,1) (Sec. 5.5); Euler: Eq. euler-flux;
@@ -70,7 +79,7 @@ typedef struct {
   double cfl;       /* in (0, 1]; the paper uses 1/2 (Sec. 5)                                    */
   double gamma;     /* Euler ratio of specific heats, 1 < gamma <= 5/3 (wave-speed bound valid)  */
   double adv_beta[2]; /* advection velocity                                                      */
-  int limiter;      /* sidp_limiter: HO target only, LO IDP only, or subcell FCT/convex limiting */
+  int limiter;      /* sidp_limiter: HO target only, LO IDP only, subcell or elementwise limiting */
   int smoothness;   /* 1: the subcell-resolution smoothness indicator (Sec. 4.4) relaxes the bounds
                        of the limited field: eps_K u^min + (1 - eps_K) g^min, likewise the maximum   */
   double si_s0;     /* s0; 0 selects log10(p^-4) (Sec. 4.4)                                      */
@@ -86,8 +95,9 @@ typedef struct {
   double mass[4];               /* sum_i m_i u_i per field (Sec. 2.4 conservation)              */
   double umin[4], umax[4];      /* nodal min / max per field                                   */
   double rho_min, p_min;        /* Euler: min density and pressure (0 for scalar laws)          */
-  double max_bound_violation;   /* max over stages and nodes of the relative excess of the
-                                   limited field (scalar or rho) over its local bounds          */
+  double max_bound_violation;   /* max over stages and nodes of the excess of the limited field
+                                   (scalar or rho) over its local bounds, relative to
+                                   max(|bound|, max |field| at the last host set_state)         */
   double max_entropy_violation; /* Euler: max over stages of max(0, 1 - sigma(u_i)/K_i)          */
   int rootfind_max_iters;       /* largest iteration count of the entropy line search           */
   long long rootfind_cap_hits;  /* line searches stopped by the iteration cap                   */

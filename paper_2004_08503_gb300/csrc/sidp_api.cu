@@ -362,7 +362,7 @@ sidp_status validate_config(const sidp_config* cfg, std::string& msg) {
       (cfg->bc[2] == SIDP_BC_PERIODIC) != (cfg->bc[3] == SIDP_BC_PERIODIC)) { msg = "periodic sides must be paired"; return SIDP_ERR_ARG; }
   if (!(cfg->cfl > 0.0) || cfg->cfl > 1.0) { msg = "cfl must be in (0,1]"; return SIDP_ERR_ARG; }
   if (cfg->law == SIDP_LAW_EULER2D && !(cfg->gamma > 1.0 && cfg->gamma <= 5.0 / 3.0)) { msg = "gamma must be in (1, 5/3]"; return SIDP_ERR_ARG; }
-  if (cfg->limiter < 0 || cfg->limiter > 2) { msg = "unknown limiter"; return SIDP_ERR_ARG; }
+  if (cfg->limiter < 0 || cfg->limiter > 3) { msg = "unknown limiter"; return SIDP_ERR_ARG; }
   if (!std::isfinite(cfg->adv_beta[0]) || !std::isfinite(cfg->adv_beta[1])) { msg = "non-finite advection velocity"; return SIDP_ERR_ARG; }
   if (cfg->law == SIDP_LAW_ADVECTION_VAR2D && (!std::isfinite(cfg->adv_grad[0]) || !std::isfinite(cfg->adv_grad[1]))) {
     msg = "non-finite advection velocity gradient"; return SIDP_ERR_ARG;
@@ -516,6 +516,7 @@ sidp_status sidp_set_state(sidp_ctx* c, const double* u) {
   sidp_status st = c->mixed ? upload<float>(c, c->d_u[0], u, c->nc * N) : upload<double>(c, c->d_u[0], u, c->nc * N);
   if (st != SIDP_OK) return st;
   StageStats zs{};
+  for (long long i = 0; i < N; ++i) zs.field_scale = std::fmax(zs.field_scale, std::fabs(u[i]));
   CUDA_TRY(c, cudaMemcpy(c->d_stats, &zs, sizeof(zs), cudaMemcpyHostToDevice));
   c->stage_done = 0;
   return SIDP_OK;

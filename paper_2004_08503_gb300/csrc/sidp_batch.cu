@@ -14,6 +14,7 @@
 // little next to the per-stage work.
 #include <cfloat>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <string>
@@ -362,6 +363,10 @@ sidp_status sidp_batch_set_state(sidp_batch* b, int i, const double* u) {
       if (!(r > 0) || !(p > 0)) return bfail(b, SIDP_ERR_BOUNDS, "Euler state with rho <= 0 or p <= 0");
     }
   }
+  double scale = 0.0;
+  for (long long j = 0; j < N; ++j) scale = std::fmax(scale, std::fabs(u[j]));
+  BCUDA(b, cudaMemcpy(reinterpret_cast<char*>(b->d_stats + i) + offsetof(StageStats, field_scale), &scale, sizeof(double),
+                      cudaMemcpyHostToDevice));
   char* dst = static_cast<char*>(b->d_u[0]) + b->off[i] * b->esize;
   if (b->mixed) {
     std::vector<float> tmp(cnt);

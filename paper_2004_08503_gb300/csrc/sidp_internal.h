@@ -88,6 +88,7 @@ struct StageStats {
   unsigned int rootfind_max_iters;
   unsigned int pad;
   unsigned long long rootfind_cap_hits;
+  double field_scale;  // max |u| of the limited field at the last host set_state (violation floor)
 };
 
 // One problem instance as seen by the kernels.
@@ -188,6 +189,8 @@ SIDP_DECLARE(LAW_ADVECTION_VAR, float)
   template <>                                                                                          \
   cudaError_t launch_p<LAWID, TT, P>(int tile, const StageLaunch<TT>& a, unsigned long long* bits,     \
                                      cudaStream_t s) {                                                 \
+    if (a.limiter == 3 && !bits) /* elementwise limiting: its own kernel, default tile shape */       \
+      return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, true>(a, bits, s);       \
     switch (tile) {                                                                                    \
       case 0: return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT>(a, bits, s);     \
       case 1: return launch_tile<P, kTiles[P][1].tx, kTiles[P][1].ty, LAWTPL<TT>, TT>(a, bits, s);     \
@@ -198,6 +201,8 @@ SIDP_DECLARE(LAW_ADVECTION_VAR, float)
   }                                                                                                    \
   template <>                                                                                          \
   cudaError_t launch_batch_p<LAWID, TT, P>(int tile, const BatchLaunch<TT>& b, bool dt, cudaStream_t s) { \
+    if (b.limiter == 3 && !dt)                                                                         \
+      return launch_batch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, true>(b, dt, s);  \
     switch (tile) {                                                                                    \
       case 0: return launch_batch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT>(b, dt, s); \
       case 1: return launch_batch_tile<P, kTiles[P][1].tx, kTiles[P][1].ty, LAWTPL<TT>, TT>(b, dt, s); \

@@ -76,6 +76,7 @@ struct TileSmem {
   T Vinv[G::NN];  // smoothness indicator: nodal -> modal transform
   T nrm[G::n];
   T eps[G::NE];   // smoothness factor epsilon_K per element of the tile
+  T aK[G::NE];    // elementwise limiting: alpha_K per element of the tile
 };
 
 // Trace of the neighbouring element across `side` (0 W, 1 E, 2 S, 3 N) of element (ex, ey) at
@@ -322,6 +323,95 @@ __device__ __forceinline__ void warp_max_atomic(T v, unsigned long long* dst) {
   if ((threadIdx.x & 31) == 0 && d > 0.0) atomicMax(dst, (unsigned long long)__double_as_longlong(d));
 }
 
+// Euler: largest t in [0, tcap] with u^L + t w in {rho > 0, psi_K >= min(0, psi_K(u^L))} for the
+// single direction w (elementwise limiting, Eq. convex-provisional-elementwise).
+template <class LAW, typename T>
+__device__ T entropy_limit_dir(const T* uL, T K, const T* w, T tcap, const LawParamsT<T>& lp, int& iters, int& caps) {
+  if (!(tcap > T(0))) return tcap;
+  const T target = LAW::psi_certainly_ge(uL, K, T(0), lp) ? T(0) : tmin(LAW::psi(uL, K, lp), T(0));
+  T ut[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) ut[f] = uL[f] + tcap * w[f];
+  if (ut[0] > T(0) && (LAW::psi_certainly_ge(ut, K, target, lp) || LAW::psi(ut, K, lp) >= target)) return tcap;
+  return entropy_root<LAW>(uL, w, K, LAW::psi(uL, K, lp), target, tcap, lp, iters, caps);
+}
+
+// Elementwise limiting (Sec. 4.1.2 linear, Sec. 4.2.1 convex constraints): alpha-tilde_i is the
+// largest coefficient in [0,1] keeping u^L_i + alpha (dt/m_i) r_i, r_i = sum_k (r^H_ik - r^L_ik),
+// inside the bounds of the limited field (Zalesak with the single flux r_i) and, for Euler, in
+// the entropy set; every node of element K then takes alpha_K = min over K.  Writes u^FE with
+// the SSP-RK3 combination and the stage statistics.
+template <int P, int TX, int TY, class LAW, typename T, class S>
+__device__ __forceinline__ void elementwise_update(S& s, const Instance<T>& I, const LawParamsT<T>& lp, bool slot, bool act,
+                                                bool move, long long g, int le, int me, int a, int b, const T* uL,
+                                                const T* rx, const T* ry, T lo, T hi, T K, T m, T dt, T dtm) {
+  constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
+  const long long N = I.N;
+  T rn[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) rn[q] = rx[q] + ry[q];
+  T at = T(1);
+  int iters = 0, caps = 0;
+  if (slot) {
+    if (move) {
+      const T mdt = fdiv(m, dt);
+      const T Qp = tmax(T(0), mdt * (hi - uL[0]));
+      const T Qm = tmin(T(0), mdt * (lo - uL[0]));
+      const T Rp = (rn[0] > T(0)) ? tmin(T(1), fdiv(Qp, rn[0])) : T(1);
+      const T Rm = (rn[0] < T(0)) ? tmin(T(1), fdiv(Qm, rn[0])) : T(1);
+      at = tmin(Rp, Rm);
+      if constexpr (LAW::kEntropy) {
+        T w[NC];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) w[q] = dtm * rn[q];
+        at = entropy_limit_dir<LAW>(uL, K * (T(1) + Prec<T>::entropy_margin), w, at, lp, iters, caps);
+      }
+    }
+    s.alpha[me] = at;
+    if (I.dbg_lo && act) {
+      I.dbg_lo[g] = (double)lo;
+      I.dbg_hi[g] = (double)hi;
+      I.dbg_K[g] = (double)K;
+      I.dbg_alpha[g] = (double)at;
+    }
+  }
+  __syncthreads();
+  if (slot && a == 0 && b == 0) {
+    T mn = T(1);
+    for (int i = 0; i < NN; ++i) mn = tmin(mn, s.alpha[le * NN + i]);
+    s.aK[le] = mn;
+  }
+  __syncthreads();
+  T fe[NC];
+  if (slot) {
+    const T ak = s.aK[le];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) fe[q] = uL[q] + ak * dtm * rn[q];
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q)
+        I.uout[q * N + g] = (I.c0 == T(0)) ? fe[q] : I.c0 * I.u0[q * N + g] + I.c1 * fe[q];
+    }
+  }
+  if (I.stats) {
+    T v = T(0), ev = T(0);
+    if (act && move) {
+      const T scale = tmax(tmax(fabs(lo), fabs(hi)), T(I.stats->field_scale));
+      v = tmax(lo - fe[0], fe[0] - hi);
+      v = (v > T(0)) ? fdiv(v, scale > T(0) ? scale : T(1)) : T(0);
+      if constexpr (LAW::kEntropy) {
+        const T sg = LAW::sigma_of(fe, lp);
+        ev = tmax(T(0), T(1) - sg / K);
+        if (!(fe[0] > T(0))) ev = T(1);
+      }
+      if (caps) atomicAdd(&I.stats->rootfind_cap_hits, (unsigned long long)caps);
+      if (iters) atomicMax(&I.stats->rootfind_max_iters, (unsigned int)iters);
+    }
+    warp_max_atomic(v, &I.stats->max_bound_violation);
+    warp_max_atomic(ev, &I.stats->max_entropy_violation);
+  }
+}
+
 // Slots of the four neighbours of node slot t = (le, a, b) at tile position (row, col):
 // within the element, across an element face inside the tile, or in the halo.
 template <int P, int TX, int TY>
@@ -365,7 +455,9 @@ __device__ __forceinline__ void face_eval_r(S& s, int k, int L, const Vec<T, LAW
 }
 
 // The whole stage for one tile of one problem instance.
-template <int P, int TX, int TY, class LAW, typename T>
+// ELW selects elementwise limiting at compile time (its kernels are separate instantiations, so
+// the subcell kernels carry none of its code).
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false>
 __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const Instance<T>& I, const Tables<T>& tab,
                                            const LawParamsT<T>& lp, int limiter, const SmoothnessT<T>& si, int tile_x,
                                            int tile_y) {
@@ -408,7 +500,7 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
   // Legendre coefficients of the limited field (separable nodal -> modal transform), s_K =
   // log10(||u - u-hat||^2 / ||u||^2) with u-hat dropping the modes of degree p in either variable
   const bool slot0 = (G::NT == G::THREADS) || (t < G::NT);
-  if (si.on && limiter == 2) {
+  if (si.on && limiter >= 2) {
     const int base = le * NN;
     if (slot0) {
       T c1 = T(0);
@@ -493,7 +585,7 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
       rx[q] = rHx - rLx;
       ry[q] = rHy - rLy;
     }
-    if (limiter != 2 && act) {  // high-order target or low-order update only: done
+    if (limiter < 2 && act) {  // high-order target or low-order update only: done
 #pragma unroll
       for (int q = 0; q < NC; ++q)
         I.uout[q * N + g] = (I.c0 == T(0)) ? out[q] : I.c0 * I.u0[q * N + g] + I.c1 * out[q];
@@ -509,7 +601,11 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
     // K_i = min sigma over the node and its four neighbours = min over its four faces' minima
     if constexpr (LAW::kEntropy) K = tmin(tmin(bl.v[1], br.v[1]), tmin(bd.v[1], bu.v[1]));
   }
-  if (limiter != 2) return;  // uniform across the CTA
+  if (limiter < 2) return;  // uniform across the CTA
+  if constexpr (ELW) {      // elementwise limiting (Sec. 4.1.2, 4.2.1)
+    elementwise_update<P, TX, TY, LAW, T>(s, I, lp, slot, act, move, g, le, me, a, b, uL, rx, ry, lo, hi, K, m, dt, dtm);
+    return;
+  }
   // ---------------- D: subcell fluxes and nodal alpha-tilde
   T xp[NC], xm[NC], yp[NC], ym[NC];
   T at = T(1);
@@ -615,7 +711,9 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
   if (I.stats) {
     T v = T(0), ev = T(0);
     if (act && move) {
-      const T scale = tmax(fabs(lo), fabs(hi));
+      // relative to the local bound, floored at the field's magnitude (bounds that are zero up to
+      // rounding would otherwise turn rounding into large relative values)
+      const T scale = tmax(tmax(fabs(lo), fabs(hi)), T(I.stats->field_scale));
       v = tmax(lo - fe[0], fe[0] - hi);
       v = (v > T(0)) ? fdiv(v, scale > T(0) ? scale : T(1)) : T(0);
       if constexpr (LAW::kEntropy) {
@@ -631,14 +729,14 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
   }
 }
 
-template <int P, int TX, int TY, class LAW, typename T>
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false>
 __global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
 k_stage(const StageLaunch<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto& s = *reinterpret_cast<TileSmem<P, TX, TY, LAW, T>*>(smem_raw);
   const int tiles_x = (A.inst.nx + TX - 1) / TX;
   const int tile_y = blockIdx.x / tiles_x, tile_x = blockIdx.x - tile_y * tiles_x;
-  stage_body<P, TX, TY, LAW, T>(s, A.inst, A.tab, A.lp, A.limiter, A.si, tile_x, tile_y);
+  stage_body<P, TX, TY, LAW, T, ELW>(s, A.inst, A.tab, A.lp, A.limiter, A.si, tile_x, tile_y);
 }
 
 // Copy the instance descriptor of this CTA's task into shared memory (all threads help).
@@ -653,7 +751,7 @@ __device__ __forceinline__ void load_instance(Instance<T>& dst, const Instance<T
 
 // Batched stage: CTA blockIdx.x runs task (instance, tile) of the task table; all tasks of one
 // launch share P, the tile shape, law and precision.
-template <int P, int TX, int TY, class LAW, typename T>
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false>
 __global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
 k_stage_batch(const BatchLaunch<T> B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -663,7 +761,7 @@ k_stage_batch(const BatchLaunch<T> B) {
   load_instance(sI, B.insts + task.x);
   const int tiles_x = (sI.nx + TX - 1) / TX;
   const int tile_y = task.y / tiles_x, tile_x = task.y - tile_y * tiles_x;
-  stage_body<P, TX, TY, LAW, T>(s, sI, B.tab, B.lp, B.limiter, B.si, tile_x, tile_y);
+  stage_body<P, TX, TY, LAW, T, ELW>(s, sI, B.tab, B.lp, B.limiter, B.si, tile_x, tile_y);
 }
 
 // CFL bound of Eq. cfl-low per node, m_i / (2 sum_{j != i} d-hat_ij) with d-hat = (h w / 2) lambda on
@@ -752,13 +850,13 @@ k_dt_batch(const BatchLaunch<T> B) {
   dt_body<P, TX, TY, LAW, T>(s, sI, B.tab, B.lp, tile_x, tile_y, B.bits + task.x);
 }
 
-template <int P, int TX, int TY, class LAW, typename T>
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false>
 cudaError_t launch_tile(const StageLaunch<T>& a, unsigned long long* dt_bits, cudaStream_t s) {
   using G = TileGeom<P, TX, TY>;
   constexpr size_t smem = sizeof(TileSmem<P, TX, TY, LAW, T>);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(k_stage<P, TX, TY, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = cudaFuncSetAttribute(k_stage<P, TX, TY, LAW, T, ELW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(k_dt<P, TX, TY, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -767,17 +865,17 @@ cudaError_t launch_tile(const StageLaunch<T>& a, unsigned long long* dt_bits, cu
   const long long tiles = (long long)((a.inst.nx + TX - 1) / TX) * ((a.inst.ny + TY - 1) / TY);
   if (tiles <= 0) return cudaSuccess;
   if (dt_bits) k_dt<P, TX, TY, LAW, T><<<(unsigned)tiles, G::THREADS, smem, s>>>(a, dt_bits);
-  else k_stage<P, TX, TY, LAW, T><<<(unsigned)tiles, G::THREADS, smem, s>>>(a);
+  else k_stage<P, TX, TY, LAW, T, ELW><<<(unsigned)tiles, G::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int P, int TX, int TY, class LAW, typename T>
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false>
 cudaError_t launch_batch_tile(const BatchLaunch<T>& B, bool dt, cudaStream_t s) {
   using G = TileGeom<P, TX, TY>;
   constexpr size_t smem = sizeof(TileSmem<P, TX, TY, LAW, T>);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(k_stage_batch<P, TX, TY, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = cudaFuncSetAttribute(k_stage_batch<P, TX, TY, LAW, T, ELW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(k_dt_batch<P, TX, TY, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -785,7 +883,7 @@ cudaError_t launch_batch_tile(const BatchLaunch<T>& B, bool dt, cudaStream_t s) 
   }
   if (B.ntasks <= 0) return cudaSuccess;
   if (dt) k_dt_batch<P, TX, TY, LAW, T><<<(unsigned)B.ntasks, G::THREADS, smem, s>>>(B);
-  else k_stage_batch<P, TX, TY, LAW, T><<<(unsigned)B.ntasks, G::THREADS, smem, s>>>(B);
+  else k_stage_batch<P, TX, TY, LAW, T, ELW><<<(unsigned)B.ntasks, G::THREADS, smem, s>>>(B);
   return cudaGetLastError();
 }
 

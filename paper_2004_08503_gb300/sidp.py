@@ -19,7 +19,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "sidp.h")
 LAWS = {"burgers": 1, "euler": 2, "advection": 3, "advection_var": 4}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 BCS = {"periodic": 0, "outflow": 1, "exact": 2}
-LIMITERS = {"none": 0, "lo": 1, "subcell": 2}
+LIMITERS = {"none": 0, "lo": 1, "subcell": 2, "elementwise": 3}
 SIDES = {"W": 0, "E": 1, "S": 2, "N": 3}
 
 

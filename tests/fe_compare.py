@@ -73,3 +73,44 @@ def scalar_fe_check(pb, U, dt, got, tol=1e-12, tau=1e-10):
     slack = tol * scale
     assert np.all(g[bad] >= info["lo"][bad] - slack) and np.all(g[bad] <= info["hi"][bad] + slack)
     return float(bad.mean())
+
+
+def elementwise_fe_check(pb, U, dt, got, tol=1e-12, ulp=None, kappa=64.0, tau=1e-6, eta_rel=1e-10):
+    """Elementwise limiting (Sec. 4.1.2, 4.2.1): compare `got` with the oracle's stage from U.
+
+    alpha_K = min over the element of alpha-tilde_i.  Rounding moves alpha-tilde_i of a binding
+    Zalesak ratio Q/|r_i| by about kappa ulp (m/dt) max|u| / |r_i|; a rounding-level 0/0 (node on
+    its bound, noise-level r_i) may take any value in [0, 1]; for Euler a node whose psi_K(u^L) is
+    below tau rho e has an entropy root that rounding can move anywhere below its density value.
+    The interval of alpha_K follows; each node may then differ by (its width) |dt/m r_i| plus
+    tol max|u|, and must stay inside the bounds (and sigma >= K for Euler)."""
+    ulp = np.finfo(float).eps if ulp is None else ulp
+    exp, info = pb.fe_stage(U, dt, full=True)
+    got = np.asarray(got).reshape(exp.shape)
+    at, aK, rn, uL = info["alpha_tilde"], info["alpha_K"], info["rn"], info["uL"]
+    m = pb.mass[None, :]
+    scale = max(np.max(np.abs(exp)), 1e-300)
+    s0 = max(np.max(np.abs(uL[0])), 1e-300)
+    r0 = np.abs(rn[0])
+    delta = kappa * ulp * (m / dt) * s0 / np.where(r0 > 0, r0, np.inf)
+    eta = eta_rel * (m / dt) * s0
+    Qp = m / dt * np.maximum(info["hi"] - uL[0], 0.0)
+    Qm = m / dt * np.maximum(uL[0] - info["lo"], 0.0)
+    zero_zero = (r0 <= eta) & (np.minimum(Qp, Qm) <= eta)
+    lo_i = np.where(zero_zero, 0.0, at - delta)
+    hi_i = np.where(zero_zero, 1.0, at + delta)
+    if pb.law.name == "euler":
+        rhoe = pb.law.pressure(uL) / (pb.law.gamma - 1.0)
+        ill = pb.law.psi(uL, info["K"]) < tau * rhoe
+        lo_i = np.where(ill, 0.0, lo_i)
+        hi_i = np.where(ill, 1.0, hi_i)
+    width = np.clip(np.min(hi_i, axis=1), 0, 1) - np.clip(np.min(lo_i, axis=1), 0, 1)
+    w = dt / m[None] * np.abs(rn)
+    allowed = width[None, :, None] * w + tol * scale
+    err = np.abs(got - exp)
+    assert np.all(err <= allowed), np.max(err - allowed)
+    slack = 10 * tol * scale
+    assert np.all(got[0] >= info["lo"] - slack) and np.all(got[0] <= info["hi"] + slack)
+    if pb.law.name == "euler":
+        assert np.all(pb.law.sigma(got) >= info["K"] * (1 - 10 * tol))
+    return float(np.mean(width > 0))

@@ -21,16 +21,25 @@ def _cfgs(law, precision):
     for i, (nx, ny, p) in enumerate(shapes):
         h = 1.0 / max(nx, ny)
         bc = ("outflow",) * 4 if i % 2 else ("periodic",) * 4
-        cfgs.append(dict(law=law, p=p, nx=nx, ny=ny, precision=precision, domain=(0.0, nx * h, 0.0, ny * h), bc=bc,
-                         cfl=0.4 if i % 3 else 0.5))
+        c = dict(law=law, p=p, nx=nx, ny=ny, precision=precision, domain=(0.0, nx * h, 0.0, ny * h), bc=bc,
+                 cfl=0.4 if i % 3 else 0.5)
+        if law == "advection_var":
+            v = inputs.SOLID_BODY_VELOCITY
+            c.update(beta=(v[0], v[2]), grad=(v[1], v[3]))
+        cfgs.append(c)
     return cfgs
 
 
 def _state(law, x, y, seed):
-    return inputs.four_quadrant(x, y, seed) if law == "euler" else inputs.burgers_pulse(x, y)
+    if law == "euler":
+        return inputs.four_quadrant(x, y, seed)
+    if law == "advection_var":
+        return inputs.solid_body(x, y)
+    return inputs.burgers_pulse(x, y)
 
 
-@pytest.mark.parametrize("law,precision", [("euler", "fp64"), ("euler", "mixed"), ("burgers", "fp64")])
+@pytest.mark.parametrize("law,precision", [("euler", "fp64"), ("euler", "mixed"), ("burgers", "fp64"),
+                                           ("advection_var", "fp64"), ("advection_var", "mixed")])
 def test_batch_equals_instances_alone(law, precision, monkeypatch):
     # the same tile shape on both sides: different shapes are different instantiations whose
     # float roundings may differ in the last bit (checked to a tolerance below)

@@ -132,3 +132,26 @@ def test_square_waves_subcell_improves_with_p_elementwise_does_not():
     assert sub[7][0] < sub[3][0] < sub[1][0]
     assert elw[3][0] >= elw[1][0] and elw[7][0] >= elw[1][0]
     assert elw[7][0] > 2 * sub[7][0]
+
+
+@pytest.mark.parametrize("lawname,p", [("burgers", 3), ("euler", 3), ("euler", 5)])
+def test_elementwise_comparator_accepts_oracle_under_input_noise(lawname, p):
+    """The GPU comparator for elementwise limiting must accept the oracle against itself under
+    one-ulp input noise (the rounding-level 0/0 of Zalesak's ratio and ill-conditioned entropy
+    roots decide alpha_K of whole elements), and reject a planted error."""
+    import fe_compare
+    law = laws.Burgers() if lawname == "burgers" else laws.Euler(G)
+    pb = scheme.Problem(law, p, 4, 3, domain=(0, 1, 0, 0.75), limiter="elementwise", bc=("outflow",) * 4)
+    X, Y = pb.node_coords()
+    U = inputs.burgers_pulse(X, Y) if lawname == "burgers" else _euler_state(pb, p)
+    if lawname == "euler":
+        U, _ = scheme.Problem(law, p, 4, 3, domain=(0, 1, 0, 0.75), bc=("outflow",) * 4).ssp_rk3_step(U)
+    dt = pb.compute_dt(U)
+    for seed in range(6):
+        rng = np.random.default_rng(seed)
+        noisy = U * (1 + 2.2e-16 * rng.standard_normal(U.shape))
+        fe_compare.elementwise_fe_check(pb, U, dt, pb.fe_stage(noisy, dt))
+    bad = pb.fe_stage(U, dt).copy()
+    bad[0, 5, 3] += 1e-9 * np.max(np.abs(bad[0]))
+    with pytest.raises(AssertionError):
+        fe_compare.elementwise_fe_check(pb, U, dt, bad)
