@@ -49,8 +49,10 @@ class Problem:
         self.x0, self.y0, self.h = x0, y0, h
         self.bc = dict(zip(SIDES, bc))
         for s in SIDES:
-            if self.bc[s] not in ("periodic", "outflow", "exact"):
+            if self.bc[s] not in ("periodic", "outflow", "exact", "wall"):
                 raise ValueError(self.bc[s])
+            if self.bc[s] == "wall" and law.name != "euler":
+                raise ValueError("slip walls are defined for the Euler equations")
         self.ghost = ghost or {}
         self.cfl, self.limiter = float(cfl), limiter
         self.smoothness = None
@@ -113,7 +115,9 @@ class Problem:
         """u^+ at the face nodes of `side` for elements `elems`: (nc, len(elems), n).
 
         periodic: trace of the neighbouring element; outflow (reading: ghost = interior
-        trace, u^+ = u^-); exact: user ghost trace self.ghost[side] of shape (nc, n_side, n).
+        trace, u^+ = u^-); exact: user ghost trace self.ghost[side] of shape (nc, n_side, n);
+        wall (slip, Sec. 5.7): the mirror image of the interior trace, normal momentum negated, so
+        that the face flux carries no mass and the face is a plane of symmetry.
         """
         nx, ny = self.nx, self.ny
         ex, ey = elems % nx, elems // nx
@@ -133,6 +137,9 @@ class Problem:
         own = U[:, elems][:, :, self.fnodes[side]]
         if bc == "outflow":
             alt = own
+        elif bc == "wall":
+            alt = own.copy()
+            alt[1 if side in ("W", "E") else 2] *= -1.0
         else:
             pos = ey if side in ("W", "E") else ex
             alt = np.asarray(self.ghost[side])[:, pos, :]

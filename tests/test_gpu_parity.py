@@ -6,6 +6,7 @@ Bar: the FP64 GPU path matches the oracle within 1e-12 relative per field per st
 import numpy as np
 import pytest
 
+from fe_compare import euler_fe_check
 from oracle import laws, scheme
 from paper_2004_08503_gb300 import build, inputs, sidp
 
@@ -35,43 +36,6 @@ def rel(a, b):
     a = a.reshape(b.shape[0], -1)
     b = b.reshape(b.shape[0], -1)
     return np.max(np.abs(a - b), axis=1) / np.maximum(np.max(np.abs(b), axis=1), 1e-300)
-
-
-def euler_fe_check(pb, U, dt, got, tol=TOL, tau=1e-6):
-    """Compare a GPU forward-Euler stage with the oracle's on the entropy-limited Euler path.
-
-    The entropy coefficient of node i is the root t* of psi_K(u^L + t w) = min(0, psi_K(u^L)),
-    psi_K concave.  Concavity gives |psi'(t*)| >= psi_0 / t* with psi_0 = psi_K(u^L), so a
-    rounding-level change delta of psi moves the root by at most t* delta / psi_0: nodes with
-    psi_0 >= tau rho e have roots fixed to relative precision ~eps/tau.  Nodes closer than tau to
-    the bound (constant regions, isentropic flow) have roots that rounding-level differences of
-    the inputs can move far (the oracle itself moves there under 1e-16 input noise).  Those nodes
-    and their face neighbours (alpha on a subcell face is the min of the two nodes) are checked
-    for validity instead: density inside its bounds, sigma >= K_i, and a difference no larger than
-    the sum of the node's absolute subcell corrections dt/m sum |r-bar|.  All other nodes must
-    match to `tol` (normwise per field).  Returns the fraction of nodes checked by validity."""
-    exp, info = pb.fe_stage(U, dt, full=True)
-    n = pb.n
-    got = got.reshape(exp.shape)
-    scale = np.max(np.abs(exp), axis=(1, 2))
-    uL, K = info["uL"], info["K"]
-    rhoe = pb.law.pressure(uL) / (pb.law.gamma - 1.0)
-    ic = pb.law.psi(uL, K) < tau * rhoe
-    A = ic.reshape(-1, n, n)
-    spread = A.copy()
-    spread[:, :, 1:] |= A[:, :, :-1]
-    spread[:, :, :-1] |= A[:, :, 1:]
-    spread[:, 1:, :] |= A[:, :-1, :]
-    spread[:, :-1, :] |= A[:, 1:, :]
-    bad = spread.reshape(ic.shape)
-    err = np.abs(got - exp) / scale[:, None, None]
-    assert np.all(err[:, ~bad] <= tol), np.max(err[:, ~bad], axis=1)
-    xp, xm, yp, ym = pb._node_face_fluxes(info["rbar"])
-    corr = dt / pb.mass * (np.abs(xp) + np.abs(xm) + np.abs(yp) + np.abs(ym)) / scale[:, None, None]
-    assert np.all(err[:, bad] <= corr[:, bad] + tol)
-    assert np.all(got[0][bad] >= info["lo"][bad] * (1 - 1e-12)) and np.all(got[0][bad] <= info["hi"][bad] * (1 + 1e-12))
-    assert np.all(pb.law.sigma(got)[bad] >= K[bad] * (1 - 1e-12))
-    return float(bad.mean())
 
 
 def initial(pb, kind, seed=0):
