@@ -50,7 +50,12 @@ typedef enum {
   SIDP_LAW_ADVECTION_VAR2D = 4
 } sidp_law;
 typedef enum { SIDP_FP64 = 0, SIDP_MIXED = 1 } sidp_precision;
-typedef enum { SIDP_BC_PERIODIC = 0, SIDP_BC_OUTFLOW = 1, SIDP_BC_EXACT_STATE = 2 } sidp_bc;
+typedef enum {
+  SIDP_BC_PERIODIC = 0,
+  SIDP_BC_OUTFLOW = 1,
+  SIDP_BC_EXACT_STATE = 2,
+  SIDP_BC_SLIP_WALL = 3 /* Euler only: ghost = mirror image of the trace (Sec. 5.7 slip wall) */
+} sidp_bc;
 /* NONE: the high-order DG-SEM target (Eq. dg-strong); LOW_ORDER: the sparse IDP method
  * (Eq. dg-idp); SUBCELL: subcell flux correction with Zalesak (Sec. 4.1.3) and, for Euler, convex
  * entropy limiting (Sec. 4.3); ELEMENTWISE: one coefficient per element (Sec. 4.1.2, 4.2.1), the
@@ -75,7 +80,8 @@ typedef struct {
   double x0, x1, y0, y1;  /* domain; elements must be square                                     */
   int bc[4];        /* sidp_bc for the W, E, S, N sides.  Periodic must be paired (W with E,
                        S with N).  Outflow: ghost = interior trace.  Exact: ghost traces set by
-                       sidp_set_ghost_state                                                       */
+                       sidp_set_ghost_state.  Slip wall: the trace with its normal momentum
+                       negated (Euler)                                                            */
   double cfl;       /* in (0, 1]; the paper uses 1/2 (Sec. 5)                                    */
   double gamma;     /* Euler ratio of specific heats, 1 < gamma <= 5/3 (wave-speed bound valid)  */
   double adv_beta[2]; /* advection velocity                                                      */
@@ -86,6 +92,10 @@ typedef struct {
   double si_kappa;  /* kappa; <= 0 selects 1                                                     */
   double si_gmin, si_gmax; /* global bounds g^min <= g^max of the limited field (scalar or rho)   */
   double adv_grad[2]; /* variable-velocity advection: d beta_x / dy and d beta_y / dx            */
+  int unsparsified; /* 0: the sparse low-order operator of the paper (Eq. didp).  1: graph
+                       viscosity on the dense DG-SEM operator, the comparison of Sec. 3.4 (every
+                       pair of a line of an element coupled; bounds and time step follow).  Single
+                       contexts only (a batch rejects it)                                         */
 } sidp_config;
 
 typedef struct {

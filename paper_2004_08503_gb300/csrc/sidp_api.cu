@@ -171,6 +171,7 @@ void fill_launch(const sidp_ctx* c, StageLaunch<T>& L) {
     L.si = make_smoothness<T>(c->cfg);
   }
   L.limiter = c->cfg.limiter;
+  L.dense = c->cfg.unsparsified;
   if (c->debug) {
     L.inst.dbg_lo = c->d_dbg;
     L.inst.dbg_hi = c->d_dbg + c->N;
@@ -356,8 +357,10 @@ sidp_status validate_config(const sidp_config* cfg, std::string& msg) {
   if (cfg->precision != SIDP_FP64 && cfg->precision != SIDP_MIXED) { msg = "unknown precision"; return SIDP_ERR_ARG; }
   const double hx = (cfg->x1 - cfg->x0) / cfg->nx, hy = (cfg->y1 - cfg->y0) / cfg->ny;
   if (!(hx > 0) || !(hy > 0) || std::fabs(hx - hy) > 1e-12 * hx) { msg = "elements must be square with positive size"; return SIDP_ERR_ARG; }
-  for (int s = 0; s < 4; ++s)
-    if (cfg->bc[s] < 0 || cfg->bc[s] > 2) { msg = "unknown boundary condition"; return SIDP_ERR_ARG; }
+  for (int s = 0; s < 4; ++s) {
+    if (cfg->bc[s] < 0 || cfg->bc[s] > 3) { msg = "unknown boundary condition"; return SIDP_ERR_ARG; }
+    if (cfg->bc[s] == SIDP_BC_SLIP_WALL && cfg->law != SIDP_LAW_EULER2D) { msg = "slip walls need the Euler law"; return SIDP_ERR_ARG; }
+  }
   if ((cfg->bc[0] == SIDP_BC_PERIODIC) != (cfg->bc[1] == SIDP_BC_PERIODIC) ||
       (cfg->bc[2] == SIDP_BC_PERIODIC) != (cfg->bc[3] == SIDP_BC_PERIODIC)) { msg = "periodic sides must be paired"; return SIDP_ERR_ARG; }
   if (!(cfg->cfl > 0.0) || cfg->cfl > 1.0) { msg = "cfl must be in (0,1]"; return SIDP_ERR_ARG; }
@@ -368,6 +371,7 @@ sidp_status validate_config(const sidp_config* cfg, std::string& msg) {
     msg = "non-finite advection velocity gradient"; return SIDP_ERR_ARG;
   }
   if (cfg->smoothness != 0 && cfg->smoothness != 1) { msg = "smoothness must be 0 or 1"; return SIDP_ERR_ARG; }
+  if (cfg->unsparsified != 0 && cfg->unsparsified != 1) { msg = "unsparsified must be 0 or 1"; return SIDP_ERR_ARG; }
   if (cfg->smoothness && (!std::isfinite(cfg->si_gmin) || !std::isfinite(cfg->si_gmax) || cfg->si_gmin > cfg->si_gmax ||
                           !std::isfinite(cfg->si_s0) || !std::isfinite(cfg->si_kappa))) {
     msg = "smoothness indicator needs finite s0, kappa and g_min <= g_max"; return SIDP_ERR_ARG;

@@ -135,6 +135,7 @@ struct StageLaunch {
   Tables<T> tab;
   LawParamsT<T> lp;
   int limiter;
+  int dense;  // unsparsified graph viscosity (Sec. 3.4 comparison mode)
   SmoothnessT<T> si;
 };
 
@@ -189,6 +190,11 @@ SIDP_DECLARE(LAW_ADVECTION_VAR, float)
   template <>                                                                                          \
   cudaError_t launch_p<LAWID, TT, P>(int tile, const StageLaunch<TT>& a, unsigned long long* bits,     \
                                      cudaStream_t s) {                                                 \
+    if (a.dense) { /* unsparsified comparison mode: its own kernels, default tile shape */             \
+      if (bits || a.limiter != 3)                                                                      \
+        return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, false, true>(a, bits, s); \
+      return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, true, true>(a, bits, s);  \
+    }                                                                                                  \
     if (a.limiter == 3 && !bits) /* elementwise limiting: its own kernel, default tile shape */       \
       return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, true>(a, bits, s);       \
     switch (tile) {                                                                                    \

@@ -81,7 +81,8 @@ struct TileSmem {
 
 // Trace of the neighbouring element across `side` (0 W, 1 E, 2 S, 3 N) of element (ex, ey) at
 // position `pos` along the face.  Periodic wraps; outflow (reading: ghost = interior trace) copies
-// the element's own trace node; exact-state reads the ghost buffer.
+// the element's own trace node; exact-state reads the ghost buffer; a slip wall (Sec. 5.7) mirrors
+// the own trace node (normal momentum negated).
 template <int P, int NC, typename T>
 __device__ __forceinline__ void neighbor_trace(const Instance<T>& I, int side, int ex, int ey, int pos, T* out) {
   constexpr int n = P + 1, NN = n * n;
@@ -106,6 +107,9 @@ __device__ __forceinline__ void neighbor_trace(const Instance<T>& I, int side, i
   } else {
 #pragma unroll
     for (int f = 0; f < NC; ++f) out[f] = I.uin[f * I.N + e * NN + own];
+    if constexpr (NC == 4) {  // slip wall (Euler): the mirror image, normal momentum negated
+      if (bc == 3) out[side < 2 ? 1 : 2] = -out[side < 2 ? 1 : 2];
+    }
   }
 }
 
@@ -455,9 +459,49 @@ __device__ __forceinline__ void face_eval_r(S& s, int k, int L, const Vec<T, LAW
 }
 
 // The whole stage for one tile of one problem instance.
+// Unsparsified graph viscosity (Sec. 3.4 comparison mode): the low-order operator built on the
+// dense DG-SEM differentiation matrix couples node j of a line of its element with every other
+// node c of that line: c_jc = h w D[c][j] e_k, d_jc = lambda h w |D[c][j]| (|D[c][j]| = |D[j][c]| for
+// c != j by summation by parts), bar state 1/2 (u_j + u_c) + sign(D[c][j]) (F_c - F_j) / (2 lambda).
+// Accumulates, without the factor h w: vol = sum_c D[c][j] F_c, visc = sum_c lambda |D[c][j]| (u_c - u_j),
+// lam = sum_c lambda |D[c][j]|, and the bar-state extremes of field 0 and the sigma minimum.
+template <int P, class LAW, typename T, class S>
+__device__ __forceinline__ void dense_line(const S& s, int k, int base, int stride, int j, const LawParamsT<T>& lp,
+                                           T* vol, T* visc, T& lam, T& lo, T& hi, T& smin) {
+  constexpr int n = P + 1, NC = LAW::NC;
+  using V = Vec<T, NC>;
+  const int me = base + j * stride;
+  const V ui = s.u[me];
+  const V Fi = (k == 0) ? s.fx[me] : s.fy[me];
+  const typename LAW::Aux ai = s.aux[me];
+#pragma unroll 1
+  for (int c = 0; c < n; ++c) {
+    const int sc = base + c * stride;
+    const V Fc = (k == 0) ? s.fx[sc] : s.fy[sc];
+    const T dcj = s.D[c * n + j];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) vol[q] += dcj * Fc.v[q];
+    if (c == j || dcj == T(0)) continue;  // pairs with c_jc = c_cj = 0 are not in the stencil
+    const V uc = s.u[sc];
+    const typename LAW::Aux ac = s.aux[sc];
+    // the pair's Riemann problem runs along n_jc = -c_jc/|c_jc| = -sign(D[c][j]) e_k: node j is its
+    // left state when D[c][j] < 0 (for the dense operator this need not match the nodes' order)
+    const T l = (dcj < T(0)) ? LAW::lam(k, ui.v, ai, uc.v, ac, lp) : LAW::lam(k, uc.v, ac, ui.v, ai, lp);
+    const T ad = fabs(dcj);
+    lam += l * ad;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) visc[q] += l * ad * (uc.v[q] - ui.v[q]);
+    T bar = T(0.5) * (ui.v[0] + uc.v[0]);
+    if (l > T(0)) bar += ((dcj > T(0)) ? T(1) : T(-1)) * fdiv(Fc.v[0] - Fi.v[0], T(2) * l);
+    lo = tmin(lo, bar);
+    hi = tmax(hi, bar);
+    if constexpr (LAW::kEntropy) smin = tmin(smin, s.sig[sc]);
+  }
+}
+
 // ELW selects elementwise limiting at compile time (its kernels are separate instantiations, so
 // the subcell kernels carry none of its code).
-template <int P, int TX, int TY, class LAW, typename T, bool ELW = false>
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool DENSE = false>
 __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const Instance<T>& I, const Tables<T>& tab,
                                            const LawParamsT<T>& lp, int limiter, const SmoothnessT<T>& si, int tile_x,
                                            int tile_y) {
@@ -570,6 +614,15 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
 #pragma unroll
       for (int q = 0; q < NC; ++q) { sx[q] += dx * Fxc.v[q]; sy[q] += dy * Fyc.v[q]; }
     }
+    T dvx[NC], dgx[NC], dvy[NC], dgy[NC];
+    T dlo = vu.v[0], dhi = vu.v[0], dsig = T(0), dlam = T(0);
+    if constexpr (DENSE) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) { dvx[q] = dgx[q] = dvy[q] = dgy[q] = T(0); }
+      if constexpr (LAW::kEntropy) dsig = s.sig[me];
+      dense_line<P, LAW>(s, 0, le * NN + a * n, 1, b, lp, dvx, dgx, dlam, dlo, dhi, dsig);
+      dense_line<P, LAW>(s, 1, le * NN + b, n, a, lp, dvy, dgy, dlam, dlo, dhi, dsig);
+    }
     T out[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
@@ -578,8 +631,12 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
       if (a == 0) sy[q] += vfy.v[q] - fd.v[q];
       if (a == P) sy[q] += fu.v[q] - vfy.v[q];
       const T rHx = -hwa * sx[q], rHy = -hwb * sy[q];
-      const T rLx = -hwa * (fr.v[q] - fl.v[q]);
-      const T rLy = -hwb * (fu.v[q] - fd.v[q]);
+      T rLx = -hwa * (fr.v[q] - fl.v[q]);
+      T rLy = -hwb * (fu.v[q] - fd.v[q]);
+      if constexpr (DENSE) {  // dense volume term and graph viscosity, element-face fluxes only
+        rLx = hwa * (dvx[q] + dgx[q] + ((b == 0) ? fl.v[q] : T(0)) - ((b == P) ? fr.v[q] : T(0)));
+        rLy = hwb * (dvy[q] + dgy[q] + ((a == 0) ? fd.v[q] : T(0)) - ((a == P) ? fu.v[q] : T(0)));
+      }
       uL[q] = vu.v[q] + dtm * (rLx + rLy);
       out[q] = (limiter == 0) ? vu.v[q] + dtm * (rHx + rHy) : uL[q];
       rx[q] = rHx - rLx;
@@ -591,15 +648,34 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
         I.uout[q * N + g] = (I.c0 == T(0)) ? out[q] : I.c0 * I.u0[q * N + g] + I.c1 * out[q];
     }
     const auto bl = s.bbx[ix], br = s.bbx[ix + 1], bd = s.bby[iy], bu = s.bby[iy + G::NX];
-    lo = tmin(tmin(vu.v[0], tmin(bl.v[0], br.v[0])), tmin(bd.v[0], bu.v[0]));
-    hi = tmax(tmax(vu.v[0], tmax(bl.v[0], br.v[0])), tmax(bd.v[0], bu.v[0]));
+    if constexpr (DENSE) {  // in-element pairs from the dense lines, plus the element-face pairs
+      lo = dlo;
+      hi = dhi;
+      if (b == 0) { lo = tmin(lo, bl.v[0]); hi = tmax(hi, bl.v[0]); }
+      if (b == P) { lo = tmin(lo, br.v[0]); hi = tmax(hi, br.v[0]); }
+      if (a == 0) { lo = tmin(lo, bd.v[0]); hi = tmax(hi, bd.v[0]); }
+      if (a == P) { lo = tmin(lo, bu.v[0]); hi = tmax(hi, bu.v[0]); }
+    } else {
+      lo = tmin(tmin(vu.v[0], tmin(bl.v[0], br.v[0])), tmin(bd.v[0], bu.v[0]));
+      hi = tmax(tmax(vu.v[0], tmax(bl.v[0], br.v[0])), tmax(bd.v[0], bu.v[0]));
+    }
     if (si.on) {  // Eq. relaxed-bounds
       const T e = s.eps[le];
       lo = e * lo + (T(1) - e) * si.gmin;
       hi = e * hi + (T(1) - e) * si.gmax;
     }
     // K_i = min sigma over the node and its four neighbours = min over its four faces' minima
-    if constexpr (LAW::kEntropy) K = tmin(tmin(bl.v[1], br.v[1]), tmin(bd.v[1], bu.v[1]));
+    if constexpr (LAW::kEntropy) {
+      if constexpr (DENSE) {
+        K = dsig;
+        if (b == 0) K = tmin(K, bl.v[1]);
+        if (b == P) K = tmin(K, br.v[1]);
+        if (a == 0) K = tmin(K, bd.v[1]);
+        if (a == P) K = tmin(K, bu.v[1]);
+      } else {
+        K = tmin(tmin(bl.v[1], br.v[1]), tmin(bd.v[1], bu.v[1]));
+      }
+    }
   }
   if (limiter < 2) return;  // uniform across the CTA
   if constexpr (ELW) {      // elementwise limiting (Sec. 4.1.2, 4.2.1)
@@ -729,14 +805,14 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
   }
 }
 
-template <int P, int TX, int TY, class LAW, typename T, bool ELW = false>
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool DENSE = false>
 __global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
 k_stage(const StageLaunch<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto& s = *reinterpret_cast<TileSmem<P, TX, TY, LAW, T>*>(smem_raw);
   const int tiles_x = (A.inst.nx + TX - 1) / TX;
   const int tile_y = blockIdx.x / tiles_x, tile_x = blockIdx.x - tile_y * tiles_x;
-  stage_body<P, TX, TY, LAW, T, ELW>(s, A.inst, A.tab, A.lp, A.limiter, A.si, tile_x, tile_y);
+  stage_body<P, TX, TY, LAW, T, ELW, DENSE>(s, A.inst, A.tab, A.lp, A.limiter, A.si, tile_x, tile_y);
 }
 
 // Copy the instance descriptor of this CTA's task into shared memory (all threads help).
@@ -767,7 +843,7 @@ k_stage_batch(const BatchLaunch<T> B) {
 // CFL bound of Eq. cfl-low per node, m_i / (2 sum_{j != i} d-hat_ij) with d-hat = (h w / 2) lambda on
 // the node's four faces, min-reduced into *out_bits (positive doubles order like their bit patterns).
 // Same tile machinery as the stage kernel: node quantities once per node, lambda once per face.
-template <int P, int TX, int TY, class LAW, typename T>
+template <int P, int TX, int TY, class LAW, typename T, bool DENSE = false>
 __device__ __forceinline__ void dt_body(TileSmem<P, TX, TY, LAW, T>& s, const Instance<T>& I, const Tables<T>& tab,
                                         const LawParamsT<T>& lp, int tile_x, int tile_y, unsigned long long* out_bits) {
   using G = TileGeom<P, TX, TY>;
@@ -811,7 +887,32 @@ __device__ __forceinline__ void dt_body(TileSmem<P, TX, TY, LAW, T>& s, const In
     const int ix = row * (G::NX + 1) + col, iy = row * G::NX + col;
     const T h = I.hT;
     const T wa = s.w[a], wb = s.w[b];
-    const T sumd = T(0.5) * h * wa * (lamx[ix] + lamx[ix + 1]) + T(0.5) * h * wb * (lamy[iy] + lamy[iy + G::NX]);
+    T sumd = T(0.5) * h * wa * (lamx[ix] + lamx[ix + 1]) + T(0.5) * h * wb * (lamy[iy] + lamy[iy + G::NX]);
+    if constexpr (DENSE) {  // element-face pairs as above; every in-element pair of the dense lines
+      constexpr int NN = n * n;
+      sumd = T(0.5) * h * wa * (((b == 0) ? lamx[ix] : T(0)) + ((b == P) ? lamx[ix + 1] : T(0))) +
+             T(0.5) * h * wb * (((a == 0) ? lamy[iy] : T(0)) + ((a == P) ? lamy[iy + G::NX] : T(0)));
+      const int me = le * NN + a * n + b;
+      const V ui = s.u[me];
+      const typename LAW::Aux ai = s.aux[me];
+#pragma unroll 1
+      for (int c = 0; c < n; ++c) {
+        if (c != b && s.D[c * n + b] != T(0)) {
+          const int sc = le * NN + a * n + c;
+          const V uc = s.u[sc];
+          const T l = (s.D[c * n + b] < T(0)) ? LAW::lam(0, ui.v, ai, uc.v, s.aux[sc], lp)
+                                               : LAW::lam(0, uc.v, s.aux[sc], ui.v, ai, lp);
+          sumd += h * wa * l * fabs(s.D[c * n + b]);
+        }
+        if (c != a && s.D[c * n + a] != T(0)) {
+          const int sc = le * NN + c * n + b;
+          const V uc = s.u[sc];
+          const T l = (s.D[c * n + a] < T(0)) ? LAW::lam(1, ui.v, ai, uc.v, s.aux[sc], lp)
+                                               : LAW::lam(1, uc.v, s.aux[sc], ui.v, ai, lp);
+          sumd += h * wb * l * fabs(s.D[c * n + a]);
+        }
+      }
+    }
     if (sumd > T(0)) val = fdiv(h * h * wa * wb, T(2) * sumd);
   }
 #pragma unroll
@@ -827,14 +928,14 @@ __device__ __forceinline__ void dt_body(TileSmem<P, TX, TY, LAW, T>& s, const In
   }
 }
 
-template <int P, int TX, int TY, class LAW, typename T>
+template <int P, int TX, int TY, class LAW, typename T, bool DENSE = false>
 __global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
 k_dt(const StageLaunch<T> A, unsigned long long* out_bits) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto& s = *reinterpret_cast<TileSmem<P, TX, TY, LAW, T>*>(smem_raw);
   const int tiles_x = (A.inst.nx + TX - 1) / TX;
   const int tile_y = blockIdx.x / tiles_x, tile_x = blockIdx.x - tile_y * tiles_x;
-  dt_body<P, TX, TY, LAW, T>(s, A.inst, A.tab, A.lp, tile_x, tile_y, out_bits);
+  dt_body<P, TX, TY, LAW, T, DENSE>(s, A.inst, A.tab, A.lp, tile_x, tile_y, out_bits);
 }
 
 template <int P, int TX, int TY, class LAW, typename T>
@@ -850,22 +951,22 @@ k_dt_batch(const BatchLaunch<T> B) {
   dt_body<P, TX, TY, LAW, T>(s, sI, B.tab, B.lp, tile_x, tile_y, B.bits + task.x);
 }
 
-template <int P, int TX, int TY, class LAW, typename T, bool ELW = false>
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool DENSE = false>
 cudaError_t launch_tile(const StageLaunch<T>& a, unsigned long long* dt_bits, cudaStream_t s) {
   using G = TileGeom<P, TX, TY>;
   constexpr size_t smem = sizeof(TileSmem<P, TX, TY, LAW, T>);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(k_stage<P, TX, TY, LAW, T, ELW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = cudaFuncSetAttribute(k_stage<P, TX, TY, LAW, T, ELW, DENSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    err = cudaFuncSetAttribute(k_dt<P, TX, TY, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    err = cudaFuncSetAttribute(k_dt<P, TX, TY, LAW, T, DENSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     attr_set = true;
   }
   const long long tiles = (long long)((a.inst.nx + TX - 1) / TX) * ((a.inst.ny + TY - 1) / TY);
   if (tiles <= 0) return cudaSuccess;
-  if (dt_bits) k_dt<P, TX, TY, LAW, T><<<(unsigned)tiles, G::THREADS, smem, s>>>(a, dt_bits);
-  else k_stage<P, TX, TY, LAW, T, ELW><<<(unsigned)tiles, G::THREADS, smem, s>>>(a);
+  if (dt_bits) k_dt<P, TX, TY, LAW, T, DENSE><<<(unsigned)tiles, G::THREADS, smem, s>>>(a, dt_bits);
+  else k_stage<P, TX, TY, LAW, T, ELW, DENSE><<<(unsigned)tiles, G::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 

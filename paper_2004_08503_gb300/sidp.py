@@ -18,7 +18,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "sidp.h")
 
 LAWS = {"burgers": 1, "euler": 2, "advection": 3, "advection_var": 4}
 PRECISIONS = {"fp64": 0, "mixed": 1}
-BCS = {"periodic": 0, "outflow": 1, "exact": 2}
+BCS = {"periodic": 0, "outflow": 1, "exact": 2, "wall": 3}
 LIMITERS = {"none": 0, "lo": 1, "subcell": 2, "elementwise": 3}
 SIDES = {"W": 0, "E": 1, "S": 2, "N": 3}
 
@@ -30,7 +30,7 @@ class sidp_config(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("gamma", ctypes.c_double), ("adv_beta", ctypes.c_double * 2),
                 ("limiter", ctypes.c_int), ("smoothness", ctypes.c_int), ("si_s0", ctypes.c_double),
                 ("si_kappa", ctypes.c_double), ("si_gmin", ctypes.c_double), ("si_gmax", ctypes.c_double),
-                ("adv_grad", ctypes.c_double * 2)]
+                ("adv_grad", ctypes.c_double * 2), ("unsparsified", ctypes.c_int)]
 
 
 class sidp_diag(ctypes.Structure):
@@ -131,9 +131,10 @@ def _stream_handle(stream):
 
 def make_config(law="euler", p=3, nx=8, ny=8, precision="fp64", domain=(0.0, 1.0, 0.0, 1.0),
                 bc=("periodic",) * 4, cfl=0.5, gamma=1.4, beta=(1.0, 0.0), limiter="subcell", smoothness=None,
-                grad=(0.0, 0.0)):
+                grad=(0.0, 0.0), sparsify=True):
     """smoothness: None, or dict(gmin, gmax[, s0, kappa]) for the Sec. 4.4 indicator.
-    law "advection_var": velocity (beta[0] + grad[0] y, beta[1] + grad[1] x)."""
+    law "advection_var": velocity (beta[0] + grad[0] y, beta[1] + grad[1] x).
+    sparsify=False: the unsparsified graph-viscosity comparison mode (Sec. 3.4)."""
     c = sidp_config()
     c.law, c.p, c.nx, c.ny = LAWS[law], p, nx, ny
     c.precision = PRECISIONS[precision]
@@ -143,6 +144,7 @@ def make_config(law="euler", p=3, nx=8, ny=8, precision="fp64", domain=(0.0, 1.0
     c.cfl, c.gamma = cfl, gamma
     c.adv_beta[0], c.adv_beta[1] = beta
     c.adv_grad[0], c.adv_grad[1] = grad
+    c.unsparsified = 0 if sparsify else 1
     c.limiter = LIMITERS[limiter]
     if smoothness is not None:
         c.smoothness = 1

@@ -110,3 +110,26 @@ def test_wall_limited_stage_equals_mirrored_problem(p, side):
 def test_wall_rejects_scalar_laws():
     with pytest.raises(ValueError):
         scheme.Problem(laws.Burgers(), 2, 2, 2, bc=("wall", "outflow", "outflow", "outflow"))
+
+
+@pytest.mark.parametrize("p,bc", [(2, ("wall", "outflow", "wall", "outflow")), (5, ("wall",) * 4),
+                                  (3, ("outflow",) * 4)])
+def test_euler_comparator_accepts_oracle_under_input_noise(p, bc):
+    """The conditioning-aware Euler check must accept the oracle against itself under one-ulp
+    input noise: entropy roots near the entropy bound, and Zalesak's density ratio on the density
+    plateau of this data (lo = u^L exactly, noise-level density fluxes, genuine momentum fluxes),
+    move under rounding by far more than 1e-12."""
+    law = laws.Euler(G)
+    pb = scheme.Problem(law, p, 5, 3, domain=(0.0, 1.0, 0.0, 0.6), bc=bc)
+    X, Y = pb.node_coords()
+    U = law.prim_to_cons(*_data(X, Y))
+    dt = pb.compute_dt(U)
+    base = pb.fe_stage(U, dt)
+    worst = 0.0
+    for seed in range(6):
+        rng = np.random.default_rng(seed)
+        noisy = U * (1 + 2.2e-16 * rng.standard_normal(U.shape))
+        got = pb.fe_stage(noisy, dt)
+        worst = max(worst, float(np.max(np.abs(got - base) / np.max(np.abs(base), axis=(1, 2))[:, None, None])))
+        euler_fe_check(pb, U, dt, got)
+    assert worst > 1e-12   # the sensitivity is real
