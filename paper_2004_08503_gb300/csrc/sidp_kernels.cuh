@@ -79,6 +79,21 @@ struct TileSmem {
   T aK[G::NE];    // elementwise limiting: alpha_K per element of the tile
 };
 
+// The time-step kernel's shared memory: node states and records, one wave-speed bound per face,
+// and the tables the tile loader fills.  About a third of TileSmem, so more CTAs fit on an SM.
+template <int P, int TX, int TY, class LAW, typename T>
+struct DtSmem {
+  using G = TileGeom<P, TX, TY>;
+  Vec<T, LAW::NC> u[G::NS];
+  typename LAW::Aux aux[G::NS];
+  T lamx[G::NFX];
+  T lamy[G::NFY];
+  T D[G::NN];
+  T w[G::n];
+  T Vinv[G::NN];
+  T nrm[G::n];
+};
+
 // Trace of the neighbouring element across `side` (0 W, 1 E, 2 S, 3 N) of element (ex, ey) at
 // position `pos` along the face.  Periodic wraps; outflow (reading: ghost = interior trace) copies
 // the element's own trace node; exact-state reads the ghost buffer; a slip wall (Sec. 5.7) mirrors
@@ -844,7 +859,7 @@ k_stage_batch(const BatchLaunch<T> B) {
 // the node's four faces, min-reduced into *out_bits (positive doubles order like their bit patterns).
 // Same tile machinery as the stage kernel: node quantities once per node, lambda once per face.
 template <int P, int TX, int TY, class LAW, typename T, bool DENSE = false>
-__device__ __forceinline__ void dt_body(TileSmem<P, TX, TY, LAW, T>& s, const Instance<T>& I, const Tables<T>& tab,
+__device__ __forceinline__ void dt_body(DtSmem<P, TX, TY, LAW, T>& s, const Instance<T>& I, const Tables<T>& tab,
                                         const LawParamsT<T>& lp, int tile_x, int tile_y, unsigned long long* out_bits) {
   using G = TileGeom<P, TX, TY>;
   using V = Vec<T, LAW::NC>;
@@ -854,8 +869,8 @@ __device__ __forceinline__ void dt_body(TileSmem<P, TX, TY, LAW, T>& s, const In
   long long g;
   const bool act = load_tile<P, TX, TY, LAW, true>(s, I, tab, lp, tile_x, tile_y, le, a, b, g);
   __syncthreads();
-  T* lamx = reinterpret_cast<T*>(s.bbx);  // face lambdas reuse the bar-state arrays
-  T* lamy = reinterpret_cast<T*>(s.bby);
+  T* lamx = s.lamx;
+  T* lamy = s.lamy;
   if (t < G::NT) {
     const int row = (le / TX) * n + a, col = (le % TX) * n + b;
     const V uR = s.u[t];
@@ -932,7 +947,7 @@ template <int P, int TX, int TY, class LAW, typename T, bool DENSE = false>
 __global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
 k_dt(const StageLaunch<T> A, unsigned long long* out_bits) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  auto& s = *reinterpret_cast<TileSmem<P, TX, TY, LAW, T>*>(smem_raw);
+  auto& s = *reinterpret_cast<DtSmem<P, TX, TY, LAW, T>*>(smem_raw);
   const int tiles_x = (A.inst.nx + TX - 1) / TX;
   const int tile_y = blockIdx.x / tiles_x, tile_x = blockIdx.x - tile_y * tiles_x;
   dt_body<P, TX, TY, LAW, T, DENSE>(s, A.inst, A.tab, A.lp, tile_x, tile_y, out_bits);
@@ -942,7 +957,7 @@ template <int P, int TX, int TY, class LAW, typename T>
 __global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
 k_dt_batch(const BatchLaunch<T> B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  auto& s = *reinterpret_cast<TileSmem<P, TX, TY, LAW, T>*>(smem_raw);
+  auto& s = *reinterpret_cast<DtSmem<P, TX, TY, LAW, T>*>(smem_raw);
   __shared__ Instance<T> sI;
   const int2 task = B.tasks[blockIdx.x];
   load_instance(sI, B.insts + task.x);
@@ -955,17 +970,18 @@ template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool D
 cudaError_t launch_tile(const StageLaunch<T>& a, unsigned long long* dt_bits, cudaStream_t s) {
   using G = TileGeom<P, TX, TY>;
   constexpr size_t smem = sizeof(TileSmem<P, TX, TY, LAW, T>);
+  constexpr size_t smem_dt = sizeof(DtSmem<P, TX, TY, LAW, T>);
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t err = cudaFuncSetAttribute(k_stage<P, TX, TY, LAW, T, ELW, DENSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    err = cudaFuncSetAttribute(k_dt<P, TX, TY, LAW, T, DENSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    err = cudaFuncSetAttribute(k_dt<P, TX, TY, LAW, T, DENSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dt);
     if (err != cudaSuccess) return err;
     attr_set = true;
   }
   const long long tiles = (long long)((a.inst.nx + TX - 1) / TX) * ((a.inst.ny + TY - 1) / TY);
   if (tiles <= 0) return cudaSuccess;
-  if (dt_bits) k_dt<P, TX, TY, LAW, T, DENSE><<<(unsigned)tiles, G::THREADS, smem, s>>>(a, dt_bits);
+  if (dt_bits) k_dt<P, TX, TY, LAW, T, DENSE><<<(unsigned)tiles, G::THREADS, smem_dt, s>>>(a, dt_bits);
   else k_stage<P, TX, TY, LAW, T, ELW, DENSE><<<(unsigned)tiles, G::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -974,16 +990,17 @@ template <int P, int TX, int TY, class LAW, typename T, bool ELW = false>
 cudaError_t launch_batch_tile(const BatchLaunch<T>& B, bool dt, cudaStream_t s) {
   using G = TileGeom<P, TX, TY>;
   constexpr size_t smem = sizeof(TileSmem<P, TX, TY, LAW, T>);
+  constexpr size_t smem_dt = sizeof(DtSmem<P, TX, TY, LAW, T>);
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t err = cudaFuncSetAttribute(k_stage_batch<P, TX, TY, LAW, T, ELW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    err = cudaFuncSetAttribute(k_dt_batch<P, TX, TY, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    err = cudaFuncSetAttribute(k_dt_batch<P, TX, TY, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dt);
     if (err != cudaSuccess) return err;
     attr_set = true;
   }
   if (B.ntasks <= 0) return cudaSuccess;
-  if (dt) k_dt_batch<P, TX, TY, LAW, T><<<(unsigned)B.ntasks, G::THREADS, smem, s>>>(B);
+  if (dt) k_dt_batch<P, TX, TY, LAW, T><<<(unsigned)B.ntasks, G::THREADS, smem_dt, s>>>(B);
   else k_stage_batch<P, TX, TY, LAW, T, ELW><<<(unsigned)B.ntasks, G::THREADS, smem, s>>>(B);
   return cudaGetLastError();
 }
