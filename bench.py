@@ -302,7 +302,7 @@ def run_batched(torch, sidp, stream, steps, warmup, seed=0, count=512):
     return {"value": nodes * 3 * steps / sec, "unit": UNIT, "instances": count, "nodes": nodes, "steps": steps,
             "ms_per_step": 1e3 * sec / steps, "launches_per_step": "4 per (p, tile) group + 1",
             "invariants_sampled": worst, "workload": f"{count} Euler instances, elements per side in {{8,16,32,64}}, "
-            f"p in {{2..7}} (seed {seed}), four-quadrant data, mixed precision, one CUDA graph per step"}
+            f"p in {{2..7}} (seed {seed}), four-quadrant data, mixed precision, one CUDA graph per step, degree groups on concurrent graph branches"}
 
 
 def run_accuracy(sidp, stream, stages=200):

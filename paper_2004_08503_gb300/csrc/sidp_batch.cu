@@ -68,6 +68,9 @@ struct sidp_batch {
   unsigned long long* d_bits = nullptr;
   StageStats* d_stats = nullptr;
   std::vector<Group> groups;
+  std::vector<cudaStream_t> gstream;  // one stream per degree group (the groups are independent)
+  std::vector<cudaEvent_t> gdone;     // a group's work on its stream is done
+  cudaEvent_t fork = nullptr;         // work so far on the batch stream is done
   cudaGraphExec_t graph = nullptr;
   bool warm = false;
   bool stats_on = true;
@@ -151,10 +154,11 @@ cudaError_t launch_batch_law(int p, int tile, const BatchLaunch<T>& bl, bool dt,
   }
 }
 
-// k = 0: time-step launch; k = 1..3: SSP-RK3 stage k (Sec. 5).
+// k = 0: time-step launch; k = 1..3: SSP-RK3 stage k (Sec. 5), for degree group gi on stream st.
 template <typename T>
-cudaError_t launch_groups(sidp_batch* b, int k) {
-  for (const Group& gr : b->groups) {
+cudaError_t launch_group(sidp_batch* b, int gi, int k, cudaStream_t st) {
+  {
+    const Group& gr = b->groups[gi];
     BatchLaunch<T> bl;
     std::memset(&bl, 0, sizeof(bl));
     bl.insts = static_cast<const Instance<T>*>(b->d_inst[k]);
@@ -177,28 +181,39 @@ cudaError_t launch_groups(sidp_batch* b, int k) {
     }
     bl.limiter = b->limiter;
     bl.bits = b->d_bits;
-    cudaError_t e;
     switch (b->law) {
-      case LAW_BURGERS: e = launch_batch_law<LAW_BURGERS, T>(gr.p, gr.tile, bl, k == 0, b->stream); break;
-      case LAW_EULER: e = launch_batch_law<LAW_EULER, T>(gr.p, gr.tile, bl, k == 0, b->stream); break;
-      case LAW_ADVECTION_VAR: e = launch_batch_law<LAW_ADVECTION_VAR, T>(gr.p, gr.tile, bl, k == 0, b->stream); break;
-      default: e = launch_batch_law<LAW_ADVECTION, T>(gr.p, gr.tile, bl, k == 0, b->stream); break;
+      case LAW_BURGERS: return launch_batch_law<LAW_BURGERS, T>(gr.p, gr.tile, bl, k == 0, st);
+      case LAW_EULER: return launch_batch_law<LAW_EULER, T>(gr.p, gr.tile, bl, k == 0, st);
+      case LAW_ADVECTION_VAR: return launch_batch_law<LAW_ADVECTION_VAR, T>(gr.p, gr.tile, bl, k == 0, st);
+      default: return launch_batch_law<LAW_ADVECTION, T>(gr.p, gr.tile, bl, k == 0, st);
     }
-    if (e != cudaSuccess) return e;
   }
-  if (k == 0) {
-    k_batch_finalize<<<(b->n + 127) / 128, 128, 0, b->stream>>>(b->d_bits, b->d_cfl, b->d_dt, b->d_dtf, b->d_clock, b->n);
-    return cudaGetLastError();
-  }
-  return cudaSuccess;
 }
 
-cudaError_t run_batch_step(sidp_batch* b) {
-  for (int k = 0; k <= 3; ++k) {
-    cudaError_t e = b->mixed ? launch_groups<float>(b, k) : launch_groups<double>(b, k);
-    if (e != cudaSuccess) return e;
+// Launches k0..k1 of every degree group, each group on its own stream forked from the batch stream
+// and joined back into it (under stream capture: parallel graph branches), so that one group's
+// launch tail overlaps the others' work.
+cudaError_t run_groups(sidp_batch* b, int k0, int k1) {
+  cudaError_t e = cudaEventRecord(b->fork, b->stream);
+  for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
+    const cudaStream_t st = b->gstream[gi];
+    e = cudaStreamWaitEvent(st, b->fork, 0);
+    for (int k = k0; k <= k1 && e == cudaSuccess; ++k)
+      e = b->mixed ? launch_group<float>(b, (int)gi, k, st) : launch_group<double>(b, (int)gi, k, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->gdone[gi], st);
   }
-  return cudaSuccess;
+  for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) e = cudaStreamWaitEvent(b->stream, b->gdone[gi], 0);
+  return e;
+}
+
+// One SSP-RK3 step of every instance: per-instance time steps (all groups), their finalize, then
+// the three stages (all groups).
+cudaError_t run_batch_step(sidp_batch* b) {
+  cudaError_t e = run_groups(b, 0, 0);
+  if (e != cudaSuccess) return e;
+  k_batch_finalize<<<(b->n + 127) / 128, 128, 0, b->stream>>>(b->d_bits, b->d_cfl, b->d_dt, b->d_dtf, b->d_clock, b->n);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return run_groups(b, 1, 3);
 }
 
 }  // namespace
@@ -297,6 +312,15 @@ sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int cou
     if ((e = cudaMemcpy(g.d_tasks, kv.second.data(), sizeof(int2) * g.ntasks, cudaMemcpyHostToDevice)) != cudaSuccess)
       return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
   }
+  if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess) return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
+    b->gstream.push_back(st);
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
+    b->gdone.push_back(ev);
+  }
   *out = b;
   return SIDP_OK;
 }
@@ -314,6 +338,9 @@ sidp_status sidp_batch_destroy(sidp_batch* b) {
   cudaFree(b->d_cfl);
   cudaFree(b->d_bits);
   cudaFree(b->d_stats);
+  for (cudaStream_t st : b->gstream) cudaStreamDestroy(st);
+  for (cudaEvent_t ev : b->gdone) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;
   return SIDP_OK;

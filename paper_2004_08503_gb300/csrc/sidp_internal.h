@@ -49,19 +49,20 @@ inline LawParamsT<T> make_law_params(double gamma, const double* beta, const dou
   return p;
 }
 
-// Element tile shapes (elements along x, y per CTA) for each degree; index 0 is the default and
-// the autotuner picks among them per (law, p, precision).
+// Element tile shapes (elements along x, y per CTA) for each degree; index 0 is the default (the
+// fastest on the Euler float32 path where the candidates were measured) and the autotuner picks
+// among them per (law, p, precision).
 struct TileShape { int tx, ty; };
 constexpr int kNumTiles = 4;
 constexpr TileShape kTiles[kMaxP + 1][kNumTiles] = {
     {{0, 0}, {0, 0}, {0, 0}, {0, 0}},
     {{8, 8}, {16, 4}, {4, 16}, {16, 8}},  // p=1: 256 / 256 / 256 / 512 threads
-    {{5, 5}, {7, 4}, {4, 7}, {7, 7}},     // p=2: 225 / 252 / 252 / 441
+    {{4, 7}, {7, 4}, {5, 5}, {7, 7}},     // p=2: 252 / 252 / 225 / 441
     {{4, 4}, {8, 2}, {2, 8}, {8, 4}},     // p=3: 256 / 256 / 256 / 512
-    {{3, 3}, {5, 2}, {2, 5}, {4, 5}},     // p=4: 225 / 250 / 250 / 500
-    {{2, 3}, {3, 2}, {7, 1}, {3, 4}},     // p=5: 216 / 216 / 252 / 432
-    {{2, 2}, {5, 1}, {1, 5}, {3, 3}},     // p=6: 196 / 245 / 245 / 441
-    {{2, 2}, {4, 1}, {1, 4}, {4, 2}},     // p=7: 256 / 256 / 256 / 512
+    {{2, 5}, {5, 2}, {3, 3}, {4, 5}},     // p=4: 250 / 250 / 225 / 500
+    {{7, 1}, {3, 2}, {2, 3}, {3, 4}},     // p=5: 252 / 216 / 216 / 432
+    {{1, 5}, {5, 1}, {2, 2}, {3, 3}},     // p=6: 245 / 245 / 196 / 441
+    {{1, 4}, {4, 1}, {2, 2}, {4, 2}},     // p=7: 256 / 256 / 256 / 512
 };
 
 // Reference-element tables for one degree p, in the stage precision T.
