@@ -154,6 +154,36 @@ __device__ __forceinline__ void fill_slot(S& s, int slot, const T* uu, T x, T y,
 }
 
 // Phase A: node slots and the halo.  Returns true for threads that own an active mesh node.
+// Halo slot h of a tile: the trace of the neighbouring element across the tile's edge (or the
+// boundary ghost), and its position (the face node's; the normal velocity is continuous).
+template <int P, int TX, int TY, int NC, typename T>
+__device__ __forceinline__ void halo_load(const Instance<T>& I, const Tables<T>& tab, int h, int ex0, int ey0, T hh,
+                                          T* uu, T& px, T& py) {
+  using G = TileGeom<P, TX, TY>;
+  constexpr int n = P + 1, NN = n * n;
+  int side, pos;
+  if (h < G::NY) { side = 0; pos = h; }
+  else if (h < 2 * G::NY) { side = 1; pos = h - G::NY; }
+  else if (h < 2 * G::NY + G::NX) { side = 2; pos = h - 2 * G::NY; }
+  else { side = 3; pos = h - 2 * G::NY - G::NX; }
+  int ex, ey, along;
+  if (side < 2) { ex = (side == 0) ? ex0 : ex0 + TX - 1; ey = ey0 + pos / n; along = pos % n; }
+  else { ey = (side == 2) ? ey0 : ey0 + TY - 1; ex = ex0 + pos / n; along = pos % n; }
+  if (side < 2) {
+    px = I.x0 + hh * T(side == 0 ? ex0 : ex0 + TX);
+    py = I.y0 + hh * (T(ey) + tab.xi[along]);
+  } else {
+    px = I.x0 + hh * (T(ex) + tab.xi[along]);
+    py = I.y0 + hh * T(side == 2 ? ey0 : ey0 + TY);
+  }
+  if (ex < I.nx && ey < I.ny) {
+    neighbor_trace<P, NC>(I, side, ex, ey, along, uu);
+  } else {
+#pragma unroll
+    for (int f = 0; f < NC; ++f) uu[f] = I.uin[f * I.N + ((long long)ey0 * I.nx + ex0) * NN];
+  }
+}
+
 template <int P, int TX, int TY, class LAW, bool LEAN, typename T, class S>
 __device__ __forceinline__ bool load_tile(S& s, const Instance<T>& I, const Tables<T>& tab, const LawParamsT<T>& lp,
                                           int tile_x, int tile_y, int& le, int& a, int& b, long long& g) {
@@ -189,33 +219,16 @@ __device__ __forceinline__ bool load_tile(S& s, const Instance<T>& I, const Tabl
 #pragma unroll
       for (int f = 0; f < NC; ++f) uu[f] = I.uin[f * I.N + ((long long)ey0 * I.nx + ex0) * NN];
     }
+    // the thread's first halo slot is loaded before the node slot is processed, so that the two
+    // global-load latencies overlap instead of adding up on the threads that own halo slots
+    T uh[NC], hx = T(0), hy = T(0);
+    if (t < G::NH) halo_load<P, TX, TY, NC>(I, tab, t, ex0, ey0, hh, uh, hx, hy);
     fill_slot<LAW, LEAN>(s, t, uu, px, py, lp);
+    if (t < G::NH) fill_slot<LAW, LEAN>(s, G::NT + t, uh, hx, hy, lp);
   }
-  for (int h = t; h < G::NH; h += G::THREADS) {
-    T uu[NC];
-    int side, pos;
-    if (h < G::NY) { side = 0; pos = h; }
-    else if (h < 2 * G::NY) { side = 1; pos = h - G::NY; }
-    else if (h < 2 * G::NY + G::NX) { side = 2; pos = h - 2 * G::NY; }
-    else { side = 3; pos = h - 2 * G::NY - G::NX; }
-    int ex, ey, along;
-    if (side < 2) { ex = (side == 0) ? ex0 : ex0 + TX - 1; ey = ey0 + pos / n; along = pos % n; }
-    else { ey = (side == 2) ? ey0 : ey0 + TY - 1; ex = ex0 + pos / n; along = pos % n; }
-    // halo position: the face node's (the normal velocity component is constant across the face)
-    T px, py;
-    if (side < 2) {
-      px = I.x0 + hh * T(side == 0 ? ex0 : ex0 + TX);
-      py = I.y0 + hh * (T(ey) + tab.xi[along]);
-    } else {
-      px = I.x0 + hh * (T(ex) + tab.xi[along]);
-      py = I.y0 + hh * T(side == 2 ? ey0 : ey0 + TY);
-    }
-    if (ex < I.nx && ey < I.ny) {
-      neighbor_trace<P, NC>(I, side, ex, ey, along, uu);
-    } else {
-#pragma unroll
-      for (int f = 0; f < NC; ++f) uu[f] = I.uin[f * I.N + ((long long)ey0 * I.nx + ex0) * NN];
-    }
+  for (int h = (t < G::NT) ? t + G::THREADS : t; h < G::NH; h += G::THREADS) {
+    T uu[NC], px, py;
+    halo_load<P, TX, TY, NC>(I, tab, h, ex0, ey0, hh, uu, px, py);
     fill_slot<LAW, LEAN>(s, G::NT + h, uu, px, py, lp);
   }
   return act;
