@@ -33,6 +33,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "node-updates/s per RK stage (Euler 2D p=3), mixed vs FP64; % HBM roofline"
 UNIT = "node-updates/s"
+# dram__bytes (read + write) per node and stage launch, averaged over the three stages, measured by
+# ncu on the 768x768 p=3 blast (profiles/k_stage_euler_mixed_p3.md).  The counters belong to the
+# stage kernel as committed with that profile; a changed kernel needs a new capture.
+STAGE_DRAM_BYTES_PER_NODE = 39.4
 NEL, P = 1024, 3
 WORKLOAD = "2D Euler blast, 1024x1024 elements, p=3 (16.8M nodes x 4 fields), outflow, CFL 0.5, subcell convex limiting"
 HBM_FALLBACK = 6800.0
@@ -381,6 +385,9 @@ def main():
     kt = stage_kernel_times(torch, sv, stream, reps=20)
     s = 4
     bytes_stage = [2 * 4 * s * nodes, 3 * 4 * s * nodes, 3 * 4 * s * nodes]
+    # DRAM traffic of the stage kernel per launch (average over stages 1-3), from one ncu capture
+    # of the 768x768 case (profiles/k_stage_euler_mixed_p3.md) scaled to this launch by nodes
+    traffic = STAGE_DRAM_BYTES_PER_NODE * nodes
     ach = sum(bytes_stage) / sum(kt) / 1e9
     # whole step on the per-node figure 3 * nc * s bytes per node per stage (dt pass included)
     step_gbs = 3 * 4 * s * nodes * 3 * args.steps / sec / 1e9
@@ -424,7 +431,7 @@ def main():
                            "l2": "state >= 151 MB per buffer > L2 (no flush needed)",
                            "parallelism": "independent replica per GPU"},
                 "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                             "traffic": None, "kernel": "k_stage<3, LawEuler<float>, float>",
+                             "traffic": traffic, "kernel": "k_stage<3, LawEuler<float>, float>",
                              "stage_ms": [1e3 * t for t in kt], "peak_kind": peak_kind,
                              "whole_step_gbs": step_gbs, "whole_step_frac": step_gbs / hbm},
                 "fp64": fp64, "batched": batched, "invariants": diag_stats, "accuracy": accuracy,
