@@ -35,11 +35,15 @@ class Problem:
     """Mesh, law, reference operators and boundary data of one simulation."""
 
     def __init__(self, law, p, nx, ny, domain=(0.0, 1.0, 0.0, 1.0), bc=("periodic",) * 4,
-                 ghost=None, cfl=0.5, limiter="subcell", sparsify=True, smoothness=None):
+                 ghost=None, cfl=0.5, limiter="subcell", sparsify=True, smoothness=None, split=None):
         """sparsify=False swaps D-hat for the dense D in the low-order operator: the
         unsparsified graph-viscosity method the paper compares against (Sec. 3.4).
         smoothness: None, or dict(gmin, gmax[, s0, kappa]) enabling the subcell-resolution
-        smoothness indicator of Sec. 4.4 (relaxed bounds of the limited field)."""
+        smoothness indicator of Sec. 4.4 (relaxed bounds of the limited field).
+        split: {side: dict(s0, speed, a, b)} for sides with bc "split": the ghost state is `a`
+        where the coordinate along the side is below s0 + speed t and `b` elsewhere (b None: a
+        slip wall there), t the time of the stage (the boundaries of the double Mach reflection,
+        Sec. 5.7)."""
         x0, x1, y0, y1 = map(float, domain)
         h = (x1 - x0) / nx
         if abs((y1 - y0) / ny - h) > 1e-14 * max(1.0, abs(h)):
@@ -49,11 +53,18 @@ class Problem:
         self.x0, self.y0, self.h = x0, y0, h
         self.bc = dict(zip(SIDES, bc))
         for s in SIDES:
-            if self.bc[s] not in ("periodic", "outflow", "exact", "wall"):
+            if self.bc[s] not in ("periodic", "outflow", "exact", "wall", "split"):
                 raise ValueError(self.bc[s])
             if self.bc[s] == "wall" and law.name != "euler":
                 raise ValueError("slip walls are defined for the Euler equations")
+            if self.bc[s] == "split" and (split is None or s not in split):
+                raise ValueError("split side without parameters")
         self.ghost = ghost or {}
+        self.split = split or {}
+        # simulated time t^n, and the time at which time-dependent ghost states are evaluated
+        # (t^n for dt and stage 1, t^n + dt for stage 2, t^n + dt/2 for stage 3 of SSP-RK3)
+        self.time = 0.0
+        self.t_eval = 0.0
         self.cfl, self.limiter = float(cfl), limiter
         self.smoothness = None
         if smoothness is not None:
@@ -117,7 +128,8 @@ class Problem:
         periodic: trace of the neighbouring element; outflow (reading: ghost = interior
         trace, u^+ = u^-); exact: user ghost trace self.ghost[side] of shape (nc, n_side, n);
         wall (slip, Sec. 5.7): the mirror image of the interior trace, normal momentum negated, so
-        that the face flux carries no mass and the face is a plane of symmetry.
+        that the face flux carries no mass and the face is a plane of symmetry; split: the state a
+        below the moving split point s0 + speed t_eval along the side, b (or a wall) above it.
         """
         nx, ny = self.nx, self.ny
         ex, ey = elems % nx, elems // nx
@@ -140,6 +152,20 @@ class Problem:
         elif bc == "wall":
             alt = own.copy()
             alt[1 if side in ("W", "E") else 2] *= -1.0
+        elif bc == "split":
+            sp = self.split[side]
+            if side in ("W", "E"):   # coordinate along the side of each face node: y
+                coord = self.y0 + self.h * (ey[:, None] + self.xi[None, :])
+            else:
+                coord = self.x0 + self.h * (ex[:, None] + self.xi[None, :])
+            below = coord < sp["s0"] + sp["speed"] * self.t_eval
+            a = np.asarray(sp["a"], dtype=float)[:, None, None] * np.ones_like(own)
+            if sp.get("b") is None:
+                b = own.copy()
+                b[1 if side in ("W", "E") else 2] *= -1.0
+            else:
+                b = np.asarray(sp["b"], dtype=float)[:, None, None] * np.ones_like(own)
+            alt = np.where(below[None], a, b)
         else:
             pos = ey if side in ("W", "E") else ex
             alt = np.asarray(self.ghost[side])[:, pos, :]
@@ -299,6 +325,7 @@ class Problem:
         reading: Eq. (cfl-low) divides by d-hat_ii = -sum d-hat_ij < 0; the convex-combination
         form Eq. (convex-combination) needs dt <= m_i / (2 sum_{j != i} d-hat_ij), used here.
         """
+        self.t_eval = self.time
         tot = self.sum_dhat(U)
         # a node with sum d-hat = 0 (a stagnation point of a velocity field) puts no limit on dt
         with np.errstate(divide="ignore"):
@@ -534,12 +561,21 @@ class Problem:
         """
         if dt is None:
             dt = self.compute_dt(U)
+        t = self.time
+        self.t_eval = t
         u1 = self.fe_stage(U, dt)
+        self.t_eval = t + dt
         u2 = 0.75 * U + 0.25 * self.fe_stage(u1, dt)
-        return U / 3.0 + (2.0 / 3.0) * self.fe_stage(u2, dt), dt
+        self.t_eval = t + 0.5 * dt
+        out = U / 3.0 + (2.0 / 3.0) * self.fe_stage(u2, dt)
+        self.time = self.t_eval = t + dt
+        return out, dt
 
     def stage(self, U, U0, dt, k, elems=None):
-        """SSP-RK3 stage k in {1,2,3} on elements `elems`: FE update plus the RK combination."""
+        """SSP-RK3 stage k in {1,2,3} on elements `elems`: FE update plus the RK combination.
+        Time-dependent ghost states are evaluated at self.time + (0, 1, 1/2)[k-1] dt (self.time
+        is not advanced)."""
+        self.t_eval = self.time + (0.0, 1.0, 0.5)[k - 1] * dt
         fe = self.fe_stage(U, dt, elems)
         U0e = U0[:, np.arange(self.Ne) if elems is None else np.asarray(elems)]
         if k == 1:

@@ -23,6 +23,9 @@ Recipes (all float64):
                      cylinder at (0.5,0.75): 1 where |x - 0.5| >= 0.025 or y >= 0.85, else 0;
                      zero outside the disks.  Rotation velocity (2 pi (1/2 - y), 2 pi (x - 1/2)).
   smooth_bump        cos(pi r/2)^6 on a disk of radius r0 around (xc, yc) (C^5), zero outside
+  double_mach        Sec. 5.7 on [0,4] x [0,1]: a Mach 10 shock through (1/6, 0) inclined at 60 degrees
+                     to the wall; pre-shock (rho, v, p) = (1.4, 0, 1), post-shock (8, 8.25 (cos 30,
+                     -sin 30), 116.5); the shock line at time t is x = 1/6 + (y + 20 t)/sqrt(3)
   batch_shapes       seeded (elements per side, p) pairs of a batch of independent problems
 """
 import numpy as np
@@ -119,6 +122,41 @@ def solid_body(x, y):
 def smooth_bump(x, y, xc=0.5, yc=0.3, r0=0.2):
     r = np.minimum(np.hypot(x - xc, y - yc) / r0, 1.0)
     return (np.cos(0.5 * np.pi * r) ** 6)[None]
+
+
+DMR_PRE = (1.4, 0.0, 0.0, 1.0)                                          # rho, vx, vy, p
+DMR_POST = (8.0, 8.25 * np.cos(np.pi / 6), -8.25 * np.sin(np.pi / 6), 116.5)
+
+
+def dmr_shock_x(y, t):
+    """x of the incident shock at height y and time t (Sec. 5.7)."""
+    return 1.0 / 6.0 + (y + 20.0 * t) / np.sqrt(3.0)
+
+
+def dmr_cons(prim, gamma=GAMMA):
+    rho, vx, vy, p = prim
+    return np.array([rho, rho * vx, rho * vy, p / (gamma - 1.0) + 0.5 * rho * (vx * vx + vy * vy)])
+
+
+def double_mach(x, y, gamma=GAMMA):
+    post = x < dmr_shock_x(y, 0.0)
+    rho = np.where(post, DMR_POST[0], DMR_PRE[0])
+    vx = np.where(post, DMR_POST[1], DMR_PRE[1])
+    vy = np.where(post, DMR_POST[2], DMR_PRE[2])
+    p = np.where(post, DMR_POST[3], DMR_PRE[3])
+    return _cons(rho, vx, vy, p, gamma)
+
+
+def double_mach_boundaries(gamma=GAMMA):
+    """Boundary data of Sec. 5.7 as split-side parameters: west inflow (post-shock), south
+    post-shock up to x = 1/6 then a slip wall, north post-shock / pre-shock split at the moving
+    shock; the east side is outflow."""
+    post, pre = dmr_cons(DMR_POST, gamma), dmr_cons(DMR_PRE, gamma)
+    return {
+        "W": dict(s0=1e30, speed=0.0, a=post, b=post),
+        "S": dict(s0=1.0 / 6.0, speed=0.0, a=post, b=None),
+        "N": dict(s0=dmr_shock_x(1.0, 0.0), speed=20.0 / np.sqrt(3.0), a=post, b=pre),
+    }
 
 
 def constant_state(x, y, prim=(0.7, 0.3, -0.2, 0.9), gamma=GAMMA):
