@@ -54,7 +54,8 @@ typedef enum {
   SIDP_BC_PERIODIC = 0,
   SIDP_BC_OUTFLOW = 1,
   SIDP_BC_EXACT_STATE = 2,
-  SIDP_BC_SLIP_WALL = 3 /* Euler only: ghost = mirror image of the trace (Sec. 5.7 slip wall) */
+  SIDP_BC_SLIP_WALL = 3, /* Euler only: ghost = mirror image of the trace (Sec. 5.7 slip wall) */
+  SIDP_BC_SPLIT = 4      /* two ghost states split at a moving point: sidp_set_split_boundary */
 } sidp_bc;
 /* NONE: the high-order DG-SEM target (Eq. dg-strong); LOW_ORDER: the sparse IDP method
  * (Eq. dg-idp); SUBCELL: subcell flux correction with Zalesak (Sec. 4.1.3) and, for Euler, convex
@@ -81,7 +82,7 @@ typedef struct {
   int bc[4];        /* sidp_bc for the W, E, S, N sides.  Periodic must be paired (W with E,
                        S with N).  Outflow: ghost = interior trace.  Exact: ghost traces set by
                        sidp_set_ghost_state.  Slip wall: the trace with its normal momentum
-                       negated (Euler)                                                            */
+                       negated (Euler).  Split: sidp_set_split_boundary                           */
   double cfl;       /* in (0, 1]; the paper uses 1/2 (Sec. 5)                                    */
   double gamma;     /* Euler ratio of specific heats, 1 < gamma <= 5/3 (wave-speed bound valid)  */
   double adv_beta[2]; /* advection velocity                                                      */
@@ -149,6 +150,22 @@ sidp_status sidp_download_state(sidp_ctx* ctx, int which, void* host);
 /* Ghost trace for SIDP_BC_EXACT_STATE on `side` (0 W, 1 E, 2 S, 3 N): float64 [nc][n_side][p+1]
  * with n_side = ny for W/E and nx for S/N, ordered along the side. */
 sidp_status sidp_set_ghost_state(sidp_ctx* ctx, int side, const double* u);
+
+/* Parameters of a SIDP_BC_SPLIT side (0 W, 1 E, 2 S, 3 N), as in the double Mach reflection
+ * (Sec. 5.7: a prescribed post-shock state that turns into a slip wall along the bottom, and a
+ * top boundary state that switches at the exact position of the moving incident shock).  At a
+ * face node whose coordinate along the side (y on W/E, x on S/N) is below s0 + speed * t, the
+ * ghost state is state_a (float64 [nc], conserved variables), elsewhere state_b, or a slip wall
+ * (the mirrored trace, Euler only) when state_b is NULL.  t is the stage time: t^n for the time
+ * step and stage 1, t^n + dt for stage 2, t^n + dt/2 for stage 3 (SSP-RK3); sidp_step advances
+ * t^n, explicit sidp_stage calls use the current simulated time as t^n.  Until set, a split side
+ * behaves as outflow.  SIDP_ERR_STATE if the side is not a split side; the values are copied
+ * (synchronous).  Not available in batches. */
+sidp_status sidp_set_split_boundary(sidp_ctx* ctx, int side, double s0, double speed, const double* state_a,
+                                    const double* state_b);
+
+/* Set the simulated time (for example to resume from a saved state); ordered on the stream. */
+sidp_status sidp_set_time(sidp_ctx* ctx, double t);
 
 /* Lend the device buffer of u^n: *dptr = device pointer of [nc][N] values of type *dtype
  * (0 float64, 1 float32); *field_stride = N.  Valid until sidp_destroy. */

@@ -16,9 +16,16 @@ using namespace sidp;
 namespace {
 
 // ---------------------------------------------------------------- small kernels
-__global__ void k_set_scalar(double* dst, double v) {
+// dt of an explicit stage call; stage 1 also takes the clock as the time base of the step.
+__global__ void k_set_scalar(double* dst, double v, int step_start) {
   dst[0] = v;
   *reinterpret_cast<float*>(dst + 2) = (float)v;
+  if (step_start) dst[3] = dst[1];
+}
+
+__global__ void k_set_time(double* dst, double t) {
+  dst[1] = t;
+  dst[3] = t;
 }
 
 // dt = cfl * min (Eq. cfl-low with the CFL constant); 0 when no wave moves; advances the clock
@@ -28,7 +35,10 @@ __global__ void k_dt_finalize(unsigned long long* bits, double cfl, double* dt, 
   const double v = (mn < DBL_MAX) ? cfl * mn : 0.0;
   dt[0] = v;
   *reinterpret_cast<float*>(dt + 2) = (float)v;
-  if (clock) *clock += v;
+  if (clock) {
+    dt[3] = *clock;  // t^n: the time base of the step's stages
+    *clock += v;
+  }
   *bits = (unsigned long long)__double_as_longlong(DBL_MAX);
 }
 
@@ -106,7 +116,8 @@ struct sidp_ctx {
   bool own_stream = false;
   void* d_u[3] = {nullptr, nullptr, nullptr};  // u^n, u^(1), u^(2)
   void* d_ghost[4] = {nullptr, nullptr, nullptr, nullptr};
-  double* d_scal = nullptr;  // [0] dt, [1] clock, [2] dt as float32
+  double* d_scal = nullptr;  // [0] dt, [1] clock, [2] dt as float32, [3] time at the step's start
+  void* d_split = nullptr;   // SplitBC<T>[4]
   unsigned long long* d_bits = nullptr;
   StageStats* d_stats = nullptr;
   double* d_dbg = nullptr;  // 4 * N
@@ -139,7 +150,7 @@ sidp_status fail(sidp_ctx* c, sidp_status s, const std::string& msg) {
       return fail(ctx, SIDP_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));         \
   } while (0)
 
-// d_scal layout: [0] dt (float64), [1] simulated time, [2] dt as float32 (low 4 bytes)
+// d_scal layout: [0] dt (float64), [1] simulated time, [2] dt as float32 (low 4 bytes), [3] t^n
 template <typename T> const T* dt_ptr(const sidp_ctx* c);
 template <> const double* dt_ptr<double>(const sidp_ctx* c) { return c->d_scal; }
 template <> const float* dt_ptr<float>(const sidp_ctx* c) { return reinterpret_cast<const float*>(c->d_scal + 2); }
@@ -159,6 +170,9 @@ void fill_launch(const sidp_ctx* c, StageLaunch<T>& L) {
   L.inst.x0 = T(c->cfg.x0);
   L.inst.y0 = T(c->cfg.y0);
   L.inst.dt = c->d_scal;
+  L.inst.split = static_cast<const SplitBC<T>*>(c->d_split);
+  L.inst.tnow = c->d_scal + 3;
+  L.inst.ck = 0.0;
   L.inst.dtT = dt_ptr<T>(c);
   for (int i = 0; i < c->n; ++i) { L.tab.w[i] = T(c->w[i]); L.tab.xi[i] = T(c->xi[i]); }
   for (int i = 0; i < c->n * c->n; ++i) L.tab.D[i] = T(c->D[i]);
@@ -217,6 +231,7 @@ cudaError_t run_stage_t(sidp_ctx* c, int k) {
   if (k == 1) { L.inst.uin = un; L.inst.u0 = un; L.inst.uout = u1; L.inst.c0 = T(0); L.inst.c1 = T(1); }
   else if (k == 2) { L.inst.uin = u1; L.inst.u0 = un; L.inst.uout = u2; L.inst.c0 = T(0.75); L.inst.c1 = T(0.25); }
   else { L.inst.uin = u2; L.inst.u0 = un; L.inst.uout = un; L.inst.c0 = T(1.0 / 3.0); L.inst.c1 = T(2.0 / 3.0); }
+  L.inst.ck = (k == 1) ? 0.0 : (k == 2) ? 1.0 : 0.5;  // SSP-RK3 stage times t^n + ck dt
   return dispatch<T>(c->cfg.law, c->cfg.p, c->tile, L, nullptr, c->stream);
 }
 
@@ -227,6 +242,7 @@ cudaError_t run_dt_t(sidp_ctx* c, bool advance_clock) {
   StageLaunch<T> L;
   fill_launch(c, L);
   L.inst.uin = static_cast<const T*>(c->d_u[0]);
+  L.inst.tnow = c->d_scal + 1;  // the time step is taken at t^n (the clock before it advances)
   cudaError_t e = dispatch<T>(c->cfg.law, c->cfg.p, c->tile, L, c->d_bits, c->stream);
   if (e != cudaSuccess) return e;
   k_dt_finalize<<<1, 1, 0, c->stream>>>(c->d_bits, c->cfg.cfl, c->d_scal, advance_clock ? c->d_scal + 1 : nullptr);
@@ -291,7 +307,7 @@ int tuned_tile(int law, int p, int mixed) {
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
   tune_table_init();
-  if (law < 1 || law > 3 || p < 1 || p > kMaxP || mixed < 0 || mixed > 1) return -1;
+  if (law < 1 || law > LAW_ADVECTION_VAR || p < 1 || p > kMaxP || mixed < 0 || mixed > 1) return -1;
   return g_tune[law][p][mixed];
 }
 }  // namespace sidp
@@ -358,7 +374,7 @@ sidp_status validate_config(const sidp_config* cfg, std::string& msg) {
   const double hx = (cfg->x1 - cfg->x0) / cfg->nx, hy = (cfg->y1 - cfg->y0) / cfg->ny;
   if (!(hx > 0) || !(hy > 0) || std::fabs(hx - hy) > 1e-12 * hx) { msg = "elements must be square with positive size"; return SIDP_ERR_ARG; }
   for (int s = 0; s < 4; ++s) {
-    if (cfg->bc[s] < 0 || cfg->bc[s] > 3) { msg = "unknown boundary condition"; return SIDP_ERR_ARG; }
+    if (cfg->bc[s] < 0 || cfg->bc[s] > 4) { msg = "unknown boundary condition"; return SIDP_ERR_ARG; }
     if (cfg->bc[s] == SIDP_BC_SLIP_WALL && cfg->law != SIDP_LAW_EULER2D) { msg = "slip walls need the Euler law"; return SIDP_ERR_ARG; }
   }
   if ((cfg->bc[0] == SIDP_BC_PERIODIC) != (cfg->bc[1] == SIDP_BC_PERIODIC) ||
@@ -400,6 +416,23 @@ sidp_status download(sidp_ctx* c, const void* src, double* dst, long long count)
   return SIDP_OK;
 }
 
+}  // namespace
+
+namespace {
+template <typename T>
+SplitBC<T> make_split(double s0, double speed, const double* a, const double* b, int nc) {
+  SplitBC<T> sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.s0 = s0;
+  sp.speed = speed;
+  for (int f = 0; f < nc; ++f) {
+    sp.a[f] = T(a[f]);
+    sp.b[f] = b ? T(b[f]) : T(0);
+  }
+  sp.wall_b = b ? 0 : 1;
+  sp.set = 1;
+  return sp;
+}
 }  // namespace
 
 extern "C" {
@@ -449,7 +482,8 @@ sidp_status sidp_create(sidp_ctx** out, const sidp_config* cfg, void* cuda_strea
       cudaMalloc(&c->d_stats, sizeof(StageStats)) != cudaSuccess ||
       cudaMalloc(&c->d_wtab, kMaxN * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&c->d_part, kDiagBlocks * kDiagK * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&c->d_diag, kDiagK * sizeof(double)) != cudaSuccess)
+      cudaMalloc(&c->d_diag, kDiagK * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->d_split, 4 * (c->mixed ? sizeof(SplitBC<float>) : sizeof(SplitBC<double>))) != cudaSuccess)
     return bail(SIDP_ERR_OOM, "scratch allocation failed");
   double zero2[4] = {0.0, 0.0, 0.0, 0.0};
   const unsigned long long big = (unsigned long long)0x7fefffffffffffffULL;  // DBL_MAX bits
@@ -458,7 +492,8 @@ sidp_status sidp_create(sidp_ctx** out, const sidp_config* cfg, void* cuda_strea
       (e = cudaMemcpy(c->d_bits, &big, sizeof(big), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(c->d_stats, &zs, sizeof(zs), cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(c->d_wtab, c->w, kMaxN * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemset(c->d_u[0], 0, bytes)) != cudaSuccess)
+      (e = cudaMemset(c->d_u[0], 0, bytes)) != cudaSuccess ||
+      (e = cudaMemset(c->d_split, 0, 4 * (c->mixed ? sizeof(SplitBC<float>) : sizeof(SplitBC<double>)))) != cudaSuccess)
     return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
   *out = c;
   return SIDP_OK;
@@ -471,6 +506,7 @@ sidp_status sidp_destroy(sidp_ctx* c) {
   for (int i = 0; i < 3; ++i) cudaFree(c->d_u[i]);
   for (int s = 0; s < 4; ++s) cudaFree(c->d_ghost[s]);
   cudaFree(c->d_scal);
+  cudaFree(c->d_split);
   cudaFree(c->d_bits);
   cudaFree(c->d_stats);
   cudaFree(c->d_dbg);
@@ -557,6 +593,32 @@ sidp_status sidp_set_ghost_state(sidp_ctx* c, int side, const double* u) {
   return c->mixed ? upload<float>(c, c->d_ghost[side], u, count) : upload<double>(c, c->d_ghost[side], u, count);
 }
 
+
+sidp_status sidp_set_split_boundary(sidp_ctx* c, int side, double s0, double speed, const double* state_a,
+                                    const double* state_b) {
+  if (!c || side < 0 || side > 3 || !state_a) return fail(c, SIDP_ERR_ARG, "bad argument");
+  if (c->cfg.bc[side] != SIDP_BC_SPLIT) return fail(c, SIDP_ERR_STATE, "the side is not a split side");
+  if (!state_b && c->cfg.law != SIDP_LAW_EULER2D) return fail(c, SIDP_ERR_ARG, "a slip-wall part needs the Euler law");
+  if (std::isnan(s0) || !std::isfinite(speed)) return fail(c, SIDP_ERR_ARG, "split point must be a number, speed finite");
+  for (int f = 0; f < c->nc; ++f)
+    if (!std::isfinite(state_a[f]) || (state_b && !std::isfinite(state_b[f]))) return fail(c, SIDP_ERR_NONFINITE, "non-finite state");
+  if (c->mixed) {
+    const SplitBC<float> sp = make_split<float>(s0, speed, state_a, state_b, c->nc);
+    CUDA_TRY(c, cudaMemcpy(static_cast<SplitBC<float>*>(c->d_split) + side, &sp, sizeof(sp), cudaMemcpyHostToDevice));
+  } else {
+    const SplitBC<double> sp = make_split<double>(s0, speed, state_a, state_b, c->nc);
+    CUDA_TRY(c, cudaMemcpy(static_cast<SplitBC<double>*>(c->d_split) + side, &sp, sizeof(sp), cudaMemcpyHostToDevice));
+  }
+  return SIDP_OK;
+}
+
+sidp_status sidp_set_time(sidp_ctx* c, double t) {
+  if (!c || !std::isfinite(t)) return fail(c, SIDP_ERR_ARG, "bad argument");
+  k_set_time<<<1, 1, 0, c->stream>>>(c->d_scal, t);
+  CUDA_TRY(c, cudaGetLastError());
+  return SIDP_OK;
+}
+
 sidp_status sidp_device_state(sidp_ctx* c, void** dptr, int* dtype, long long* stride) {
   if (!c || !dptr) return fail(c, SIDP_ERR_ARG, "null argument");
   *dptr = c->d_u[0];
@@ -578,7 +640,7 @@ sidp_status sidp_stage(sidp_ctx* c, int k, double dt) {
   if (k < 1 || k > 3) return fail(c, SIDP_ERR_ARG, "stage must be 1, 2 or 3");
   if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(c, SIDP_ERR_ARG, "dt must be finite and >= 0");
   if (k != 1 && c->stage_done != k - 1) return fail(c, SIDP_ERR_STATE, "stages must run in the order 1, 2, 3");
-  k_set_scalar<<<1, 1, 0, c->stream>>>(c->d_scal, dt);
+  k_set_scalar<<<1, 1, 0, c->stream>>>(c->d_scal, dt, k == 1 ? 1 : 0);
   CUDA_TRY(c, cudaGetLastError());
   CUDA_TRY(c, run_stage(c, k));
   c->stage_done = (k == 3) ? 0 : k;

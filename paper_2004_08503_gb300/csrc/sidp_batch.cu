@@ -235,7 +235,8 @@ sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int cou
         cfgs[i].si_gmin != cfgs[0].si_gmin || cfgs[i].si_gmax != cfgs[0].si_gmax)
       return bfail(nullptr, SIDP_ERR_ARG, "all instances of a batch share law, precision, limiter, law and smoothness parameters");
     for (int s = 0; s < 4; ++s)
-      if (cfgs[i].bc[s] == SIDP_BC_EXACT_STATE) return bfail(nullptr, SIDP_ERR_ARG, "exact-state sides are not supported in batches");
+      if (cfgs[i].bc[s] == SIDP_BC_EXACT_STATE || cfgs[i].bc[s] == SIDP_BC_SPLIT)
+        return bfail(nullptr, SIDP_ERR_ARG, "exact-state and split sides are not supported in batches");
     if (cfgs[i].unsparsified) return bfail(nullptr, SIDP_ERR_ARG, "the unsparsified comparison mode is not supported in batches");
   }
   sidp_batch* b = new sidp_batch();

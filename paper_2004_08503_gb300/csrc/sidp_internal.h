@@ -92,6 +92,17 @@ struct StageStats {
   double field_scale;  // max |u| of the limited field at the last host set_state (violation floor)
 };
 
+// Moving two-state ghost of one side (the boundaries of the double Mach reflection, Sec. 5.7): the
+// ghost state is a where the coordinate along the side (y on W/E, x on S/N) is below
+// s0 + speed t (t the stage time), else b, or the mirrored trace (a slip wall) when wall_b.
+template <typename T>
+struct SplitBC {
+  double s0, speed;
+  T a[4], b[4];
+  int wall_b;
+  int set;  // 0 until sidp_set_split_boundary: the side then behaves as outflow
+};
+
 // One problem instance as seen by the kernels.
 template <typename T>
 struct Instance {
@@ -108,6 +119,9 @@ struct Instance {
   T hT;              // h in the stage precision
   T x0, y0;          // lower-left corner of the domain (node positions)
   T c0, c1;          // RK combination uout = c0 u0 + c1 FE(uin)
+  const SplitBC<T>* split;  // per side (split sides only), or null
+  const double* tnow;       // time base of the launch (device scalar)
+  double ck;                // stage time = *tnow + ck * dt
   // debug outputs (null = off), per node
   double* dbg_lo;
   double* dbg_hi;

@@ -97,9 +97,11 @@ struct DtSmem {
 // Trace of the neighbouring element across `side` (0 W, 1 E, 2 S, 3 N) of element (ex, ey) at
 // position `pos` along the face.  Periodic wraps; outflow (reading: ghost = interior trace) copies
 // the element's own trace node; exact-state reads the ghost buffer; a slip wall (Sec. 5.7) mirrors
-// the own trace node (normal momentum negated).
+// the own trace node (normal momentum negated); a split side takes one of two states (or the
+// mirror) by the node's position against a moving split point.  xi: Gauss-Lobatto points on [0,1].
 template <int P, int NC, typename T>
-__device__ __forceinline__ void neighbor_trace(const Instance<T>& I, int side, int ex, int ey, int pos, T* out) {
+__device__ __forceinline__ void neighbor_trace(const Instance<T>& I, int side, int ex, int ey, int pos, const T* xi,
+                                               T* out) {
   constexpr int n = P + 1, NN = n * n;
   const long long e = (long long)ey * I.nx + ex;
   long long ne = -1;
@@ -119,6 +121,24 @@ __device__ __forceinline__ void neighbor_trace(const Instance<T>& I, int side, i
     const long long along = (side < 2) ? ey : ex;
 #pragma unroll
     for (int f = 0; f < NC; ++f) out[f] = I.ghost[side][(f * nside + along) * n + pos];
+  } else if (bc == 4 && I.split != nullptr && I.split[side].set) {
+    // split side: state a below the moving split point, b (or the wall mirror) above it; decided
+    // in float64 from the face node's coordinate along the side and the stage time
+    const SplitBC<T>& sp = I.split[side];
+    const double c = (side < 2) ? (double)I.y0 + I.h * ((double)ey + (double)xi[pos])
+                                : (double)I.x0 + I.h * ((double)ex + (double)xi[pos]);
+    const double t = *I.tnow + I.ck * *I.dt;
+    if (c < sp.s0 + sp.speed * t) {
+#pragma unroll
+      for (int f = 0; f < NC; ++f) out[f] = sp.a[f];
+    } else if (!sp.wall_b) {
+#pragma unroll
+      for (int f = 0; f < NC; ++f) out[f] = sp.b[f];
+    } else {
+#pragma unroll
+      for (int f = 0; f < NC; ++f) out[f] = I.uin[f * I.N + e * NN + own];
+      if constexpr (NC == 4) out[side < 2 ? 1 : 2] = -out[side < 2 ? 1 : 2];
+    }
   } else {
 #pragma unroll
     for (int f = 0; f < NC; ++f) out[f] = I.uin[f * I.N + e * NN + own];
@@ -177,7 +197,7 @@ __device__ __forceinline__ void halo_load(const Instance<T>& I, const Tables<T>&
     py = I.y0 + hh * T(side == 2 ? ey0 : ey0 + TY);
   }
   if (ex < I.nx && ey < I.ny) {
-    neighbor_trace<P, NC>(I, side, ex, ey, along, uu);
+    neighbor_trace<P, NC>(I, side, ex, ey, along, tab.xi, uu);
   } else {
 #pragma unroll
     for (int f = 0; f < NC; ++f) uu[f] = I.uin[f * I.N + ((long long)ey0 * I.nx + ex0) * NN];
@@ -212,9 +232,9 @@ __device__ __forceinline__ bool load_tile(S& s, const Instance<T>& I, const Tabl
 #pragma unroll
       for (int f = 0; f < NC; ++f) uu[f] = I.uin[f * I.N + g];
     } else if (ey < I.ny) {
-      neighbor_trace<P, NC>(I, 1, I.nx - 1, ey, a, uu);  // east of the mesh: ghost of the last element
+      neighbor_trace<P, NC>(I, 1, I.nx - 1, ey, a, tab.xi, uu);  // east of the mesh: ghost of the last element
     } else if (ex < I.nx) {
-      neighbor_trace<P, NC>(I, 3, ex, I.ny - 1, b, uu);  // north of the mesh
+      neighbor_trace<P, NC>(I, 3, ex, I.ny - 1, b, tab.xi, uu);  // north of the mesh
     } else {
 #pragma unroll
       for (int f = 0; f < NC; ++f) uu[f] = I.uin[f * I.N + ((long long)ey0 * I.nx + ex0) * NN];

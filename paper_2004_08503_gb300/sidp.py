@@ -18,7 +18,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "sidp.h")
 
 LAWS = {"burgers": 1, "euler": 2, "advection": 3, "advection_var": 4}
 PRECISIONS = {"fp64": 0, "mixed": 1}
-BCS = {"periodic": 0, "outflow": 1, "exact": 2, "wall": 3}
+BCS = {"periodic": 0, "outflow": 1, "exact": 2, "wall": 3, "split": 4}
 LIMITERS = {"none": 0, "lo": 1, "subcell": 2, "elementwise": 3}
 SIDES = {"W": 0, "E": 1, "S": 2, "N": 3}
 
@@ -59,6 +59,8 @@ _SIGS = {
     "sidp_set_state": (ctypes.c_int, [_P, _D]),
     "sidp_get_state": (ctypes.c_int, [_P, ctypes.c_int, _D]),
     "sidp_set_ghost_state": (ctypes.c_int, [_P, ctypes.c_int, _D]),
+    "sidp_set_split_boundary": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D]),
+    "sidp_set_time": (ctypes.c_int, [_P, ctypes.c_double]),
     "sidp_upload_state": (ctypes.c_int, [_P, _P]),
     "sidp_download_state": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "sidp_device_state": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]),
@@ -202,6 +204,22 @@ def sidp_download_state(ctx, which, host_ptr):
 def sidp_set_ghost_state(ctx, side, u):
     u = np.ascontiguousarray(u, dtype=np.float64)
     _check(load().sidp_set_ghost_state(ctx, SIDES.get(side, side), _ptr(u)), ctx)
+
+
+SIDES = {"W": 0, "E": 1, "S": 2, "N": 3}
+
+
+def sidp_set_split_boundary(ctx, side, s0, speed, state_a, state_b=None):
+    """side: 0..3 or "W", "E", "S", "N"; state_b None: a slip wall on that part."""
+    side = SIDES.get(side, side)
+    a = np.ascontiguousarray(state_a, dtype=np.float64)
+    b = None if state_b is None else np.ascontiguousarray(state_b, dtype=np.float64)
+    _check(load().sidp_set_split_boundary(ctx, int(side), ctypes.c_double(s0), ctypes.c_double(speed), _ptr(a),
+                                          _ptr(b) if b is not None else None), ctx)
+
+
+def sidp_set_time(ctx, t):
+    _check(load().sidp_set_time(ctx, ctypes.c_double(t)), ctx)
 
 
 def sidp_device_state(ctx):
@@ -368,6 +386,12 @@ class Solver:
 
     def set_ghost(self, side, u):
         sidp_set_ghost_state(self.ctx, side, u)
+
+    def set_split(self, side, s0, speed, a, b=None):
+        sidp_set_split_boundary(self.ctx, side, s0, speed, a, b)
+
+    def set_time(self, t):
+        sidp_set_time(self.ctx, t)
 
     def compute_dt(self):
         return sidp_compute_dt(self.ctx)
