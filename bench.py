@@ -309,6 +309,65 @@ def run_batched(torch, sidp, stream, steps, warmup, seed=0, count=512):
             f"p in {{2..7}} (seed {seed}), four-quadrant data, mixed precision, one CUDA graph per step, degree groups on concurrent graph branches"}
 
 
+def run_dmr(sidp, nx, t_end, image=None, chunk=100, max_seconds=600.0):
+    """The double Mach reflection of Sec. 5.7 on nx x nx/4 elements of [0,4] x [0,1], p = 3, mixed
+    precision, to t_end (the paper runs 2400 x 600 to t = 0.275).  Split boundaries: post-shock
+    inflow (west), post-shock then slip wall from x = 1/6 (south), the moving incident shock
+    (north), outflow (east).  Reports throughput, invariants and where the incident shock meets the
+    top boundary against its exact position; `image`: element-mean density as a binary PGM."""
+    import time
+    from paper_2004_08503_gb300 import inputs
+    ny = nx // 4
+    sv = sidp.Solver(law="euler", p=3, nx=nx, ny=ny, precision="mixed", domain=(0.0, 4.0, 0.0, 1.0),
+                     bc=("split", "outflow", "split", "split"))
+    for side, sp in inputs.double_mach_boundaries().items():
+        sv.set_split(side, sp["s0"], sp["speed"], sp["a"], sp["b"])
+    x, y = sv.node_coords()
+    sv.set_state(inputs.double_mach(x, y))
+    sv.set_stats(True)
+    steps, t = 0, 0.0
+    sv.synchronize()
+    t0 = time.perf_counter()
+    stop = "t_end reached"
+    while t < t_end:
+        sv.step(chunk)
+        steps += chunk
+        d = sv.diag()
+        if d["nonfinite"] or not d["t"] > t:
+            stop = "stopped: non-finite state or time not advancing"
+            t = d["t"]
+            break
+        t = d["t"]
+        if steps % (50 * chunk) == 0:
+            print(f"dmr: {steps} steps, t = {t:.5f}, {time.perf_counter() - t0:.1f} s", file=sys.stderr, flush=True)
+        if time.perf_counter() - t0 > max_seconds:
+            stop = f"stopped at the {max_seconds:.0f} s wall-clock cap"
+            break
+    sec = time.perf_counter() - t0
+    d = sv.diag()
+    u = sv.get_state(0)
+    top = np.abs(y - 1.0) < 1e-12
+    order = np.argsort(x[top])
+    xs, rs = x[top][order], u[0][top][order]
+    cross = float(xs[np.argmax(rs < 0.5 * (inputs.DMR_PRE[0] + inputs.DMR_POST[0]))])
+    if image:
+        rho = u[0].reshape(ny, nx, 16).mean(axis=2)[::-1]
+        lo_, hi_ = float(rho.min()), float(rho.max())
+        g = np.clip((rho - lo_) / max(hi_ - lo_, 1e-30) * 255.0, 0, 255).astype(np.uint8)
+        with open(image, "wb") as f:
+            f.write(b"P5\n%d %d\n255\n" % (nx, ny))
+            f.write(g.tobytes())
+    out = {"elements": [nx, ny], "p": 3, "nodes": sv.N, "t": t, "steps": steps, "seconds": sec,
+           "value": sv.N * 3 * steps / sec, "unit": UNIT, "rho_min": d["rho_min"], "p_min": d["p_min"],
+           "rho_max": float(u[0].max()), "max_bound_violation": d["max_bound_violation"],
+           "max_entropy_violation": d["max_entropy_violation"], "rootfind_cap_hits": d["rootfind_cap_hits"],
+           "nonfinite": d["nonfinite"], "top_shock_x": cross, "top_shock_x_exact": float(inputs.dmr_shock_x(1.0, t)),
+           "element_width": 4.0 / nx, "end": stop,
+           "timing": "wall clock around sidp_step and diag calls (every %d steps)" % chunk}
+    sv.close()
+    return out
+
+
 def run_accuracy(sidp, stream, stages=200):
     """Mixed (float32) against float64 after `stages` RK stages on the two mixed-precision
     configurations (256x256 p=3 and 128x128 p=7, seeded four-quadrant data, outflow).  The float64
@@ -349,6 +408,10 @@ def main():
     ap.add_argument("--nel", type=int, default=NEL, help="elements per side (profiling runs only)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched leg")
     ap.add_argument("--accuracy", action="store_true", help="also report mixed-vs-float64 errors (200 stages)")
+    ap.add_argument("--dmr", type=int, default=0, help="also run the double Mach reflection on N x N/4 elements")
+    ap.add_argument("--dmr-t", type=float, default=0.275, help="final time of the double Mach reflection")
+    ap.add_argument("--dmr-image", default=None, help="write its element-mean density as a PGM file")
+    ap.add_argument("--dmr-max-seconds", type=float, default=600.0, help="wall-clock cap of the double Mach run")
     args = ap.parse_args()
     NEL = args.nel
     if args.impl == "reference":
@@ -418,6 +481,7 @@ def main():
     if not args.no_batched:
         batched = run_batched(torch, sidp, stream, steps=max(10, args.steps // 4), warmup=2)
     accuracy = run_accuracy(sidp, stream) if args.accuracy else None
+    dmr = run_dmr(sidp, args.dmr, args.dmr_t, args.dmr_image, max_seconds=args.dmr_max_seconds) if args.dmr else None
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -434,7 +498,7 @@ def main():
                              "traffic": traffic, "kernel": "k_stage<3, LawEuler<float>, float>",
                              "stage_ms": [1e3 * t for t in kt], "peak_kind": peak_kind,
                              "whole_step_gbs": step_gbs, "whole_step_frac": step_gbs / hbm},
-                "fp64": fp64, "batched": batched, "invariants": diag_stats, "accuracy": accuracy,
+                "fp64": fp64, "batched": batched, "invariants": diag_stats, "accuracy": accuracy, "dmr": dmr,
                 "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": 5 * args.steps}
         print(json.dumps(line), flush=True)

@@ -181,6 +181,7 @@ cudaError_t launch_group(sidp_batch* b, int gi, int k, cudaStream_t st) {
     }
     bl.limiter = b->limiter;
     bl.bits = b->d_bits;
+    bl.stats = b->stats_on ? 1 : 0;
     switch (b->law) {
       case LAW_BURGERS: return launch_batch_law<LAW_BURGERS, T>(gr.p, gr.tile, bl, k == 0, st);
       case LAW_EULER: return launch_batch_law<LAW_EULER, T>(gr.p, gr.tile, bl, k == 0, st);

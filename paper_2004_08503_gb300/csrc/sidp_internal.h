@@ -28,6 +28,7 @@ struct LawParamsT {
   T beta[2];    // advection velocity (variable-velocity law: its constant part)
   T bxy, byx;   // variable-velocity law: beta = (beta[0] + bxy y, beta[1] + byx x)
   int pow7;     // inv_e == 7 (gamma = 1.4): the float path multiplies instead of calling pow
+  double gamma_d;  // gamma in float64 (statistics)
 };
 
 template <typename T>
@@ -46,6 +47,7 @@ inline LawParamsT<T> make_law_params(double gamma, const double* beta, const dou
   p.bxy = grad ? T(grad[0]) : T(0);
   p.byx = grad ? T(grad[1]) : T(0);
   p.pow7 = (2.0 * g / (g - 1.0) > 7.0 - 1e-12 && 2.0 * g / (g - 1.0) < 7.0 + 1e-12) ? 1 : 0;
+  p.gamma_d = g;
   return p;
 }
 
@@ -135,6 +137,7 @@ struct Instance {
 template <typename T>
 struct BatchLaunch {
   const Instance<T>* insts;  // device array, one per instance
+  int stats;                 // the instances' statistics are on (launch the statistics kernels)
   const int2* tasks;         // device array of (instance, linear tile index)
   int ntasks;
   Tables<T> tab;
@@ -212,6 +215,8 @@ SIDP_DECLARE(LAW_ADVECTION_VAR, float)
     }                                                                                                  \
     if (a.limiter == 3 && !bits) /* elementwise limiting: its own kernel, default tile shape */       \
       return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, true>(a, bits, s);       \
+    if (a.inst.stats && !bits) /* statistics on: the statistics kernel, default tile shape */         \
+      return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, false, false, true>(a, bits, s); \
     switch (tile) {                                                                                    \
       case 0: return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT>(a, bits, s);     \
       case 1: return launch_tile<P, kTiles[P][1].tx, kTiles[P][1].ty, LAWTPL<TT>, TT>(a, bits, s);     \
@@ -224,6 +229,8 @@ SIDP_DECLARE(LAW_ADVECTION_VAR, float)
   cudaError_t launch_batch_p<LAWID, TT, P>(int tile, const BatchLaunch<TT>& b, bool dt, cudaStream_t s) { \
     if (b.limiter == 3 && !dt)                                                                         \
       return launch_batch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, true>(b, dt, s);  \
+    if (b.stats && !dt)                                                                                \
+      return launch_batch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, false, true>(b, dt, s); \
     switch (tile) {                                                                                    \
       case 0: return launch_batch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT>(b, dt, s); \
       case 1: return launch_batch_tile<P, kTiles[P][1].tx, kTiles[P][1].ty, LAWTPL<TT>, TT>(b, dt, s); \

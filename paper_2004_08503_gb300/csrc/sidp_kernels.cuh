@@ -94,6 +94,28 @@ struct DtSmem {
   T nrm[G::n];
 };
 
+// Ghost state of a split side (see SplitBC), decided in the stage precision (float64 in the FP64
+// path; in float32 a node within rounding of the moving split point may take either state).
+// own: the node's own trace.
+template <int P, int NC, typename T>
+__device__ __forceinline__ void split_ghost(const Instance<T>& I, int side, int ex, int ey, int pos, const T* xi,
+                                            const T* own, T* out) {
+  const SplitBC<T>& sp = I.split[side];
+  const T c = (side < 2) ? I.y0 + I.hT * (T(ey) + xi[pos]) : I.x0 + I.hT * (T(ex) + xi[pos]);
+  const T t = T(*I.tnow) + T(I.ck) * *I.dtT;
+  if (c < T(sp.s0) + T(sp.speed) * t) {
+#pragma unroll
+    for (int f = 0; f < NC; ++f) out[f] = sp.a[f];
+  } else if (!sp.wall_b) {
+#pragma unroll
+    for (int f = 0; f < NC; ++f) out[f] = sp.b[f];
+  } else {
+#pragma unroll
+    for (int f = 0; f < NC; ++f) out[f] = own[f * I.N];
+    if constexpr (NC == 4) out[side < 2 ? 1 : 2] = -out[side < 2 ? 1 : 2];
+  }
+}
+
 // Trace of the neighbouring element across `side` (0 W, 1 E, 2 S, 3 N) of element (ex, ey) at
 // position `pos` along the face.  Periodic wraps; outflow (reading: ghost = interior trace) copies
 // the element's own trace node; exact-state reads the ghost buffer; a slip wall (Sec. 5.7) mirrors
@@ -122,23 +144,7 @@ __device__ __forceinline__ void neighbor_trace(const Instance<T>& I, int side, i
 #pragma unroll
     for (int f = 0; f < NC; ++f) out[f] = I.ghost[side][(f * nside + along) * n + pos];
   } else if (bc == 4 && I.split != nullptr && I.split[side].set) {
-    // split side: state a below the moving split point, b (or the wall mirror) above it; decided
-    // in float64 from the face node's coordinate along the side and the stage time
-    const SplitBC<T>& sp = I.split[side];
-    const double c = (side < 2) ? (double)I.y0 + I.h * ((double)ey + (double)xi[pos])
-                                : (double)I.x0 + I.h * ((double)ex + (double)xi[pos]);
-    const double t = *I.tnow + I.ck * *I.dt;
-    if (c < sp.s0 + sp.speed * t) {
-#pragma unroll
-      for (int f = 0; f < NC; ++f) out[f] = sp.a[f];
-    } else if (!sp.wall_b) {
-#pragma unroll
-      for (int f = 0; f < NC; ++f) out[f] = sp.b[f];
-    } else {
-#pragma unroll
-      for (int f = 0; f < NC; ++f) out[f] = I.uin[f * I.N + e * NN + own];
-      if constexpr (NC == 4) out[side < 2 ? 1 : 2] = -out[side < 2 ? 1 : 2];
-    }
+    split_ghost<P, NC>(I, side, ex, ey, pos, xi, I.uin + e * NN + own, out);
   } else {
 #pragma unroll
     for (int f = 0; f < NC; ++f) out[f] = I.uin[f * I.N + e * NN + own];
@@ -375,6 +381,17 @@ __device__ __forceinline__ void warp_max_atomic(T v, unsigned long long* dst) {
   if ((threadIdx.x & 31) == 0 && d > 0.0) atomicMax(dst, (unsigned long long)__double_as_longlong(d));
 }
 
+// Root-search counters of a warp: one atomic per warp (not per thread: on a flow with many
+// limited nodes per-thread atomics on one address serialise).  All 32 lanes call it.
+__device__ __forceinline__ void warp_rootfind_stats(int caps, int iters, StageStats* st) {
+  const unsigned c = __reduce_add_sync(0xffffffffu, (unsigned)caps);
+  const unsigned m = __reduce_max_sync(0xffffffffu, (unsigned)iters);
+  if ((threadIdx.x & 31) == 0) {
+    if (c) atomicAdd(&st->rootfind_cap_hits, (unsigned long long)c);
+    if (m) atomicMax(&st->rootfind_max_iters, m);
+  }
+}
+
 // Euler: largest t in [0, tcap] with u^L + t w in {rho > 0, psi_K >= min(0, psi_K(u^L))} for the
 // single direction w (elementwise limiting, Eq. convex-provisional-elementwise).
 template <class LAW, typename T>
@@ -388,12 +405,84 @@ __device__ T entropy_limit_dir(const T* uL, T K, const T* w, T tcap, const LawPa
   return entropy_root<LAW>(uL, w, K, LAW::psi(uL, K, lp), target, tcap, lp, iters, caps);
 }
 
+// Slots of the four neighbours of node slot t = (le, a, b) at tile position (row, col):
+// within the element, across an element face inside the tile, or in the halo.
+template <int P, int TX, int TY>
+struct Nbr {
+  using G = TileGeom<P, TX, TY>;
+  static constexpr int n = P + 1, NN = n * n;
+  __device__ __forceinline__ static int left(int t, int b, int row, int col) {
+    return (col == 0) ? G::hW + row : t - ((b == 0) ? NN - P : 1);
+  }
+  __device__ __forceinline__ static int right(int t, int b, int row, int col) {
+    return (col == G::NX - 1) ? G::hE + row : t + ((b == P) ? NN - P : 1);
+  }
+  __device__ __forceinline__ static int down(int t, int a, int row, int col) {
+    return (row == 0) ? G::hS + col : t - ((a == 0) ? TX * NN - P * n : n);
+  }
+  __device__ __forceinline__ static int up(int t, int a, int row, int col) {
+    return (row == G::NY - 1) ? G::hN + col : t + ((a == P) ? TX * NN - P * n : n);
+  }
+};
+
+// Entropy-bound violation of a limited result fe at node slot me, measured in float64:
+// max(0, 1 - sigma(fe) / K_i) with K_i = min sigma over the node and its four neighbours of the
+// stage input (still in shared memory), all sigma evaluated in float64 from the stored values.  The
+// float32 path's own sigma and K carry the rounding of its fast intrinsics; this measures the
+// result against the exact bound of its input.  Statistics only.
+template <int P, int TX, int TY, class LAW, typename T, class S>
+__device__ __forceinline__ double entropy_violation64(const S& s, int me, int a, int b, int row, int col, const T* fe,
+                                                      const LawParamsT<T>& lp) {
+  auto sig = [&](const T* u) {
+    const double r = (double)u[0];
+    const double rhoe = (double)u[3] - 0.5 * ((double)u[1] * (double)u[1] + (double)u[2] * (double)u[2]) / r;
+    return rhoe * pow(r, -lp.gamma_d);
+  };
+  using N4 = Nbr<P, TX, TY>;
+  double K = sig(s.u[me].v);
+  K = fmin(K, sig(s.u[N4::left(me, b, row, col)].v));
+  K = fmin(K, sig(s.u[N4::right(me, b, row, col)].v));
+  K = fmin(K, sig(s.u[N4::down(me, a, row, col)].v));
+  K = fmin(K, sig(s.u[N4::up(me, a, row, col)].v));
+  if (!((double)fe[0] > 0.0)) return 1.0;
+  return fmax(0.0, 1.0 - sig(fe) / K);
+}
+
+// Stage statistics of one node (all lanes of the warp call it): the limited field's excess over its
+// local bounds relative to max(|bound|, field scale), the entropy-bound violation (float64 measure on
+// the float32 path), and the root-search counters; warp-reduced, one atomic per warp and quantity.
+template <int P, int TX, int TY, class LAW, typename T, bool DENSE, class S>
+__device__ __forceinline__ void stage_stats(const S& s, const Instance<T>& I, const LawParamsT<T>& lp, bool on,
+                                         Vec<T, LAW::NC> fe, T lo, T hi, T K, int caps, int iters, int me, int a, int b,
+                                         int row, int col) {
+  T v = T(0), ev = T(0);
+  if (on) {
+    // relative to the local bound, floored at the field's magnitude (bounds that are zero up to
+    // rounding would otherwise turn rounding into large relative values)
+    const T scale = tmax(tmax(fabs(lo), fabs(hi)), T(I.stats->field_scale));
+    v = tmax(lo - fe.v[0], fe.v[0] - hi);
+    v = (v > T(0)) ? fdiv(v, scale > T(0) ? scale : T(1)) : T(0);
+    if constexpr (LAW::kEntropy) {
+      if constexpr (sizeof(T) == 4 && !DENSE) {
+        ev = T(entropy_violation64<P, TX, TY, LAW, T>(s, me, a, b, row, col, fe.v, lp));
+      } else {
+        const T sg = LAW::sigma_of(fe.v, lp);
+        ev = tmax(T(0), T(1) - sg / K);
+        if (!(fe.v[0] > T(0))) ev = T(1);
+      }
+    }
+  }
+  warp_rootfind_stats(caps, iters, I.stats);
+  warp_max_atomic(v, &I.stats->max_bound_violation);
+  warp_max_atomic(ev, &I.stats->max_entropy_violation);
+}
+
 // Elementwise limiting (Sec. 4.1.2 linear, Sec. 4.2.1 convex constraints): alpha-tilde_i is the
 // largest coefficient in [0,1] keeping u^L_i + alpha (dt/m_i) r_i, r_i = sum_k (r^H_ik - r^L_ik),
 // inside the bounds of the limited field (Zalesak with the single flux r_i) and, for Euler, in
 // the entropy set; every node of element K then takes alpha_K = min over K.  Writes u^FE with
 // the SSP-RK3 combination and the stage statistics.
-template <int P, int TX, int TY, class LAW, typename T, class S>
+template <int P, int TX, int TY, class LAW, typename T, bool DENSE, class S>
 __device__ __forceinline__ void elementwise_update(S& s, const Instance<T>& I, const LawParamsT<T>& lp, bool slot, bool act,
                                                 bool move, long long g, int le, int me, int a, int b, const T* uL,
                                                 const T* rx, const T* ry, T lo, T hi, T K, T m, T dt, T dtm) {
@@ -445,44 +534,14 @@ __device__ __forceinline__ void elementwise_update(S& s, const Instance<T>& I, c
         I.uout[q * N + g] = (I.c0 == T(0)) ? fe[q] : I.c0 * I.u0[q * N + g] + I.c1 * fe[q];
     }
   }
-  if (I.stats) {
-    T v = T(0), ev = T(0);
-    if (act && move) {
-      const T scale = tmax(tmax(fabs(lo), fabs(hi)), T(I.stats->field_scale));
-      v = tmax(lo - fe[0], fe[0] - hi);
-      v = (v > T(0)) ? fdiv(v, scale > T(0) ? scale : T(1)) : T(0);
-      if constexpr (LAW::kEntropy) {
-        const T sg = LAW::sigma_of(fe, lp);
-        ev = tmax(T(0), T(1) - sg / K);
-        if (!(fe[0] > T(0))) ev = T(1);
-      }
-      if (caps) atomicAdd(&I.stats->rootfind_cap_hits, (unsigned long long)caps);
-      if (iters) atomicMax(&I.stats->rootfind_max_iters, (unsigned int)iters);
-    }
-    warp_max_atomic(v, &I.stats->max_bound_violation);
-    warp_max_atomic(ev, &I.stats->max_entropy_violation);
+  if (I.stats) {  // statistics, out of line
+    Vec<T, NC> vf;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) vf.v[q] = fe[q];
+    stage_stats<P, TX, TY, LAW, T, DENSE>(s, I, lp, act && move, vf, lo, hi, K, caps, iters, me, a, b,
+                                          (le / TX) * n + a, (le % TX) * n + b);
   }
 }
-
-// Slots of the four neighbours of node slot t = (le, a, b) at tile position (row, col):
-// within the element, across an element face inside the tile, or in the halo.
-template <int P, int TX, int TY>
-struct Nbr {
-  using G = TileGeom<P, TX, TY>;
-  static constexpr int n = P + 1, NN = n * n;
-  __device__ __forceinline__ static int left(int t, int b, int row, int col) {
-    return (col == 0) ? G::hW + row : t - ((b == 0) ? NN - P : 1);
-  }
-  __device__ __forceinline__ static int right(int t, int b, int row, int col) {
-    return (col == G::NX - 1) ? G::hE + row : t + ((b == P) ? NN - P : 1);
-  }
-  __device__ __forceinline__ static int down(int t, int a, int row, int col) {
-    return (row == 0) ? G::hS + col : t - ((a == 0) ? TX * NN - P * n : n);
-  }
-  __device__ __forceinline__ static int up(int t, int a, int row, int col) {
-    return (row == G::NY - 1) ? G::hN + col : t + ((a == P) ? TX * NN - P * n : n);
-  }
-};
 
 // Face along +e_k between the left/lower slot L (read from shared memory) and a right/upper state
 // given in registers; writes the face flux and the bar state of field 0 at index fi.
@@ -549,7 +608,7 @@ __device__ __forceinline__ void dense_line(const S& s, int k, int base, int stri
 
 // ELW selects elementwise limiting at compile time (its kernels are separate instantiations, so
 // the subcell kernels carry none of its code).
-template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool DENSE = false>
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool DENSE = false, bool STATS = true>
 __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const Instance<T>& I, const Tables<T>& tab,
                                            const LawParamsT<T>& lp, int limiter, const SmoothnessT<T>& si, int tile_x,
                                            int tile_y) {
@@ -727,7 +786,7 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
   }
   if (limiter < 2) return;  // uniform across the CTA
   if constexpr (ELW) {      // elementwise limiting (Sec. 4.1.2, 4.2.1)
-    elementwise_update<P, TX, TY, LAW, T>(s, I, lp, slot, act, move, g, le, me, a, b, uL, rx, ry, lo, hi, K, m, dt, dtm);
+    elementwise_update<P, TX, TY, LAW, T, DENSE>(s, I, lp, slot, act, move, g, le, me, a, b, uL, rx, ry, lo, hi, K, m, dt, dtm);
     return;
   }
   // ---------------- D: subcell fluxes and nodal alpha-tilde
@@ -832,35 +891,24 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
       for (int q = 0; q < NC; ++q) I.uout[q * N + g] = (I.c0 == T(0)) ? fe[q] : I.c0 * u0[q] + I.c1 * fe[q];
     }
   }
-  if (I.stats) {
-    T v = T(0), ev = T(0);
-    if (act && move) {
-      // relative to the local bound, floored at the field's magnitude (bounds that are zero up to
-      // rounding would otherwise turn rounding into large relative values)
-      const T scale = tmax(tmax(fabs(lo), fabs(hi)), T(I.stats->field_scale));
-      v = tmax(lo - fe[0], fe[0] - hi);
-      v = (v > T(0)) ? fdiv(v, scale > T(0) ? scale : T(1)) : T(0);
-      if constexpr (LAW::kEntropy) {
-        const T sg = LAW::sigma_of(fe, lp);
-        ev = tmax(T(0), T(1) - sg / K);
-        if (!(fe[0] > T(0))) ev = T(1);
-      }
-      if (caps) atomicAdd(&I.stats->rootfind_cap_hits, (unsigned long long)caps);
-      if (iters) atomicMax(&I.stats->rootfind_max_iters, (unsigned int)iters);
-    }
-    warp_max_atomic(v, &I.stats->max_bound_violation);
-    warp_max_atomic(ev, &I.stats->max_entropy_violation);
+  if (STATS && I.stats) {  // statistics: compiled only into the statistics kernels
+    Vec<T, NC> vf;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) vf.v[q] = fe[q];
+    stage_stats<P, TX, TY, LAW, T, DENSE>(s, I, lp, act && move, vf, lo, hi, K, caps, iters, me, a, b, row, col);
   }
 }
 
-template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool DENSE = false>
+// STATS: a kernel with the per-stage statistics (launched when they are on); the timed kernels
+// carry none of their code.
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool DENSE = false, bool STATS = false>
 __global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
 k_stage(const StageLaunch<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto& s = *reinterpret_cast<TileSmem<P, TX, TY, LAW, T>*>(smem_raw);
   const int tiles_x = (A.inst.nx + TX - 1) / TX;
   const int tile_y = blockIdx.x / tiles_x, tile_x = blockIdx.x - tile_y * tiles_x;
-  stage_body<P, TX, TY, LAW, T, ELW, DENSE>(s, A.inst, A.tab, A.lp, A.limiter, A.si, tile_x, tile_y);
+  stage_body<P, TX, TY, LAW, T, ELW, DENSE, STATS || ELW || DENSE>(s, A.inst, A.tab, A.lp, A.limiter, A.si, tile_x, tile_y);
 }
 
 // Copy the instance descriptor of this CTA's task into shared memory (all threads help).
@@ -875,7 +923,7 @@ __device__ __forceinline__ void load_instance(Instance<T>& dst, const Instance<T
 
 // Batched stage: CTA blockIdx.x runs task (instance, tile) of the task table; all tasks of one
 // launch share P, the tile shape, law and precision.
-template <int P, int TX, int TY, class LAW, typename T, bool ELW = false>
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool STATS = false>
 __global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
 k_stage_batch(const BatchLaunch<T> B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -885,7 +933,7 @@ k_stage_batch(const BatchLaunch<T> B) {
   load_instance(sI, B.insts + task.x);
   const int tiles_x = (sI.nx + TX - 1) / TX;
   const int tile_y = task.y / tiles_x, tile_x = task.y - tile_y * tiles_x;
-  stage_body<P, TX, TY, LAW, T, ELW>(s, sI, B.tab, B.lp, B.limiter, B.si, tile_x, tile_y);
+  stage_body<P, TX, TY, LAW, T, ELW, false, STATS || ELW>(s, sI, B.tab, B.lp, B.limiter, B.si, tile_x, tile_y);
 }
 
 // CFL bound of Eq. cfl-low per node, m_i / (2 sum_{j != i} d-hat_ij) with d-hat = (h w / 2) lambda on
@@ -999,14 +1047,14 @@ k_dt_batch(const BatchLaunch<T> B) {
   dt_body<P, TX, TY, LAW, T>(s, sI, B.tab, B.lp, tile_x, tile_y, B.bits + task.x);
 }
 
-template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool DENSE = false>
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool DENSE = false, bool STATS = false>
 cudaError_t launch_tile(const StageLaunch<T>& a, unsigned long long* dt_bits, cudaStream_t s) {
   using G = TileGeom<P, TX, TY>;
   constexpr size_t smem = sizeof(TileSmem<P, TX, TY, LAW, T>);
   constexpr size_t smem_dt = sizeof(DtSmem<P, TX, TY, LAW, T>);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(k_stage<P, TX, TY, LAW, T, ELW, DENSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = cudaFuncSetAttribute(k_stage<P, TX, TY, LAW, T, ELW, DENSE, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(k_dt<P, TX, TY, LAW, T, DENSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dt);
     if (err != cudaSuccess) return err;
@@ -1015,18 +1063,18 @@ cudaError_t launch_tile(const StageLaunch<T>& a, unsigned long long* dt_bits, cu
   const long long tiles = (long long)((a.inst.nx + TX - 1) / TX) * ((a.inst.ny + TY - 1) / TY);
   if (tiles <= 0) return cudaSuccess;
   if (dt_bits) k_dt<P, TX, TY, LAW, T, DENSE><<<(unsigned)tiles, G::THREADS, smem_dt, s>>>(a, dt_bits);
-  else k_stage<P, TX, TY, LAW, T, ELW, DENSE><<<(unsigned)tiles, G::THREADS, smem, s>>>(a);
+  else k_stage<P, TX, TY, LAW, T, ELW, DENSE, STATS><<<(unsigned)tiles, G::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int P, int TX, int TY, class LAW, typename T, bool ELW = false>
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool STATS = false>
 cudaError_t launch_batch_tile(const BatchLaunch<T>& B, bool dt, cudaStream_t s) {
   using G = TileGeom<P, TX, TY>;
   constexpr size_t smem = sizeof(TileSmem<P, TX, TY, LAW, T>);
   constexpr size_t smem_dt = sizeof(DtSmem<P, TX, TY, LAW, T>);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(k_stage_batch<P, TX, TY, LAW, T, ELW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = cudaFuncSetAttribute(k_stage_batch<P, TX, TY, LAW, T, ELW, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(k_dt_batch<P, TX, TY, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dt);
     if (err != cudaSuccess) return err;
@@ -1034,7 +1082,7 @@ cudaError_t launch_batch_tile(const BatchLaunch<T>& B, bool dt, cudaStream_t s) 
   }
   if (B.ntasks <= 0) return cudaSuccess;
   if (dt) k_dt_batch<P, TX, TY, LAW, T><<<(unsigned)B.ntasks, G::THREADS, smem_dt, s>>>(B);
-  else k_stage_batch<P, TX, TY, LAW, T, ELW><<<(unsigned)B.ntasks, G::THREADS, smem, s>>>(B);
+  else k_stage_batch<P, TX, TY, LAW, T, ELW, STATS><<<(unsigned)B.ntasks, G::THREADS, smem, s>>>(B);
   return cudaGetLastError();
 }
 
