@@ -425,19 +425,16 @@ struct Nbr {
   }
 };
 
-// Entropy-bound violation of a limited result fe at node slot me, measured in float64:
-// max(0, 1 - sigma(fe) / K_i) with K_i = min sigma over the node and its four neighbours of the
-// stage input (still in shared memory), all sigma evaluated in float64 from the stored values.  The
-// float32 path's own sigma and K carry the rounding of its fast intrinsics; this measures the
-// result against the exact bound of its input.  Statistics only.
+// Entropy-bound violation of a limited result fe at node slot me: max(0, 1 - sigma(fe) / K_i) with
+// K_i = min sigma over the node and its four neighbours of the stage input (still in shared
+// memory).  sigma is evaluated accurately - compensated rho e (a few ulp even where kinetic energy
+// dominates) and the correctly rounding-class powf (not the fast intrinsic), the ratio in
+// float64 - so that the statistic measures the result against the bound of its input to a few
+// 1e-7, not the ~1e-6 rounding of the limiter's fast float32 evaluation.  Statistics only.
 template <int P, int TX, int TY, class LAW, typename T, class S>
 __device__ __forceinline__ double entropy_violation64(const S& s, int me, int a, int b, int row, int col, const T* fe,
                                                       const LawParamsT<T>& lp) {
-  auto sig = [&](const T* u) {
-    const double r = (double)u[0];
-    const double rhoe = (double)u[3] - 0.5 * ((double)u[1] * (double)u[1] + (double)u[2] * (double)u[2]) / r;
-    return rhoe * pow(r, -lp.gamma_d);
-  };
+  auto sig = [&](const T* u) { return (double)LAW::rhoe(u) * (double)powf(u[0], -lp.gamma); };
   using N4 = Nbr<P, TX, TY>;
   double K = sig(s.u[me].v);
   K = fmin(K, sig(s.u[N4::left(me, b, row, col)].v));
