@@ -206,8 +206,8 @@ sidp_status sidp_get_tile(const sidp_ctx* ctx, int* tx, int* ty);
 /* Enable (1) or disable (0) CUDA-graph replay in sidp_step (default 1). */
 sidp_status sidp_set_graph(sidp_ctx* ctx, int use_graph);
 
-/* Enable (1) / disable (0) the per-stage statistics of sidp_diag (default 1): bound and entropy
- * violations and root-search counters.  With them on, a statistics variant of the stage kernel
+/* Enable (1) / disable (0) the per-stage statistics reported in sidp_diag, on by default: bound
+ * and entropy violations and root-search counters.  With them on, a statistics variant of the stage kernel
  * runs (default tile shape); in the float32 form it evaluates the entropy bound accurately and
  * costs about 2.5x a plain stage.  Turn them off for timed runs. */
 sidp_status sidp_set_stats(sidp_ctx* ctx, int on);
