@@ -37,6 +37,12 @@ UNIT = "node-updates/s"
 # ncu on the 768x768 p=3 blast (profiles/k_stage_euler_mixed_p3.md).  The counters belong to the
 # stage kernel as committed with that profile; a changed kernel needs a new capture.
 STAGE_DRAM_BYTES_PER_NODE = 39.4
+# Executed FP32 flops (2 x FFMA + FADD + FMUL) and warp instructions per node of stages 1, 2, 3
+# from the InstructionStats counters of the same capture: the two other ceilings of the stage
+# kernel, reported beside the HBM roofline (the kernel is bound by instruction issue).
+STAGE_FP32_FLOP_PER_NODE = (691.0, 449.0, 449.0)
+STAGE_WARP_INSTR_PER_NODE = (36.3, 28.4, 28.4)
+SMS, FP32_LANES_PER_SM, SCHEDULERS_PER_SM = 152, 128, 4
 NEL, P = 1024, 3
 WORKLOAD = "2D Euler blast, 1024x1024 elements, p=3 (16.8M nodes x 4 fields), outflow, CFL 0.5, subcell convex limiting"
 HBM_FALLBACK = 6800.0
@@ -149,6 +155,23 @@ def time_steps(torch, sv, stream, steps, warmup, dist=None, clocks_gpu=None):
         clk.__exit__()
     sec = max_over_ranks(torch, ev0.elapsed_time(ev1) / 1e3, dist, "cuda")
     return sec, (clk.summary() if clk else None)
+
+
+def other_ceilings(nodes, kt, clk):
+    """FP32 pipe and instruction-issue fractions of the stage kernel at the sampled SM clock."""
+    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz")
+    if not mhz or not all(kt):
+        return None
+    hz = 1e6 * float(mhz)
+    flops = sum(f * nodes for f in STAGE_FP32_FLOP_PER_NODE) / sum(kt)
+    issue = sum(w * nodes for w in STAGE_WARP_INSTR_PER_NODE) / sum(kt)
+    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * hz
+    issue_peak = SMS * SCHEDULERS_PER_SM * hz
+    return {"sm_mhz": float(mhz),
+            "fp32": {"achieved": flops / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                     "frac": flops / fp32_peak, "flop_per_node": list(STAGE_FP32_FLOP_PER_NODE)},
+            "issue": {"achieved": issue / 1e12, "peak": issue_peak / 1e12, "unit": "T warp-instr/s",
+                      "frac": issue / issue_peak, "warp_instr_per_node": list(STAGE_WARP_INSTR_PER_NODE)}}
 
 
 def stage_kernel_times(torch, sv, stream, reps):
@@ -503,7 +526,8 @@ def main():
                 "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                              "traffic": traffic, "kernel": "k_stage<3, LawEuler<float>, float>",
                              "stage_ms": [1e3 * t for t in kt], "peak_kind": peak_kind,
-                             "whole_step_gbs": step_gbs, "whole_step_frac": step_gbs / hbm},
+                             "whole_step_gbs": step_gbs, "whole_step_frac": step_gbs / hbm,
+                             "other_ceilings": other_ceilings(nodes, kt, clk)},
                 "fp64": fp64, "batched": batched, "invariants": diag_stats, "accuracy": accuracy, "dmr": dmr,
                 "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": 5 * args.steps}
