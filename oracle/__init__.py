@@ -14,8 +14,10 @@ Modules
   laws    -- physical laws: constant advection, 2D Burgers, 2D Euler (Sec. 4.3, Eq. euler-eos/flux)
   scheme  -- HO residual, LO IDP residual, bar states, bounds, subcell FCT/convex limiter,
              CFL time step, SSP-RK3 (Sec. 2-4)
+  curved  -- curved (mapped) quadrilateral meshes: metric terms, face normals, the conservative
+             metric correction of Sec. 3.1 and the residuals on mapped elements
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 (closed forms, invariants, textbook special cases, brute force); none is "parity unpinned".
 """
-from . import gll, laws, scheme  # noqa: F401
+from . import curved, gll, laws, scheme  # noqa: F401

@@ -112,6 +112,11 @@ class Problem:
             self.BX, self.BY = law.velocity(X, Y)
 
     # ------------------------------------------------------------------ geometry
+    def _mass(self, elems):
+        """m_i of the nodes of `elems`, broadcastable against (len(elems), n*n): on a Cartesian
+        mesh every element has the same masses, so a single row (1, n*n)."""
+        return self.mass[None, :]
+
     def node_coords(self):
         """Physical coordinates (Ne, n*n) of all nodes."""
         n, nx = self.n, self.nx
@@ -329,7 +334,7 @@ class Problem:
         tot = self.sum_dhat(U)
         # a node with sum d-hat = 0 (a stagnation point of a velocity field) puts no limit on dt
         with np.errstate(divide="ignore"):
-            return self.cfl * float(np.min(self.mass[None, :] / (2.0 * tot)))
+            return self.cfl * float(np.min(self._mass(None) / (2.0 * tot)))
 
     # ------------------------------------------------------------------ limiting
     def bounds(self, U, bars, elems):
@@ -418,7 +423,7 @@ class Problem:
                            np.where(sK > s0 + kap, 1.0, 0.5 + 0.5 * np.sin(np.pi * (sK - s0) / (2.0 * kap))))
         return eps, sK
 
-    def zalesak(self, uL, lo, hi, rbar, dt, field=0):
+    def zalesak(self, uL, lo, hi, rbar, dt, field=0, elems=None):
         """Nodal alpha-tilde from the sums of positive and negative parts of the adjacent
         subcell fluxes (Sec. 4.1.3), Zalesak-style.
 
@@ -430,14 +435,14 @@ class Problem:
         c = np.stack([xp[field], -xm[field], yp[field], -ym[field]])
         Pp = np.sum(np.maximum(c, 0.0), axis=0)
         Pm = np.sum(np.minimum(c, 0.0), axis=0)
-        m = self.mass[None, :]
+        m = self._mass(elems)
         Qp = np.maximum(0.0, m / dt * (hi - uL[field]))
         Qm = np.minimum(0.0, m / dt * (lo - uL[field]))
         Rp = np.where(Pp > 0, np.minimum(1.0, Qp / np.where(Pp > 0, Pp, 1.0)), 1.0)
         Rm = np.where(Pm < 0, np.minimum(1.0, Qm / np.where(Pm < 0, Pm, -1.0)), 1.0)
         return np.minimum(Rp, Rm)
 
-    def entropy_limit(self, uL, K, rbar, dt, amax, iters=80):
+    def entropy_limit(self, uL, K, rbar, dt, amax, iters=80, elems=None):
         """Largest t in [0, amax] with every candidate of Eq. (convex-provisional),
         u^L + gamma_d t (dt/m_i)(+-r-bar_{m_i^+-,k}), gamma_d = 2d = 4, in the entropy set (Sec. 4.3).
 
@@ -446,7 +451,7 @@ class Problem:
         so along a candidate the admissible t form an interval [0, t*]; t* is found by bisection.
         """
         xp, xm, yp, ym = self._node_face_fluxes(rbar)
-        scale = 4.0 * dt / self.mass[None, :]
+        scale = 4.0 * dt / self._mass(elems)
         return self.entropy_line_search(uL, K, [scale[None] * v for v in (xp, -xm, yp, -ym)], amax, iters)
 
     def entropy_line_search(self, uL, K, dirs, amax, iters=80):
@@ -474,7 +479,7 @@ class Problem:
             t_all = np.minimum(t_all, t)
         return t_all
 
-    def elementwise_alpha(self, uL, lo, hi, K, rn, dt):
+    def elementwise_alpha(self, uL, lo, hi, K, rn, dt, elems=None):
         """Elementwise limiting (Sec. 4.1.2 linear, Sec. 4.2.1 convex constraints).
 
         alpha-tilde_i is the largest value in [0,1] for which u^L_i + alpha (dt/m_i) r_i, with the
@@ -484,7 +489,7 @@ class Problem:
         (Eq. convex-provisional-elementwise, one candidate, no gamma_d factor).  Every node of the
         element then takes alpha_K = min of alpha-tilde over the element.  Returns (Ne, 1).
         """
-        m = self.mass[None, :]
+        m = self._mass(elems)
         r0 = rn[0]
         Pp = np.maximum(r0, 0.0)
         Pm = np.minimum(r0, 0.0)
@@ -503,7 +508,7 @@ class Problem:
         limiter = self.limiter if limiter is None else limiter
         elems = np.arange(self.Ne) if elems is None else np.asarray(elems)
         Ue = U[:, elems]
-        m = self.mass[None, None, :]
+        m = self._mass(elems)[None]
         rH = self.ho_residual(U, elems)
         rL, bars, dij, dface = self.lo_residual(U, elems, want_bars=True)
         uH = Ue + dt / m * (rH[0] + rH[1])
@@ -520,7 +525,7 @@ class Problem:
                 lo = eps[:, None] * lo + (1.0 - eps[:, None]) * self.smoothness["gmin"]
                 hi = eps[:, None] * hi + (1.0 - eps[:, None]) * self.smoothness["gmax"]
             rn = (rH[0] + rH[1]) - (rL[0] + rL[1])
-            aK, at = self.elementwise_alpha(uL, lo, hi, K, rn, dt)
+            aK, at = self.elementwise_alpha(uL, lo, hi, K, rn, dt, elems)
             out = uL + dt / m * aK[None] * rn
             info.update({"lo": lo, "hi": hi, "K": K, "alpha_tilde": at, "alpha_K": aK[:, 0], "rn": rn})
         elif limiter == "subcell":
@@ -532,9 +537,9 @@ class Problem:
                 eps, _ = self.smoothness_factor(U, elems)
                 lo = eps[:, None] * lo + (1.0 - eps[:, None]) * self.smoothness["gmin"]
                 hi = eps[:, None] * hi + (1.0 - eps[:, None]) * self.smoothness["gmax"]
-            at = self.zalesak(uL, lo, hi, rbar, dt)
+            at = self.zalesak(uL, lo, hi, rbar, dt, elems=elems)
             if self.law.name == "euler":
-                at = self.entropy_limit(uL, K, rbar, dt, at)
+                at = self.entropy_limit(uL, K, rbar, dt, at, elems=elems)
             n = self.n
             ne = len(elems)
             A = at.reshape(ne, n, n)
@@ -586,4 +591,4 @@ class Problem:
 
     def total_mass(self, U):
         """sum_i m_i u_i per field (Sec. 2.4, conservation)."""
-        return np.sum(U * self.mass[None, None, :], axis=(1, 2))
+        return np.sum(U * self._mass(None)[None], axis=(1, 2))

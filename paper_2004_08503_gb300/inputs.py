@@ -27,6 +27,12 @@ Recipes (all float64):
                      to the wall; pre-shock (rho, v, p) = (1.4, 0, 1), post-shock (8, 8.25 (cos 30,
                      -sin 30), 116.5); the shock line at time t is x = 1/6 + (y + 20 t)/sqrt(3)
   batch_shapes       seeded (elements per side, p) pairs of a batch of independent problems
+
+Curved-mesh node coordinates (the caller maps the nodes of a Cartesian mesh; shared face nodes
+of neighbouring elements get identical coordinates since they map the same point):
+  warped_coords      x = X + eps Lx s, y = Y + eps Ly s, s = sin(2 pi X/Lx) sin(2 pi Y/Ly) on
+                     [0,Lx] x [0,Ly] (a periodic displacement; eps <= 0.1 keeps det J > 0)
+  rotated_coords     rotation of (X, Y) by theta about (xc, yc)
 """
 import numpy as np
 
@@ -169,3 +175,13 @@ def batch_shapes(seed, count=512, sides=(8, 16, 32, 64), degrees=(2, 3, 4, 5, 6,
     nel = rng.choice(np.array(sides), size=count)
     ps = rng.choice(np.array(degrees), size=count)
     return [(int(a), int(b)) for a, b in zip(nel, ps)]
+
+
+def warped_coords(X, Y, eps=0.05, L=(1.0, 1.0)):
+    s = np.sin(2.0 * np.pi * X / L[0]) * np.sin(2.0 * np.pi * Y / L[1])
+    return X + eps * L[0] * s, Y + eps * L[1] * s
+
+
+def rotated_coords(X, Y, theta, xc=0.5, yc=0.5):
+    c, s = np.cos(theta), np.sin(theta)
+    return xc + c * (X - xc) - s * (Y - yc), yc + s * (X - xc) + c * (Y - yc)

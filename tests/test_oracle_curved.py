@@ -1,0 +1,192 @@
+"""Pins of the oracle's curved-mesh operators (Sec. 2.3 metric terms, Sec. 3.1 conservative
+correction) against what the paper and the mathematics fix: rotation equivariance against the
+Cartesian oracle, free-stream preservation with and without the correction, conservation, the
+minimum-norm property of the correction and its O(h) size, the invariant domain of the low-order
+update, and the design order of the high-order operator."""
+import numpy as np
+import pytest
+
+from oracle import laws, scheme
+from oracle.curved import CurvedProblem
+from paper_2004_08503_gb300 import inputs
+
+G = 1.4
+
+
+def _cart(law, p, nx, ny, bc=("periodic",) * 4, L=(1.0, 1.0), **kw):
+    return scheme.Problem(law, p, nx, ny, domain=(0.0, L[0], 0.0, L[1]), bc=bc, **kw)
+
+
+def _warped(law, p, nx, ny, eps=0.08, bc=("periodic",) * 4, L=(1.0, 1.0), **kw):
+    X, Y = _cart(law, p, nx, ny, L=L).node_coords()
+    Xw, Yw = inputs.warped_coords(X, Y, eps, L)
+    return CurvedProblem(law, p, nx, ny, Xw, Yw, bc=bc, **kw)
+
+
+def _rotate_momentum(U, th):
+    c, s = np.cos(th), np.sin(th)
+    V = U.copy()
+    V[1], V[2] = c * U[1] - s * U[2], s * U[1] + c * U[2]
+    return V
+
+
+@pytest.mark.parametrize("limiter", ["none", "lo", "subcell"])
+@pytest.mark.parametrize("p", [2, 3])
+def test_cartesian_coordinates_reproduce_the_cartesian_oracle(p, limiter):
+    law = laws.Euler(G)
+    pc = _cart(law, p, 4, 3, L=(1.0, 0.75), limiter=limiter)
+    X, Y = pc.node_coords()
+    cu = CurvedProblem(law, p, 4, 3, X, Y, limiter=limiter)
+    assert np.max(np.abs(cu.C)) < 1e-14
+    U = inputs.four_quadrant(X, Y, 3)
+    a, da = pc.ssp_rk3_step(U)
+    b, db = cu.ssp_rk3_step(U)
+    assert db == pytest.approx(da, rel=1e-13)
+    np.testing.assert_allclose(b, a, rtol=0, atol=1e-13 * np.abs(a).max())
+
+
+@pytest.mark.parametrize("limiter", ["none", "subcell"])
+@pytest.mark.parametrize("theta", [0.3, 2.0])
+def test_rotated_mesh_gives_the_rotated_solution(theta, limiter):
+    """The Euler equations, the Lax-Friedrichs flux, lambda_max, the bounds and the entropy are
+    invariant under rotation: on the rotated image of a Cartesian mesh (outflow sides), with the
+    rotated data, one SSP-RK3 step equals the rotated Cartesian step.  This fixes the orientation
+    of every metric row, face normal and pair coefficient."""
+    law = laws.Euler(G)
+    bc = ("outflow",) * 4
+    pc = _cart(law, 3, 4, 4, bc=bc, limiter=limiter)
+    X, Y = pc.node_coords()
+    U = inputs.four_quadrant(X, Y, 5)
+    Xr, Yr = inputs.rotated_coords(X, Y, theta)
+    cu = CurvedProblem(law, 3, 4, 4, Xr, Yr, bc=bc, limiter=limiter)
+    assert np.max(np.abs(cu.C)) < 1e-14                      # affine elements: no correction
+    a, da = pc.ssp_rk3_step(U)
+    b, db = cu.ssp_rk3_step(_rotate_momentum(U, theta))
+    assert db == pytest.approx(da, rel=1e-12)
+    np.testing.assert_allclose(b, _rotate_momentum(a, theta), rtol=0, atol=1e-12 * np.abs(a).max())
+
+
+def test_rotated_mesh_advection():
+    beta = np.array([0.8, -0.3])
+    th = 0.7
+    c, s = np.cos(th), np.sin(th)
+    pc = _cart(laws.Advection(beta), 2, 5, 5, bc=("outflow",) * 4)
+    X, Y = pc.node_coords()
+    U = inputs.burgers_pulse(X, Y)
+    Xr, Yr = inputs.rotated_coords(X, Y, th)
+    cu = CurvedProblem(laws.Advection((c * beta[0] - s * beta[1], s * beta[0] + c * beta[1])), 2, 5, 5,
+                       Xr, Yr, bc=("outflow",) * 4)
+    a, da = pc.ssp_rk3_step(U)
+    b, db = cu.ssp_rk3_step(U)
+    assert db == pytest.approx(da, rel=1e-12)
+    np.testing.assert_allclose(b, a, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 5, 7])
+def test_free_stream_preservation_needs_the_correction(p):
+    """Sec. 2.4 / Sec. 3.1: with the metric identity (2D cross-product metrics) the strong form
+    preserves constants; the sparse low-order operator preserves them only with the corrected
+    metric terms of Eq. (metric-perturbation)."""
+    law = laws.Euler(G)
+    cw = _warped(law, p, 4, 3, L=(1.0, 0.75))
+    X, Y = cw.node_coords()
+    Uc = inputs.constant_state(X, Y)
+    scale = np.abs(Uc).max() * np.abs(cw.R1).max()
+    rh, rl = cw.ho_residual(Uc), cw.lo_residual(Uc)
+    assert np.abs(rh[0] + rh[1]).max() < 1e-13 * scale
+    assert np.abs(rl[0] + rl[1]).max() < 1e-13 * scale
+    cn = _warped(law, p, 4, 3, L=(1.0, 0.75), correct=False)
+    rn = cn.lo_residual(Uc)
+    if p >= 2:   # at p = 1 the sparse operator is the full one: nothing to correct
+        assert np.abs(rn[0] + rn[1]).max() > 1e-4 * scale
+    # a whole limited step keeps the constant state
+    out, _ = cw.ssp_rk3_step(Uc)
+    np.testing.assert_allclose(out, Uc, rtol=1e-13)
+
+
+@pytest.mark.parametrize("p", [2, 4, 6])
+def test_correction_is_the_minimum_norm_solution(p):
+    """Eq. (idp-sbp) holds after the correction, and C is the minimum-norm solution of
+    Eq. (metric-perturbation): compared with the solution of the regularised normal equations
+    A^T (A A^T + 1 1^T / NN)^-1 rhs (a route without the SVD; the right-hand side sums to zero)."""
+    cw = _warped(laws.Euler(G), p, 3, 3, eps=0.1)
+    NN = cw.n * cw.n
+    A = np.hstack([cw.DhX.T, cw.DhY.T])
+    M = A @ A.T + np.ones((NN, NN)) / NN
+    for j in (0, 1):
+        bnd = np.zeros((cw.Ne, NN))
+        for s in scheme.SIDES:
+            bnd[:, cw.fnodes[s]] += cw.fw[s][None, :] * cw.nface[s][j]
+        lhs = cw.Q1[j] @ cw.DhX + cw.Q2[j] @ cw.DhY
+        assert np.abs(lhs - bnd).max() < 1e-14
+        rhs = bnd - (cw.R1[j] @ cw.DhX + cw.R2[j] @ cw.DhY)
+        assert np.abs(rhs.sum(axis=1)).max() < 1e-14          # solvable (metric identity)
+        sol = np.linalg.solve(M, rhs.T).T @ A                    # rows: A^T y
+        np.testing.assert_allclose(np.concatenate([cw.C[0, j], cw.C[1, j]], axis=1), sol, atol=1e-13)
+
+
+def test_correction_shrinks_with_h():
+    """Sec. 3.1: the correction is O(h) (it is smaller still on a smooth map: the sparse operator
+    differentiates the metric terms to first order, and they vary by O(h) across an element)."""
+    sizes = []
+    for nx in (4, 8, 16):
+        cw = _warped(laws.Euler(G), 3, nx, nx, eps=0.05)
+        sizes.append(np.abs(cw.C).max())
+    assert sizes[1] < sizes[0] / 1.8 and sizes[2] < sizes[1] / 1.8
+
+
+def test_conservation_on_a_periodic_curved_mesh():
+    law = laws.Euler(G)
+    cw = _warped(law, 3, 4, 3, L=(1.0, 0.75))
+    X, Y = cw.node_coords()
+    U = inputs.four_quadrant(X, Y, 7)
+    m0 = cw.total_mass(U)
+    for _ in range(3):
+        U, _ = cw.ssp_rk3_step(U)
+    np.testing.assert_allclose(cw.total_mass(U), m0, rtol=1e-14, atol=1e-14 * np.abs(m0).max())
+
+
+@pytest.mark.parametrize("law", [laws.Burgers(), laws.Advection((1.0, 0.5))])
+def test_low_order_update_is_a_convex_combination(law):
+    """Eq. (convex-combination) on curved elements: at dt from Eq. (cfl-low) every low-order
+    state lies between the node's value and its bar states (local maximum principle)."""
+    cw = _warped(law, 3, 4, 4, eps=0.1, limiter="lo")
+    X, Y = cw.node_coords()
+    U = inputs.burgers_pulse(X, Y)
+    dt = cw.compute_dt(U)
+    out, info = cw.fe_stage(U, dt, full=True)
+    lo, hi, _ = cw.bounds(U, info["bars"], np.arange(cw.Ne))
+    tol = 1e-13 * np.abs(U).max()
+    assert np.all(out[0] >= lo - tol) and np.all(out[0] <= hi + tol)
+
+
+def test_limited_euler_stage_keeps_the_bounds():
+    law = laws.Euler(G)
+    cw = _warped(law, 3, 4, 4, eps=0.1, bc=("outflow",) * 4)
+    X, Y = cw.node_coords()
+    U = inputs.four_quadrant(X, Y, 11)
+    dt = cw.compute_dt(U)
+    out, info = cw.fe_stage(U, dt, full=True)
+    tol = 1e-12 * np.abs(U[0]).max()
+    assert np.all(out[0] >= info["lo"] - tol) and np.all(out[0] <= info["hi"] + tol)
+    s = law.sigma(out)
+    assert np.all(out[0] > 0) and np.all(s >= info["K"] * (1 - 1e-10))
+
+
+def test_high_order_operator_converges_at_the_design_order():
+    """Smooth advection on the warped periodic mesh, unlimited strong form: the error falls like
+    h^(p+1) (p = 2: slope about 3)."""
+    beta = (1.0, 0.5)
+    law = laws.Advection(beta)
+    errs = []
+    for nx in (6, 12):
+        cw = _warped(law, 2, nx, nx, eps=0.05, limiter="none")
+        X, Y = cw.node_coords()
+        U = np.sin(2 * np.pi * (X + Y))[None]
+        T = 0.1
+        while cw.time < T - 1e-14:
+            U, _ = cw.ssp_rk3_step(U, min(0.5 * cw.compute_dt(U), T - cw.time))
+        exact = np.sin(2 * np.pi * (X - beta[0] * T + Y - beta[1] * T))
+        errs.append(np.sum(cw.mK * np.abs(U[0] - exact)))
+    rate = np.log2(errs[0] / errs[1])
+    assert rate > 2.6, (errs, rate)
