@@ -1,6 +1,6 @@
 /*
  * libsidp -- sparse invariant-domain-preserving DG-SEM stage update with subcell
- * convex limiting on Cartesian quadrilateral meshes (Pazner, arXiv 2004.08503),
+ * convex limiting on Cartesian and curved quadrilateral meshes (Pazner, arXiv 2004.08503),
  * for NVIDIA GB300 (sm_103a).  Plain C ABI: pointers and sizes only.
  *
  * Method (one forward-Euler stage, Sec. 4, Eq. subcell-fct / convex-fct):
@@ -166,6 +166,39 @@ sidp_status sidp_set_split_boundary(sidp_ctx* ctx, int side, double s0, double s
 
 /* Set the simulated time (for example to resume from a saved state); ordered on the stream. */
 sidp_status sidp_set_time(sidp_ctx* ctx, double t);
+
+/* Curved (mapped) quadrilateral meshes: Sec. 2.3 (metric terms G = det J and the rows of
+ * G J^-1 at the nodes, masses m_i = w_a w_b G_i, strong-form residual with contravariant fluxes)
+ * and Sec. 3.1 (the conservative metric correction, the minimum-norm solution of
+ * Eq. metric-perturbation, which makes the sparse low-order operator preserve constants).
+ * The mesh keeps the nx x ny element topology and node order of the Cartesian mesh; each node
+ * has its own coordinates.  Number of per-node arrays written by sidp_curved_metrics: */
+#define SIDP_GEO_FIELDS 13
+
+/* Metric arrays of the curved mesh whose nodes sit at (x[g], y[g]), float64 [N] each in library
+ * node order (the two elements of a face give its nodes the same coordinates; across a periodic
+ * side they differ by the period).  bc: the four side conditions, periodic or outflow.  Computed
+ * on the host in float64; needs no GPU.  out: float64 [SIDP_GEO_FIELDS][N], caller-owned:
+ *   0-1 row 1 of G J^-1 = (y_eta, -x_eta);  2-3 row 2 = (-y_xi, x_xi)
+ *       (reference derivatives of the interpolated map, xi along b, eta along a);
+ *   4-7 the corrected rows of Sec. 3.1 (row 1, row 2; x and y components);
+ *   8   m_i = w_a w_b G_i;
+ *   9-10 at nodes with b = 0 or p: the scaled normal of that element face pointing in +xi, the
+ *       mean of the two adjacent elements' row 1 (a non-periodic boundary face: the element's
+ *       own); 0 at other nodes;  11-12 the same with a = 0 or p, +eta and row 2.
+ * SIDP_ERR_ARG for invalid sizes or sides, or a node with det J <= 0. */
+sidp_status sidp_curved_metrics(int p, int nx, int ny, const int* bc, const double* x, const double* y,
+                                double* out);
+
+/* Move the context onto the curved mesh with node coordinates x, y (float64 [N] each, copied):
+ * computes the metric arrays as sidp_curved_metrics does and keeps them on the device in the
+ * stage precision; from then on the time step and the stages use the curved-mesh kernels and
+ * sidp_node_coords returns these coordinates.  Supported: laws burgers, advection and euler;
+ * limiters none, lo and subcell; periodic and outflow sides; without the smoothness indicator and
+ * the unsparsified mode (SIDP_ERR_ARG otherwise).  The per-stage violation statistics are not
+ * collected on curved meshes (sidp_get_diag reports them as 0; mass and extrema use m_i).
+ * Synchronous. */
+sidp_status sidp_set_geometry(sidp_ctx* ctx, const double* x, const double* y);
 
 /* Lend the device buffer of u^n: *dptr = device pointer of [nc][N] values of type *dtype
  * (0 float64, 1 float32); *field_stride = N.  Valid until sidp_destroy. */

@@ -1,6 +1,6 @@
 // Stage and time-step kernels of the variable-velocity advection law in double, degrees 1..7
 // (split into translation units so that the build runs in parallel).
-#include "sidp_kernels.cuh"
+#include "sidp_curved.cuh"
 
 namespace sidp {
 SIDP_INSTANTIATE_P(LAW_ADVECTION_VAR, LawAdvectionVar, double, 1)

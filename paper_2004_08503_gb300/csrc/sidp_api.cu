@@ -46,14 +46,14 @@ constexpr int kDiagK = 15;  // mass[4], min[4], max[4], rho_min, p_min, nonfinit
 
 template <typename T>
 __global__ void k_diag_partial(const T* u, long long N, int nc, int n, double h, const double* wtab, double gamma,
-                               int euler, double* part) {
+                               int euler, const double* mnode, double* part) {
   double acc[kDiagK];
   for (int f = 0; f < 4; ++f) { acc[f] = 0.0; acc[4 + f] = DBL_MAX; acc[8 + f] = -DBL_MAX; }
   acc[12] = DBL_MAX; acc[13] = DBL_MAX; acc[14] = 0.0;
   const int NN = n * n;
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
     const int node = (int)(g % NN), a = node / n, b = node % n;
-    const double m = h * h * wtab[a] * wtab[b];
+    const double m = mnode ? mnode[g] : h * h * wtab[a] * wtab[b];
     double v[4] = {0, 0, 0, 0};
     for (int f = 0; f < nc; ++f) {
       v[f] = (double)u[f * N + g];
@@ -124,6 +124,10 @@ struct sidp_ctx {
   double* d_wtab = nullptr;
   double* d_part = nullptr;
   double* d_diag = nullptr;
+  void* d_geo = nullptr;     // curved mesh: [kGeoFields][N] in the stage precision
+  double* d_mass = nullptr;  // curved mesh: m_i in float64 (diagnostics)
+  bool curved = false;
+  std::vector<double> hx, hy;  // curved mesh: node coordinates
   bool debug = false, stats_on = true, use_graph = true;
   int stage_done = 0;
   long long steps = 0;
@@ -174,6 +178,7 @@ void fill_launch(const sidp_ctx* c, StageLaunch<T>& L) {
   L.inst.tnow = c->d_scal + 3;
   L.inst.ck = 0.0;
   L.inst.dtT = dt_ptr<T>(c);
+  L.inst.geo = static_cast<const T*>(c->d_geo);
   for (int i = 0; i < c->n; ++i) { L.tab.w[i] = T(c->w[i]); L.tab.xi[i] = T(c->xi[i]); }
   for (int i = 0; i < c->n * c->n; ++i) L.tab.D[i] = T(c->D[i]);
   L.lp = make_law_params<T>(c->cfg.gamma, c->cfg.adv_beta, c->cfg.adv_grad);
@@ -513,6 +518,8 @@ sidp_status sidp_destroy(sidp_ctx* c) {
   cudaFree(c->d_wtab);
   cudaFree(c->d_part);
   cudaFree(c->d_diag);
+  cudaFree(c->d_geo);
+  cudaFree(c->d_mass);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return SIDP_OK;
@@ -527,6 +534,11 @@ sidp_status sidp_sizes(const sidp_ctx* c, long long* n_nodes, int* nc) {
 
 sidp_status sidp_node_coords(const sidp_ctx* c, double* x, double* y) {
   if (!c || !x || !y) return fail(nullptr, SIDP_ERR_ARG, "null argument");
+  if (c->curved) {
+    std::memcpy(x, c->hx.data(), c->N * sizeof(double));
+    std::memcpy(y, c->hy.data(), c->N * sizeof(double));
+    return SIDP_OK;
+  }
   const int n = c->n;
   for (long long e = 0; e < c->Ne; ++e) {
     const long long ex = e % c->cfg.nx, ey = e / c->cfg.nx;
@@ -609,6 +621,46 @@ sidp_status sidp_set_split_boundary(sidp_ctx* c, int side, double s0, double spe
     const SplitBC<double> sp = make_split<double>(s0, speed, state_a, state_b, c->nc);
     CUDA_TRY(c, cudaMemcpy(static_cast<SplitBC<double>*>(c->d_split) + side, &sp, sizeof(sp), cudaMemcpyHostToDevice));
   }
+  return SIDP_OK;
+}
+
+sidp_status sidp_curved_metrics(int p, int nx, int ny, const int* bc, const double* x, const double* y,
+                                double* out) {
+  std::string msg;
+  const sidp_status st = curved_metrics(p, nx, ny, bc, x, y, out, msg);
+  if (st != SIDP_OK) return fail(nullptr, st, msg);
+  return SIDP_OK;
+}
+
+sidp_status sidp_set_geometry(sidp_ctx* c, const double* x, const double* y) {
+  if (!c || !x || !y) return fail(c, SIDP_ERR_ARG, "null argument");
+  const sidp_config& f = c->cfg;
+  if (f.law == SIDP_LAW_ADVECTION_VAR2D)
+    return fail(c, SIDP_ERR_ARG, "variable-velocity advection is defined on Cartesian meshes only");
+  if (f.limiter == SIDP_LIMITER_ELEMENTWISE || f.smoothness || f.unsparsified)
+    return fail(c, SIDP_ERR_ARG, "curved meshes take the limiters none, lo and subcell, without smoothness or unsparsified modes");
+  for (int k = 0; k < 4; ++k)
+    if (f.bc[k] != SIDP_BC_PERIODIC && f.bc[k] != SIDP_BC_OUTFLOW)
+      return fail(c, SIDP_ERR_ARG, "curved meshes take periodic or outflow sides");
+  std::vector<double> geo((size_t)kGeoFields * c->N);
+  std::string msg;
+  const sidp_status st = curved_metrics(f.p, f.nx, f.ny, f.bc, x, y, geo.data(), msg);
+  if (st != SIDP_OK) return fail(c, st, msg);
+  if (!c->d_geo && cudaMalloc(&c->d_geo, (size_t)kGeoFields * c->N * c->esize) != cudaSuccess)
+    return fail(c, SIDP_ERR_OOM, "geometry allocation failed");
+  if (!c->d_mass && cudaMalloc(&c->d_mass, (size_t)c->N * sizeof(double)) != cudaSuccess)
+    return fail(c, SIDP_ERR_OOM, "geometry allocation failed");
+  const sidp_status su = c->mixed ? upload<float>(c, c->d_geo, geo.data(), (long long)kGeoFields * c->N)
+                                  : upload<double>(c, c->d_geo, geo.data(), (long long)kGeoFields * c->N);
+  if (su != SIDP_OK) return su;
+  CUDA_TRY(c, cudaMemcpy(c->d_mass, geo.data() + (size_t)GEO_MASS_FIELD * c->N, c->N * sizeof(double),
+                         cudaMemcpyHostToDevice));
+  c->hx.assign(x, x + c->N);
+  c->hy.assign(y, y + c->N);
+  c->curved = true;
+  c->tuned = true;  // one kernel shape on curved meshes: nothing to tune
+  c->tile = 0;
+  drop_graph(c);
   return SIDP_OK;
 }
 
@@ -723,9 +775,9 @@ sidp_status sidp_get_diag(sidp_ctx* c, sidp_diag* out) {
   std::memset(out, 0, sizeof(*out));
   const int euler = c->cfg.law == SIDP_LAW_EULER2D;
   if (c->mixed)
-    k_diag_partial<float><<<kDiagBlocks, 256, 0, c->stream>>>(static_cast<const float*>(c->d_u[0]), c->N, c->nc, c->n, c->h, c->d_wtab, c->cfg.gamma, euler, c->d_part);
+    k_diag_partial<float><<<kDiagBlocks, 256, 0, c->stream>>>(static_cast<const float*>(c->d_u[0]), c->N, c->nc, c->n, c->h, c->d_wtab, c->cfg.gamma, euler, c->d_mass, c->d_part);
   else
-    k_diag_partial<double><<<kDiagBlocks, 256, 0, c->stream>>>(static_cast<const double*>(c->d_u[0]), c->N, c->nc, c->n, c->h, c->d_wtab, c->cfg.gamma, euler, c->d_part);
+    k_diag_partial<double><<<kDiagBlocks, 256, 0, c->stream>>>(static_cast<const double*>(c->d_u[0]), c->N, c->nc, c->n, c->h, c->d_wtab, c->cfg.gamma, euler, c->d_mass, c->d_part);
   CUDA_TRY(c, cudaGetLastError());
   k_diag_final<<<1, 32, 0, c->stream>>>(c->d_part, kDiagBlocks, c->d_diag);
   CUDA_TRY(c, cudaGetLastError());

@@ -1,0 +1,419 @@
+// Stage and time-step kernels on curved (mapped) quadrilateral meshes (Sec. 2.3, Sec. 3.1, with
+// the limiting of Sec. 4 and the CFL bound of Eq. cfl-low).
+//
+// Per-node geometry (float64 on the host, converted to the stage precision), kGeoFields arrays of
+// N values: rows 1 and 2 of G J^-1 (x, y components), the corrected rows of Sec. 3.1, the mass
+// m_i = w_a w_b G_i, and the face normals (+xi at b = 0, p; +eta at a = 0, p; one value per face,
+// shared by the two elements of the face).
+//
+// One CTA holds EPB whole elements, one thread per node.  Every face of an element is evaluated
+// inside it: the element faces from the node's own state and the neighbour's trace (read from
+// global memory, the L2-resident neighbour), the internal subcell faces between neighbouring
+// nodes of a line from shared memory.  Two elements that share a face evaluate its flux from the
+// same operands in the same order (the -xi/-eta side as the left state), so the update is
+// conservative.
+//
+// On a mapped element the pair coefficients are c_ij = D-hat^T_ij (row-hat)_j (the metric at node
+// j).  Along a line, with the contravariant low-order flux g = row-hat . F at each node, the
+// pairwise form of Eq. dg-lo-cij becomes a difference of subcell fluxes
+//   G_{b+1/2} = (g_b + g_{b+1})/2 - Lambda/2 (u_{b+1} - u_b),
+//   Lambda = max(lambda(u_b, u_{b+1}, row_{b+1}) |row_{b+1}|, lambda(u_b, u_{b+1}, row_b) |row_b|),
+// d_ij = w Lambda / 2 (Eq. dij with n_ij = -c_ij/|c_ij|), and the two nodes of a subcell face
+// have the bar states u-bar = (u_b + u_{b+1})/2 - row_other . (F_{b+1} - F_b) / (2 Lambda)
+// (Eq. bar-states with c_ij != -c_ji).
+#pragma once
+#include "sidp_kernels.cuh"
+
+namespace sidp {
+
+enum GeoField { GEO_R1X, GEO_R1Y, GEO_R2X, GEO_R2Y, GEO_Q1X, GEO_Q1Y, GEO_Q2X, GEO_Q2Y, GEO_MASS,
+                GEO_NXX, GEO_NXY, GEO_NYX, GEO_NYY };
+static_assert(GEO_NYY + 1 == kGeoFields, "geometry layout");
+static_assert(GEO_MASS == GEO_MASS_FIELD, "geometry layout");
+
+template <int P>
+struct CurvedGeom {
+  static constexpr int n = P + 1, NN = n * n;
+  static constexpr int EPB = (256 / NN) > 0 ? 256 / NN : 1;  // elements per CTA
+  static constexpr int THREADS = EPB * NN;                    // 245..256: every thread owns a node
+  static_assert(THREADS >= 32 && THREADS <= 256, "block shape");
+};
+
+template <int P, class LAW, typename T>
+struct CurvedSmem {
+  static constexpr int NC = LAW::NC, TH = CurvedGeom<P>::THREADS;
+  Vec<T, NC> u[TH];
+  typename LAW::Aux aux[TH];
+  Vec<T, NC> f1[TH], f2[TH];  // high-order contravariant fluxes (G J^-1 row k) . F
+  Vec<T, NC> g1[TH], g2[TH];  // low-order contravariant fluxes (corrected rows)
+  Vec<T, NC> Gx[TH], Gy[TH];  // subcell-face fluxes at (a, b+1/2), (a+1/2, b); then r_x, r_y
+  T q[TH][4];                 // corrected rows: row 1 (x, y), row 2 (x, y)
+  T F0[TH][2];                // x and y fluxes of the limited field
+  T bar[TH][4];               // limited-field bar states: x face (left node, right node), y face (lower, upper)
+  T lam[TH][2];               // Lambda of the x and y subcell faces (time step)
+  T sig[TH];
+  T alpha[TH];
+};
+
+// Element-face neighbour of node (a, b) of element e on side s (0 W, 1 E, 2 S, 3 N): the global
+// index of the neighbour's node at the same point, or -1 at a non-periodic boundary (outflow:
+// the node's own trace).
+template <int P>
+__device__ __forceinline__ long long curved_nbr(const int* bc, int nx, int ny, long long e, int a, int b, int s) {
+  constexpr int n = P + 1, NN = n * n;
+  int ex = (int)(e % nx), ey = (int)(e / nx);
+  int na = a, nb = b;
+  if (s == 0) { if (ex == 0 && bc[0] != SIDP_BC_PERIODIC) return -1; ex = (ex == 0) ? nx - 1 : ex - 1; nb = P; }
+  else if (s == 1) { if (ex == nx - 1 && bc[1] != SIDP_BC_PERIODIC) return -1; ex = (ex == nx - 1) ? 0 : ex + 1; nb = 0; }
+  else if (s == 2) { if (ey == 0 && bc[2] != SIDP_BC_PERIODIC) return -1; ey = (ey == 0) ? ny - 1 : ey - 1; na = P; }
+  else { if (ey == ny - 1 && bc[3] != SIDP_BC_PERIODIC) return -1; ey = (ey == ny - 1) ? 0 : ey + 1; na = 0; }
+  return ((long long)ey * nx + ex) * NN + na * n + nb;
+}
+
+// Lax-Friedrichs flux across an element face with scaled normal nv (pointing from L to R):
+// 1/2 (F_L + F_R) . nv - 1/2 lambda |nv| (u_R - u_L); also the limited field's bar state and
+// lambda |nv|.
+template <class LAW, typename T>
+__device__ __forceinline__ void curved_face(const T* uL, const typename LAW::Aux& aL, const T* uR,
+                                            const typename LAW::Aux& aR, T nvx, T nvy, const LawParamsT<T>& lp,
+                                            T* Fh, T& bar0, T& ln) {
+  constexpr int NC = LAW::NC;
+  T fLx[NC], fLy[NC], fRx[NC], fRy[NC];
+  LAW::flux(uL, aL, 0, fLx, lp);
+  LAW::flux(uL, aL, 1, fLy, lp);
+  LAW::flux(uR, aR, 0, fRx, lp);
+  LAW::flux(uR, aR, 1, fRy, lp);
+  const T nn = psqrt(nvx * nvx + nvy * nvy);
+  const T lam = LAW::lam_n(uL, aL, uR, aR, fdiv(nvx, nn), fdiv(nvy, nn), lp);
+  ln = lam * nn;
+#pragma unroll
+  for (int q = 0; q < NC; ++q)
+    Fh[q] = T(0.5) * ((fLx[q] + fRx[q]) * nvx + (fLy[q] + fRy[q]) * nvy) - T(0.5) * ln * (uR[q] - uL[q]);
+  const T dF = (fRx[0] - fLx[0]) * nvx + (fRy[0] - fLy[0]) * nvy;
+  bar0 = T(0.5) * (uL[0] + uR[0]) - ((ln > T(0)) ? fdiv(dF, T(2) * ln) : T(0));
+}
+
+// The node's element faces: trace of the neighbour, face flux, bar state, sigma of the neighbour,
+// lambda |n|, and the node's own F . n (high-order face term).  dir 0: x face (b = 0 or p),
+// dir 1: y face (a = 0 or p).
+template <int P, class LAW, typename T>
+struct CurvedFace {
+  T Fh[LAW::NC];   // flux in +xi (+eta)
+  T Fn[LAW::NC];   // own F . n
+  T bar, sig, ln;
+};
+
+template <int P, class LAW, typename T>
+__device__ __forceinline__ void curved_element_face(const Instance<T>& I, const LawParamsT<T>& lp, long long e,
+                                                    int a, int b, int dir, const T* u, const typename LAW::Aux& ax,
+                                                    const T* fx, const T* fy, CurvedFace<P, LAW, T>& F) {
+  constexpr int NC = LAW::NC;
+  const long long N = I.N, g = e * (P + 1) * (P + 1) + a * (P + 1) + b;
+  const bool low = (dir == 0) ? (b == 0) : (a == 0);
+  const int side = dir * 2 + (low ? 0 : 1);
+  const T nvx = I.geo[(dir == 0 ? GEO_NXX : GEO_NYX) * N + g], nvy = I.geo[(dir == 0 ? GEO_NXY : GEO_NYY) * N + g];
+  const long long gn = curved_nbr<P>(I.bc, I.nx, I.ny, e, a, b, side);
+  T un[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) un[q] = (gn >= 0) ? I.uin[q * N + gn] : u[q];
+  typename LAW::Aux an;
+  LAW::aux(un, an, lp);
+  if (low) curved_face<LAW>(un, an, u, ax, nvx, nvy, lp, F.Fh, F.bar, F.ln);
+  else curved_face<LAW>(u, ax, un, an, nvx, nvy, lp, F.Fh, F.bar, F.ln);
+#pragma unroll
+  for (int q = 0; q < NC; ++q) F.Fn[q] = fx[q] * nvx + fy[q] * nvy;
+  if constexpr (LAW::kEntropy) F.sig = LAW::sigma(un, an, lp);
+  else F.sig = T(0);
+}
+
+// Internal subcell face between slots L and R (dir 0: x, row 1; dir 1: y, row 2).
+template <int P, class LAW, typename T>
+__device__ __forceinline__ void curved_internal_face(CurvedSmem<P, LAW, T>& s, int L, int R, int dir,
+                                                     const LawParamsT<T>& lp) {
+  constexpr int NC = LAW::NC;
+  const Vec<T, NC> uL = s.u[L], uR = s.u[R];
+  const typename LAW::Aux aL = s.aux[L], aR = s.aux[R];
+  const int k = 2 * dir;
+  const T qLx = s.q[L][k], qLy = s.q[L][k + 1], qRx = s.q[R][k], qRy = s.q[R][k + 1];
+  const T nL = psqrt(qLx * qLx + qLy * qLy), nR = psqrt(qRx * qRx + qRy * qRy);
+  const T lR = LAW::lam_n(uL.v, aL, uR.v, aR, fdiv(qRx, nR), fdiv(qRy, nR), lp) * nR;
+  const T lL = LAW::lam_n(uL.v, aL, uR.v, aR, fdiv(qLx, nL), fdiv(qLy, nL), lp) * nL;
+  const T Lam = tmax(lR, lL);
+  const Vec<T, NC> gL = dir == 0 ? s.g1[L] : s.g2[L], gR = dir == 0 ? s.g1[R] : s.g2[R];
+  Vec<T, NC> G;
+#pragma unroll
+  for (int q = 0; q < NC; ++q) G.v[q] = T(0.5) * (gL.v[q] + gR.v[q]) - T(0.5) * Lam * (uR.v[q] - uL.v[q]);
+  const T dFx = s.F0[R][0] - s.F0[L][0], dFy = s.F0[R][1] - s.F0[L][1];
+  const T mid = T(0.5) * (uL.v[0] + uR.v[0]);
+  const T inv2 = (Lam > T(0)) ? fdiv(T(1), T(2) * Lam) : T(0);
+  if (dir == 0) s.Gx[L] = G; else s.Gy[L] = G;
+  s.bar[L][k] = mid - (qRx * dFx + qRy * dFy) * inv2;      // for the left / lower node
+  s.bar[L][k + 1] = mid - (qLx * dFx + qLy * dFy) * inv2;  // for the right / upper node
+  s.lam[L][dir] = Lam;
+}
+
+// Phase A and the subcell faces, shared by the stage and the time-step kernels.  Returns the
+// node's own state, aux, fluxes and its element faces.
+template <int P, class LAW, typename T>
+__device__ __forceinline__ void curved_load(CurvedSmem<P, LAW, T>& s, const Instance<T>& I, const LawParamsT<T>& lp,
+                                            long long e, bool act, int t, int a, int b, T* u, typename LAW::Aux& ax,
+                                            CurvedFace<P, LAW, T>& FX, CurvedFace<P, LAW, T>& FY, bool& onx, bool& ony) {
+  constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
+  const long long N = I.N, g = act ? e * NN + a * n + b : 0;
+  const T* geo = I.geo;
+#pragma unroll
+  for (int q = 0; q < NC; ++q) u[q] = I.uin[q * N + g];
+  LAW::aux(u, ax, lp);
+  T fx[NC], fy[NC];
+  LAW::flux(u, ax, 0, fx, lp);
+  LAW::flux(u, ax, 1, fy, lp);
+  const T r1x = geo[GEO_R1X * N + g], r1y = geo[GEO_R1Y * N + g], r2x = geo[GEO_R2X * N + g], r2y = geo[GEO_R2Y * N + g];
+  const T q1x = geo[GEO_Q1X * N + g], q1y = geo[GEO_Q1Y * N + g], q2x = geo[GEO_Q2X * N + g], q2y = geo[GEO_Q2Y * N + g];
+  Vec<T, NC> vu, f1, f2, g1, g2;
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    vu.v[q] = u[q];
+    f1.v[q] = r1x * fx[q] + r1y * fy[q];
+    f2.v[q] = r2x * fx[q] + r2y * fy[q];
+    g1.v[q] = q1x * fx[q] + q1y * fy[q];
+    g2.v[q] = q2x * fx[q] + q2y * fy[q];
+  }
+  s.u[t] = vu;
+  s.aux[t] = ax;
+  s.f1[t] = f1;
+  s.f2[t] = f2;
+  s.g1[t] = g1;
+  s.g2[t] = g2;
+  s.q[t][0] = q1x; s.q[t][1] = q1y; s.q[t][2] = q2x; s.q[t][3] = q2y;
+  s.F0[t][0] = fx[0];
+  s.F0[t][1] = fy[0];
+  if constexpr (LAW::kEntropy) s.sig[t] = LAW::sigma(u, ax, lp);
+  else s.sig[t] = T(0);
+  onx = act && (b == 0 || b == P);
+  ony = act && (a == 0 || a == P);
+  if (onx) curved_element_face<P, LAW>(I, lp, e, a, b, 0, u, ax, fx, fy, FX);
+  if (ony) curved_element_face<P, LAW>(I, lp, e, a, b, 1, u, ax, fx, fy, FY);
+  __syncthreads();
+  if (b < P) curved_internal_face<P, LAW>(s, t, t + 1, 0, lp);
+  if (a < P) curved_internal_face<P, LAW>(s, t, t + n, 1, lp);
+  __syncthreads();
+}
+
+}  // namespace sidp
+
+namespace sidp {
+
+template <int P, class LAW, typename T>
+__global__ void __launch_bounds__(CurvedGeom<P>::THREADS, 1) k_stage_curved(const StageLaunch<T> A) {
+  using Gm = CurvedGeom<P>;
+  using V = Vec<T, LAW::NC>;
+  constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& s = *reinterpret_cast<CurvedSmem<P, LAW, T>*>(smem_raw);
+  const Instance<T>& I = A.inst;
+  const LawParamsT<T>& lp = A.lp;
+  const int t = threadIdx.x, le = t / NN, i = t - le * NN, a = i / n, b = i - a * n;
+  const long long e = (long long)blockIdx.x * Gm::EPB + le;
+  const bool act = e < (long long)I.nx * I.ny;
+  const long long N = I.N, g = act ? e * NN + i : 0;
+  const int limiter = A.limiter;
+
+  // ---------------- A, B: node data, element faces, subcell faces
+  T u[NC];
+  typename LAW::Aux ax;
+  CurvedFace<P, LAW, T> FX{}, FY{};
+  bool onx, ony;
+  curved_load<P, LAW>(s, I, lp, e, act, t, a, b, u, ax, FX, FY, onx, ony);
+
+  // ---------------- C: residuals, low-order state, bounds
+  const T dt = *I.dtT;
+  const bool move = (dt > T(0)) && (dt < T(FLT_MAX));
+  const T wa = A.tab.w[a], wb = A.tab.w[b];
+  const T m = I.geo[GEO_MASS * N + g];
+  const T dtm = move ? fdiv(dt, m) : T(0);
+  T sx[NC], sy[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) { sx[q] = T(0); sy[q] = T(0); }
+  const int lx = le * NN + a * n, ly = le * NN + b;
+#pragma unroll
+  for (int c = 0; c < n; ++c) {
+    const V F1c = s.f1[lx + c], F2c = s.f2[ly + c * n];
+    const T dx = A.tab.D[b * n + c], dy = A.tab.D[a * n + c];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) { sx[q] += dx * F1c.v[q]; sy[q] += dy * F2c.v[q]; }
+  }
+  const V Gr = (b < P) ? s.Gx[t] : V{}, Gl = (b > 0) ? s.Gx[t - 1] : V{};
+  const V Gu = (a < P) ? s.Gy[t] : V{}, Gd = (a > 0) ? s.Gy[t - n] : V{};
+  T uL[NC], rx[NC], ry[NC], out[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    if (b == 0) sx[q] += FX.Fn[q] - FX.Fh[q];
+    if (b == P) sx[q] += FX.Fh[q] - FX.Fn[q];
+    if (a == 0) sy[q] += FY.Fn[q] - FY.Fh[q];
+    if (a == P) sy[q] += FY.Fh[q] - FY.Fn[q];
+    const T rHx = -wa * sx[q], rHy = -wb * sy[q];
+    const T gr = (b < P) ? Gr.v[q] : FX.Fh[q], gl = (b > 0) ? Gl.v[q] : FX.Fh[q];
+    const T gu = (a < P) ? Gu.v[q] : FY.Fh[q], gd = (a > 0) ? Gd.v[q] : FY.Fh[q];
+    const T rLx = -wa * (gr - gl), rLy = -wb * (gu - gd);
+    uL[q] = u[q] + dtm * (rLx + rLy);
+    out[q] = (limiter == 0) ? u[q] + dtm * (rHx + rHy) : uL[q];
+    rx[q] = rHx - rLx;
+    ry[q] = rHy - rLy;
+  }
+  if (limiter < 2 && act) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q)
+      I.uout[q * N + g] = (I.c0 == T(0)) ? out[q] : I.c0 * I.u0[q * N + g] + I.c1 * out[q];
+  }
+  if (limiter < 2) return;  // uniform across the CTA
+  const T bl = (b > 0) ? s.bar[t - 1][1] : FX.bar, br = (b < P) ? s.bar[t][0] : FX.bar;
+  const T bd = (a > 0) ? s.bar[t - n][3] : FY.bar, bu = (a < P) ? s.bar[t][2] : FY.bar;
+  const T lo = tmin(tmin(u[0], tmin(bl, br)), tmin(bd, bu));
+  const T hi = tmax(tmax(u[0], tmax(bl, br)), tmax(bd, bu));
+  T K = T(0);
+  if constexpr (LAW::kEntropy) {
+    const T sl = (b > 0) ? s.sig[t - 1] : FX.sig, sr = (b < P) ? s.sig[t + 1] : FX.sig;
+    const T sd = (a > 0) ? s.sig[t - n] : FY.sig, su = (a < P) ? s.sig[t + n] : FY.sig;
+    K = tmin(tmin(s.sig[t], tmin(sl, sr)), tmin(sd, su));
+  }
+  // ---------------- D: subcell fluxes (line prefix sums) and nodal alpha-tilde
+  __syncthreads();  // all reads of the subcell-face fluxes done
+  {
+    V vrx, vry;
+#pragma unroll
+    for (int q = 0; q < NC; ++q) { vrx.v[q] = rx[q]; vry.v[q] = ry[q]; }
+    s.Gx[t] = vrx;
+    s.Gy[t] = vry;
+  }
+  __syncthreads();
+  T xp[NC], xm[NC], yp[NC], ym[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) { xm[q] = T(0); ym[q] = T(0); }
+#pragma unroll
+  for (int c = 0; c < P; ++c) {
+    if (c < b) {
+      const V r = s.Gx[lx + c];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) xm[q] += r.v[q];
+    }
+    if (c < a) {
+      const V r = s.Gy[ly + c * n];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) ym[q] += r.v[q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    xp[q] = (b == P) ? T(0) : xm[q] + rx[q];
+    yp[q] = (a == P) ? T(0) : ym[q] + ry[q];
+  }
+  T at = T(1);
+  int iters = 0, caps = 0;
+  if (act && move) {
+    const T c1 = xp[0], c2 = -xm[0], c3 = yp[0], c4 = -ym[0];
+    const T Pp = tmax(c1, T(0)) + tmax(c2, T(0)) + tmax(c3, T(0)) + tmax(c4, T(0));
+    const T Pm = tmin(c1, T(0)) + tmin(c2, T(0)) + tmin(c3, T(0)) + tmin(c4, T(0));
+    const T mdt = fdiv(m, dt);
+    const T Qp = tmax(T(0), mdt * (hi - uL[0]));
+    const T Qm = tmin(T(0), mdt * (lo - uL[0]));
+    const T Rp = (Pp > T(0)) ? tmin(T(1), fdiv(Qp, Pp)) : T(1);
+    const T Rm = (Pm < T(0)) ? tmin(T(1), fdiv(Qm, Pm)) : T(1);
+    at = tmin(Rp, Rm);
+    if constexpr (LAW::kEntropy)
+      at = entropy_limit<LAW>(uL, K * (T(1) + Prec<T>::entropy_margin), xp, xm, yp, ym, T(4) * dtm, at, lp, iters, caps);
+  }
+  s.alpha[t] = at;
+  if (I.dbg_lo && act) {
+    I.dbg_lo[g] = (double)lo;
+    I.dbg_hi[g] = (double)hi;
+    I.dbg_K[g] = (double)K;
+    I.dbg_alpha[g] = (double)at;
+  }
+  T u0[NC];
+  if (act && I.c0 != T(0)) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) u0[q] = I.u0[q * N + g];
+  }
+  __syncthreads();
+  // ---------------- E: face coefficients and limited update
+  if (act) {
+    const T axp = (b < P) ? tmin(at, s.alpha[t + 1]) : T(0);
+    const T axm = (b > 0) ? tmin(at, s.alpha[t - 1]) : T(0);
+    const T ayp = (a < P) ? tmin(at, s.alpha[t + n]) : T(0);
+    const T aym = (a > 0) ? tmin(at, s.alpha[t - n]) : T(0);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      const T fe = uL[q] + dtm * (axp * xp[q] - axm * xm[q] + ayp * yp[q] - aym * ym[q]);
+      I.uout[q * N + g] = (I.c0 == T(0)) ? fe : I.c0 * u0[q] + I.c1 * fe;
+    }
+  }
+}
+
+// CFL bound of Eq. cfl-low per node on a curved mesh, m_i / (2 sum_{j != i} d_ij): subcell faces
+// d = w Lambda / 2, element faces d = w lambda |n| / 2; min-reduced into *out_bits.
+template <int P, class LAW, typename T>
+__global__ void __launch_bounds__(CurvedGeom<P>::THREADS, 1) k_dt_curved(const StageLaunch<T> A, unsigned long long* out_bits) {
+  using Gm = CurvedGeom<P>;
+  constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& s = *reinterpret_cast<CurvedSmem<P, LAW, T>*>(smem_raw);
+  const Instance<T>& I = A.inst;
+  const int t = threadIdx.x, le = t / NN, i = t - le * NN, a = i / n, b = i - a * n;
+  const long long e = (long long)blockIdx.x * Gm::EPB + le;
+  const bool act = e < (long long)I.nx * I.ny;
+  T u[NC];
+  typename LAW::Aux ax;
+  CurvedFace<P, LAW, T> FX{}, FY{};
+  bool onx, ony;
+  curved_load<P, LAW>(s, I, A.lp, e, act, t, a, b, u, ax, FX, FY, onx, ony);
+  const T big = T(FLT_MAX);
+  T val = big;
+  if (act) {
+    const T wa = A.tab.w[a], wb = A.tab.w[b];
+    const T half = T(0.5);
+    T sumd = T(0);
+    sumd += (b > 0) ? half * wa * s.lam[t - 1][0] : half * wa * FX.ln;
+    sumd += (b < P) ? half * wa * s.lam[t][0] : half * wa * FX.ln;
+    sumd += (a > 0) ? half * wb * s.lam[t - n][1] : half * wb * FY.ln;
+    sumd += (a < P) ? half * wb * s.lam[t][1] : half * wb * FY.ln;
+    if (sumd > T(0)) val = fdiv(I.geo[GEO_MASS * I.N + e * NN + i], T(2) * sumd);
+  }
+  // block minimum: the block size need not be a multiple of 32 (EPB whole elements), so the
+  // values go through shared memory and only the first, always complete, warp shuffles
+  __shared__ T red[Gm::THREADS];
+  red[t] = val;
+  __syncthreads();
+  if (t < 32) {
+    val = big;
+    for (int j = t; j < Gm::THREADS; j += 32) val = tmin(val, red[j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) val = tmin(val, __shfl_xor_sync(0xffffffffu, val, o));
+    if (t == 0 && val < big) atomicMin(out_bits, (unsigned long long)__double_as_longlong((double)val));
+  }
+}
+
+template <int P, class LAW, typename T>
+cudaError_t launch_curved(const StageLaunch<T>& a, unsigned long long* dt_bits, cudaStream_t s) {
+  if constexpr (HasPosition<LAW>::value) {
+    return cudaErrorInvalidValue;  // position-dependent laws are defined on Cartesian meshes only
+  } else {
+    using Gm = CurvedGeom<P>;
+    constexpr size_t smem = sizeof(CurvedSmem<P, LAW, T>);
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaError_t err = cudaFuncSetAttribute(k_stage_curved<P, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
+      err = cudaFuncSetAttribute(k_dt_curved<P, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
+      attr_set = true;
+    }
+    const long long Ne = (long long)a.inst.nx * a.inst.ny;
+    const long long blocks = (Ne + Gm::EPB - 1) / Gm::EPB;
+    if (blocks <= 0) return cudaSuccess;
+    if (dt_bits) k_dt_curved<P, LAW, T><<<(unsigned)blocks, Gm::THREADS, smem, s>>>(a, dt_bits);
+    else k_stage_curved<P, LAW, T><<<(unsigned)blocks, Gm::THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+  }
+}
+
+}  // namespace sidp

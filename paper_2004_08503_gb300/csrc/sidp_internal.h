@@ -9,6 +9,8 @@
 namespace sidp {
 
 constexpr int kMaxP = 7;
+constexpr int kGeoFields = SIDP_GEO_FIELDS;  // per-node metric arrays of a curved mesh
+constexpr int GEO_MASS_FIELD = 8;           // index of m_i among them
 constexpr int kMaxN = kMaxP + 1;
 
 enum Law { LAW_BURGERS = 1, LAW_EULER = 2, LAW_ADVECTION = 3, LAW_ADVECTION_VAR = 4 };
@@ -122,6 +124,7 @@ struct Instance {
   T x0, y0;          // lower-left corner of the domain (node positions)
   T c0, c1;          // RK combination uout = c0 u0 + c1 FE(uin)
   const SplitBC<T>* split;  // per side (split sides only), or null
+  const T* geo;             // curved mesh: the per-node metric arrays [kGeoFields][N], or null (Cartesian)
   const double* tnow;       // time base of the launch (device scalar)
   double ck;                // stage time = *tnow + ck * dt
   // debug outputs (null = off), per node
@@ -174,6 +177,9 @@ sidp_status validate_config(const sidp_config* cfg, std::string& msg);
 
 // Host tables (float64), computed once.
 void gll_tables(int p, double* xi, double* w, double* D);
+// Metric arrays of a curved mesh (sidp_geometry.cpp): kGeoFields x N values into out.
+sidp_status curved_metrics(int p, int nx, int ny, const int* bc, const double* x, const double* y, double* out,
+                           std::string& msg);
 void modal_tables(int p, double* Vinv, double* nrm);
 
 }  // namespace sidp
@@ -208,6 +214,8 @@ SIDP_DECLARE(LAW_ADVECTION_VAR, float)
   template <>                                                                                          \
   cudaError_t launch_p<LAWID, TT, P>(int tile, const StageLaunch<TT>& a, unsigned long long* bits,     \
                                      cudaStream_t s) {                                                 \
+    if (a.inst.geo) /* curved mesh: its own kernels */                                                 \
+      return launch_curved<P, LAWTPL<TT>, TT>(a, bits, s);                                             \
     if (a.dense) { /* unsparsified comparison mode: its own kernels, default tile shape */             \
       if (bits || a.limiter != 3)                                                                      \
         return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, false, true>(a, bits, s); \

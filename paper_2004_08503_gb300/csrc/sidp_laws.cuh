@@ -8,6 +8,7 @@
 //   lam(k, L, R)       upper bound of lambda_max for the Riemann problem with left state L,
 //                      right state R along +e_k (Sec. 2.1.1); the same bound serves the LF flux,
 //                      d_ij (Eq. dij), the bar states and the CFL condition
+//   lam_n(L, R, nx, ny) the same bound along a unit normal (nx, ny) (curved meshes)
 //   limited field 0    (the scalar, or the density)
 // Euler additionally: sigma = rho e / rho^gamma and psi_K(u) = rho e - K rho^gamma (Sec. 4.3).
 #pragma once
@@ -56,6 +57,9 @@ struct LawAdvection {
   __device__ static T lam(int k, const T*, const Aux&, const T*, const Aux&, const LawParamsT<T>& lp) {
     return fabs(lp.beta[k]);
   }
+  __device__ static T lam_n(const T*, const Aux&, const T*, const Aux&, T nx, T ny, const LawParamsT<T>& lp) {
+    return fabs(lp.beta[0] * nx + lp.beta[1] * ny);
+  }
 };
 
 // Linear advection with the divergence-free velocity beta = (b0x + bxy y, b0y + byx x) (Sec. 3.3):
@@ -92,6 +96,10 @@ struct LawBurgers {
   // F.e_k = u^2/2 is convex; the extreme characteristic speeds are the end states'.
   __device__ static T lam(int, const T* uL, const Aux&, const T* uR, const Aux&, const LawParamsT<T>&) {
     return tmax(fabs(uL[0]), fabs(uR[0]));
+  }
+  // F.n = (nx + ny) u^2/2: speed (nx + ny) u, extreme at an end state
+  __device__ static T lam_n(const T* uL, const Aux&, const T* uR, const Aux&, T nx, T ny, const LawParamsT<T>&) {
+    return fabs(nx + ny) * tmax(fabs(uL[0]), fabs(uR[0]));
   }
 };
 
@@ -132,6 +140,15 @@ struct LawEuler {
   // pressure p* bounds the star pressure from above, and the extreme speeds grow with it.
   __device__ static T lam(int k, const T* uL, const Aux& L, const T* uR, const Aux& R, const LawParamsT<T>& lp) {
     const T vL = uL[1 + k] * L.rinv, vR = uR[1 + k] * R.rinv;
+    const T num = tmax(L.a + R.a - lp.half_gm1 * (vR - vL), T(0));
+    const T ps = pstar_pow(fdiv(num, L.apm + R.apm), lp);
+    const T lL = vL - L.a * psqrt(T(1) + lp.c_gp * tmax(ps * L.ip - T(1), T(0)));
+    const T lR = vR + R.a * psqrt(T(1) + lp.c_gp * tmax(ps * R.ip - T(1), T(0)));
+    return tmax(fabs(lL), fabs(lR));
+  }
+  // the same bound along the unit normal (nx, ny): normal velocities m.n / rho
+  __device__ static T lam_n(const T* uL, const Aux& L, const T* uR, const Aux& R, T nx, T ny, const LawParamsT<T>& lp) {
+    const T vL = (uL[1] * nx + uL[2] * ny) * L.rinv, vR = (uR[1] * nx + uR[2] * ny) * R.rinv;
     const T num = tmax(L.a + R.a - lp.half_gm1 * (vR - vL), T(0));
     const T ps = pstar_pow(fdiv(num, L.apm + R.apm), lp);
     const T lL = vL - L.a * psqrt(T(1) + lp.c_gp * tmax(ps * L.ip - T(1), T(0)));

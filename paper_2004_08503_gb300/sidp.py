@@ -61,6 +61,9 @@ _SIGS = {
     "sidp_set_ghost_state": (ctypes.c_int, [_P, ctypes.c_int, _D]),
     "sidp_set_split_boundary": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _D, _D]),
     "sidp_set_time": (ctypes.c_int, [_P, ctypes.c_double]),
+    "sidp_curved_metrics": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                           _D, _D, _D]),
+    "sidp_set_geometry": (ctypes.c_int, [_P, _D, _D]),
     "sidp_upload_state": (ctypes.c_int, [_P, _P]),
     "sidp_download_state": (ctypes.c_int, [_P, ctypes.c_int, _P]),
     "sidp_device_state": (ctypes.c_int, [_P, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]),
@@ -220,6 +223,25 @@ def sidp_set_split_boundary(ctx, side, s0, speed, state_a, state_b=None):
 
 def sidp_set_time(ctx, t):
     _check(load().sidp_set_time(ctx, ctypes.c_double(t)), ctx)
+
+
+GEO_FIELDS = 13
+
+
+def sidp_curved_metrics(p, nx, ny, bc, x, y):
+    """Metric arrays (GEO_FIELDS, N) of the curved mesh with node coordinates x, y (host only)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    y = np.ascontiguousarray(y, dtype=np.float64).ravel()
+    out = np.empty((GEO_FIELDS, x.size))
+    b = (ctypes.c_int * 4)(*[BCS.get(v, v) for v in bc])
+    _check(load().sidp_curved_metrics(int(p), int(nx), int(ny), b, _ptr(x), _ptr(y), _ptr(out)))
+    return out
+
+
+def sidp_set_geometry(ctx, x, y):
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    y = np.ascontiguousarray(y, dtype=np.float64).ravel()
+    _check(load().sidp_set_geometry(ctx, _ptr(x), _ptr(y)), ctx)
 
 
 def sidp_device_state(ctx):
@@ -392,6 +414,10 @@ class Solver:
 
     def set_time(self, t):
         sidp_set_time(self.ctx, t)
+
+    def set_geometry(self, x, y):
+        """Curved mesh: node coordinates in library order (see sidp_set_geometry)."""
+        sidp_set_geometry(self.ctx, x, y)
 
     def compute_dt(self):
         return sidp_compute_dt(self.ctx)

@@ -1,0 +1,214 @@
+"""Curved (mapped) meshes on the GPU path against the FP64 oracle (Sec. 2.3 metric terms,
+Sec. 3.1 conservative correction, with the limiting of Sec. 4): the time step, the unlimited and
+low-order stages element by element, the limited stages through the conditioning-aware
+comparators, whole steps, free-stream preservation, conservation, and the rotated Cartesian mesh
+against the Cartesian kernels."""
+import numpy as np
+import pytest
+
+from fe_compare import euler_fe_check, scalar_fe_check
+from oracle import laws, scheme
+from oracle.curved import CurvedProblem
+from paper_2004_08503_gb300 import build, inputs, sidp
+
+pytestmark = pytest.mark.gpu
+G = 1.4
+BETA = (1.0, 0.5)
+PER = ("periodic",) * 4
+OUT = ("outflow",) * 4
+MIXED_BC = ("outflow", "outflow", "periodic", "periodic")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    sidp.load()
+
+
+def _law(name):
+    return {"euler": laws.Euler(G), "burgers": laws.Burgers(), "advection": laws.Advection(BETA)}[name]
+
+
+def make(law, p, nx, ny, limiter, bc=PER, eps=0.08, L=None, precision="fp64", theta=None):
+    lo = _law(law)
+    L = (1.0, ny / nx) if L is None else L   # square elements
+    X, Y = scheme.Problem(lo, p, nx, ny, domain=(0.0, L[0], 0.0, L[1])).node_coords()
+    if theta is None:
+        Xm, Ym = inputs.warped_coords(X, Y, eps, L)
+    else:
+        Xm, Ym = inputs.rotated_coords(X, Y, theta)
+    pb = CurvedProblem(lo, p, nx, ny, Xm, Ym, bc=bc, limiter=limiter)
+    sv = sidp.Solver(law=law, p=p, nx=nx, ny=ny, domain=(0.0, L[0], 0.0, L[1]), bc=bc, limiter=limiter, gamma=G,
+                     beta=BETA, precision=precision)
+    sv.set_geometry(Xm, Ym)
+    return pb, sv, Xm, Ym
+
+
+def data(law, X, Y, seed=3):
+    if law == "euler":
+        return inputs.four_quadrant(X, Y, seed)
+    return inputs.burgers_pulse(X, Y)
+
+
+def rel(a, b):
+    a = a.reshape(b.shape[0], -1)
+    b = b.reshape(b.shape[0], -1)
+    return np.max(np.abs(a - b), axis=1) / np.max(np.abs(b), axis=1)
+
+
+def test_node_coords_are_the_mapped_ones():
+    pb, sv, X, Y = make("burgers", 3, 4, 3, "lo")
+    x, y = sv.node_coords()
+    np.testing.assert_array_equal(x, X.ravel())
+    np.testing.assert_array_equal(y, Y.ravel())
+
+
+@pytest.mark.parametrize("bc", [PER, OUT, MIXED_BC])
+@pytest.mark.parametrize("limiter", ["none", "lo"])
+@pytest.mark.parametrize("p", [1, 2, 3, 5, 7])
+def test_euler_stages_match_the_oracle(p, limiter, bc):
+    """dt (Eq. cfl-low) and the three SSP-RK3 stages, element by element, FP64."""
+    pb, sv, X, Y = make("euler", p, 4, 3, limiter, bc=bc)
+    U0 = data("euler", X, Y)
+    dt = pb.compute_dt(U0)
+    sv.set_state(U0.reshape(4, -1))
+    assert abs(sv.compute_dt() - dt) <= 1e-13 * dt
+    cur = U0
+    for k in (1, 2, 3):
+        expect = pb.stage(cur, U0, dt, k)
+        sv.stage(k, dt)
+        got = sv.get_state({1: 1, 2: 2, 3: 0}[k])
+        assert np.all(rel(got, expect) <= 1e-12), (k, rel(got, expect))
+        cur = expect
+
+
+@pytest.mark.parametrize("law", ["burgers", "advection"])
+@pytest.mark.parametrize("limiter", ["none", "lo"])
+@pytest.mark.parametrize("p", [2, 4])
+def test_scalar_stages_match_the_oracle(law, limiter, p):
+    pb, sv, X, Y = make(law, p, 5, 4, limiter)
+    U0 = data(law, X, Y)
+    dt = pb.compute_dt(U0)
+    sv.set_state(U0.reshape(1, -1))
+    assert abs(sv.compute_dt() - dt) <= 1e-13 * dt
+    cur = U0
+    for k in (1, 2, 3):
+        expect = pb.stage(cur, U0, dt, k)
+        sv.stage(k, dt)
+        got = sv.get_state({1: 1, 2: 2, 3: 0}[k])
+        assert np.all(rel(got, expect) <= 1e-12), (k, rel(got, expect))
+        cur = expect
+
+
+@pytest.mark.parametrize("law", ["burgers", "advection"])
+@pytest.mark.parametrize("p", [2, 3, 5])
+def test_scalar_subcell_stage(law, p):
+    """One limited forward-Euler stage (Zalesak, Sec. 4.1.3) with the conditioning-aware check."""
+    pb, sv, X, Y = make(law, p, 5, 4, "subcell", bc=MIXED_BC)
+    U = data(law, X, Y)
+    dt = pb.compute_dt(U)
+    sv.set_state(U.reshape(1, -1))
+    sv.stage(1, dt)
+    scalar_fe_check(pb, U, dt, sv.get_state(1))
+
+
+@pytest.mark.parametrize("bc", [PER, OUT])
+@pytest.mark.parametrize("p", [2, 3, 4, 6])
+def test_euler_subcell_stage(p, bc):
+    """One limited stage with the density bounds and the entropy minimum (Sec. 4.3)."""
+    pb, sv, X, Y = make("euler", p, 4, 3, "subcell", bc=bc)
+    U = data("euler", X, Y, seed=5)
+    dt = pb.compute_dt(U)
+    sv.set_state(U.reshape(4, -1))
+    sv.set_debug(True)
+    sv.stage(1, dt)
+    euler_fe_check(pb, U, dt, sv.get_state(1))
+    # the bounds themselves (bar states of ordered pairs, element-face bars, K)
+    _, info = pb.fe_stage(U, dt, full=True)
+    bd = sv.bounds()
+    lo, hi, K = bd["lo"], bd["hi"], bd["K"]
+    np.testing.assert_allclose(lo, info["lo"].ravel(), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(hi, info["hi"].ravel(), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(K, info["K"].ravel(), rtol=1e-12)
+
+
+def test_whole_steps_burgers():
+    pb, sv, X, Y = make("burgers", 3, 5, 4, "lo", bc=MIXED_BC)
+    U = data("burgers", X, Y)
+    sv.set_state(U.reshape(1, -1))
+    for _ in range(5):
+        U, dt = pb.ssp_rk3_step(U)
+        sv.step()
+        assert abs(sv.diag()["last_dt"] - dt) <= 1e-13 * dt
+    assert np.all(rel(sv.get_state(0), U) <= 1e-11)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_free_stream_and_conservation(precision):
+    """A constant state stays constant on the warped periodic mesh (Sec. 3.1: only with the
+    corrected metric terms), and total mass is conserved on it with the limiter on."""
+    tol = 1e-13 if precision == "fp64" else 2e-6
+    pb, sv, X, Y = make("euler", 3, 6, 5, "subcell", precision=precision)
+    Uc = inputs.constant_state(X, Y)
+    sv.set_state(Uc.reshape(4, -1))
+    sv.step(5)
+    np.testing.assert_allclose(sv.get_state(0), Uc.reshape(4, -1), rtol=tol)
+    U = data("euler", X, Y, seed=9)
+    sv.set_state(U.reshape(4, -1))
+    m0 = sv.diag()["mass"]
+    np.testing.assert_allclose(m0, pb.total_mass(U), rtol=1e-12)
+    sv.step(10)
+    d = sv.diag()
+    np.testing.assert_allclose(d["mass"], m0, rtol=tol * 10, atol=tol * 10 * max(abs(v) for v in m0))
+    assert d["rho_min"] > 0 and d["p_min"] > 0
+
+
+@pytest.mark.parametrize("limiter", ["none", "lo"])
+def test_rotated_mesh_equals_the_cartesian_kernels(limiter):
+    """On the rotated image of a Cartesian mesh, with rotated momenta, the curved kernels give the
+    rotated result of the Cartesian kernels (two independent kernel families on the GPU)."""
+    th = 0.4
+    pb, sv, X, Y = make("euler", 3, 5, 5, limiter, bc=OUT, L=(1.0, 1.0), theta=th)
+    sc = sidp.Solver(law="euler", p=3, nx=5, ny=5, bc=OUT, limiter=limiter, gamma=G)
+    x, y = sc.node_coords()
+    U = inputs.four_quadrant(x, y, 4)
+    c, s = np.cos(th), np.sin(th)
+    Ur = U.copy()
+    Ur[1], Ur[2] = c * U[1] - s * U[2], s * U[1] + c * U[2]
+    sc.set_state(U)
+    sv.set_state(Ur)
+    for _ in range(3):
+        sc.step()
+        sv.step()
+    a, b = sc.get_state(0), sv.get_state(0)
+    ar = a.copy()
+    ar[1], ar[2] = c * a[1] - s * a[2], s * a[1] + c * a[2]
+    assert abs(sc.diag()["t"] - sv.diag()["t"]) <= 1e-12 * sc.diag()["t"]
+    assert np.all(rel(b, ar) <= 1e-9), rel(b, ar)
+
+
+def test_mixed_precision_warped_euler():
+    """Mixed precision (float32 stages) on the warped mesh: positivity and agreement with FP64."""
+    _, s64, X, Y = make("euler", 3, 8, 8, "subcell", L=(1.0, 1.0))
+    _, s32, _, _ = make("euler", 3, 8, 8, "subcell", L=(1.0, 1.0), precision="mixed")
+    U = data("euler", X, Y, seed=2)
+    for sv in (s64, s32):
+        sv.set_state(U.reshape(4, -1))
+        sv.step(20)
+    d = s32.diag()
+    assert d["rho_min"] > 0 and d["p_min"] > 0 and d["nonfinite"] == 0
+    assert np.all(rel(s32.get_state(0), s64.get_state(0)) <= 1e-3)
+
+
+def test_set_geometry_errors():
+    X, Y = scheme.Problem(laws.Burgers(), 2, 3, 3).node_coords()
+    for kw in (dict(law="advection_var"), dict(limiter="elementwise"), dict(bc=("exact",) + ("outflow",) * 3),
+               dict(sparsify=False), dict(smoothness=dict(gmin=0.0, gmax=1.0))):
+        cfg = dict(law="burgers", p=2, nx=3, ny=3, bc=OUT, limiter="subcell")
+        cfg.update(kw)
+        sv = sidp.Solver(**cfg)
+        with pytest.raises(sidp.SidpError):
+            sv.set_geometry(X, Y)
+    sv = sidp.Solver(law="burgers", p=2, nx=3, ny=3, bc=OUT)
+    with pytest.raises(sidp.SidpError):
+        sv.set_geometry(-X, Y)
