@@ -6,8 +6,9 @@ sides, CFL 1/2, subcell convex limiting, mixed precision (float32 state and stag
 float64 dt reduction).  The state (268 MB per buffer) is larger than L2, so no flush is needed.
 
 One step = dt reduction + 3 SSP-RK3 stages (CUDA graph replay).  value = nodes * 3 * K / time.
-Also reported: the same workload in float64 ("fp64"), the stage kernel's roofline, an
-end-to-end figure through the C-ABI with host buffers, and the oracle's CPU rate.
+Also reported: the same workload in float64 ("fp64"), the stage kernel's roofline, the same
+workload on a curved (warped, periodic) mesh ("curved", Sec. 2.3 and 3.1), an end-to-end figure
+through the C-ABI with host buffers, and the oracle's CPU rate.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 Under torchrun each rank advances its own copy of the workload (independent problems: weak
@@ -45,6 +46,8 @@ STAGE_WARP_INSTR_PER_NODE = (36.3, 28.4, 28.4)
 SMS, FP32_LANES_PER_SM, SCHEDULERS_PER_SM = 152, 128, 4
 NEL, P = 1024, 3
 WORKLOAD = "2D Euler blast, 1024x1024 elements, p=3 (16.8M nodes x 4 fields), outflow, CFL 0.5, subcell convex limiting"
+WORKLOAD_CURVED = ("2D Euler blast on a curved mesh: 1024x1024 elements, p=3, nodes warped by "
+                   "x, y += 0.05 sin(2 pi x) sin(2 pi y), periodic, subcell convex limiting")
 HBM_FALLBACK = 6800.0
 
 
@@ -189,6 +192,42 @@ def stage_kernel_times(torch, sv, stream, reps):
         for k in (1, 2, 3):
             tot[k - 1] += evs[k - 1].elapsed_time(evs[k]) / 1e3
     return [t / reps for t in tot]
+
+
+def run_curved(torch, sidp, stream, steps, warmup, hbm, peak_kind):
+    """The same workload on a curved mesh (Sec. 2.3 metric terms, Sec. 3.1 corrected metric):
+    the nodes of the Cartesian mesh moved by the periodic warp x += 0.05 s, y += 0.05 s,
+    s = sin(2 pi x) sin(2 pi y) (inputs.warped_coords), periodic sides, mixed precision."""
+    from paper_2004_08503_gb300 import inputs
+    sv = sidp.Solver(stream=stream, law="euler", p=P, nx=NEL, ny=NEL, precision="mixed", domain=(0.0, 1.0, 0.0, 1.0),
+                     bc=("periodic",) * 4, cfl=0.5, gamma=1.4, limiter="subcell")
+    x, y = sv.node_coords()
+    xw, yw = inputs.warped_coords(x, y, 0.05)
+    t0 = time.time()
+    sv.set_geometry(xw, yw)
+    setup = time.time() - t0
+    sv.set_state(inputs.blast(xw, yw))
+    sv.set_stats(False)
+    nodes = sv.N
+    sec, _ = time_steps(torch, sv, stream, steps, warmup)
+    value = nodes * 3 * steps / sec
+    kt = stage_kernel_times(torch, sv, stream, reps=10)
+    d = sv.diag()
+    sv.close()
+    # algorithmic bytes per node and launch: state (u_in, u_out; u^n in stages 2-3) plus the
+    # geometry each node reads: 8 metric rows and m_i, and the face normals on face nodes
+    # (2 of every p+1 nodes along each direction carry a normal pair)
+    s, n = 4, P + 1
+    geo = s * (9 + 2 * (2.0 / n) * 2)
+    per_node = [2 * 4 * s + geo, 3 * 4 * s + geo, 3 * 4 * s + geo]
+    ach = sum(b * nodes for b in per_node) / sum(kt) / 1e9
+    return {"workload": WORKLOAD_CURVED.replace("1024x1024", f"{NEL}x{NEL}"), "value": value, "unit": UNIT,
+            "steps": steps, "ms_per_step": 1e3 * sec / steps, "stage_ms": [1e3 * t for t in kt],
+            "geometry_setup_s": setup,
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                         "traffic": None, "kernel": "k_stage_curved<3, LawEuler<float>, float>",
+                         "bytes_per_node": per_node, "peak_kind": peak_kind},
+            "invariants": {"rho_min": d["rho_min"], "p_min": d["p_min"], "nonfinite": d["nonfinite"]}}
 
 
 def cpu_baseline(seconds_target=12.0):
@@ -433,6 +472,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--nel", type=int, default=NEL, help="elements per side (profiling runs only)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched leg")
+    ap.add_argument("--no-curved", action="store_true", help="skip the curved-mesh leg")
     ap.add_argument("--accuracy", action="store_true", help="also report mixed-vs-float64 errors (200 stages)")
     ap.add_argument("--dmr", type=int, default=0, help="also run the double Mach reflection on N x N/4 elements")
     ap.add_argument("--dmr-t", type=float, default=0.275, help="final time of the double Mach reflection")
@@ -505,6 +545,10 @@ def main():
         fp64 = {"value": fp64_value, "unit": UNIT, "steps": args.fp64_steps,
                 "stage_ms": [1e3 * t for t in kt64], "speedup_mixed_over_fp64": value / fp64_value}
 
+    curved = None
+    if not args.no_curved:
+        curved = run_curved(torch, sidp, stream, max(20, args.steps // 4), 3, hbm, peak_kind)
+
     batched = None
     if not args.no_batched:
         batched = run_batched(torch, sidp, stream, steps=max(10, args.steps // 4), warmup=2)
@@ -528,7 +572,7 @@ def main():
                              "stage_ms": [1e3 * t for t in kt], "peak_kind": peak_kind,
                              "whole_step_gbs": step_gbs, "whole_step_frac": step_gbs / hbm,
                              "other_ceilings": other_ceilings(nodes, kt, clk)},
-                "fp64": fp64, "batched": batched, "invariants": diag_stats, "accuracy": accuracy, "dmr": dmr,
+                "fp64": fp64, "curved": curved, "batched": batched, "invariants": diag_stats, "accuracy": accuracy, "dmr": dmr,
                 "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": 5 * args.steps}
         print(json.dumps(line), flush=True)

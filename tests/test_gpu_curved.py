@@ -156,7 +156,8 @@ def test_free_stream_and_conservation(precision):
     U = data("euler", X, Y, seed=9)
     sv.set_state(U.reshape(4, -1))
     m0 = sv.diag()["mass"]
-    np.testing.assert_allclose(m0, pb.total_mass(U), rtol=1e-12)
+    # the mixed form stores the state in float32: its mass carries that rounding
+    np.testing.assert_allclose(m0, pb.total_mass(U), rtol=1e-12 if precision == "fp64" else 1e-6)
     sv.step(10)
     d = sv.diag()
     np.testing.assert_allclose(d["mass"], m0, rtol=tol * 10, atol=tol * 10 * max(abs(v) for v in m0))
