@@ -39,6 +39,10 @@ struct CurvedGeom {
   static_assert(THREADS >= 32 && THREADS <= 256, "block shape");
 };
 
+// Resident CTAs per SM the register budget is sized for: float32 kernels fit 3 (80 registers,
+// no spills); the float64 ones need more registers than 2 CTAs allow without spilling.
+template <typename T> struct CurvedMinBlocks { static constexpr int value = sizeof(T) == 4 ? 3 : 1; };
+
 template <int P, class LAW, typename T>
 struct CurvedSmem {
   static constexpr int NC = LAW::NC, TH = CurvedGeom<P>::THREADS;
@@ -204,7 +208,7 @@ __device__ __forceinline__ void curved_load(CurvedSmem<P, LAW, T>& s, const Inst
 namespace sidp {
 
 template <int P, class LAW, typename T>
-__global__ void __launch_bounds__(CurvedGeom<P>::THREADS, 1) k_stage_curved(const StageLaunch<T> A) {
+__global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::value) k_stage_curved(const StageLaunch<T> A) {
   using Gm = CurvedGeom<P>;
   using V = Vec<T, LAW::NC>;
   constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
@@ -352,7 +356,7 @@ __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, 1) k_stage_curved(cons
 // CFL bound of Eq. cfl-low per node on a curved mesh, m_i / (2 sum_{j != i} d_ij): subcell faces
 // d = w Lambda / 2, element faces d = w lambda |n| / 2; min-reduced into *out_bits.
 template <int P, class LAW, typename T>
-__global__ void __launch_bounds__(CurvedGeom<P>::THREADS, 1) k_dt_curved(const StageLaunch<T> A, unsigned long long* out_bits) {
+__global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::value) k_dt_curved(const StageLaunch<T> A, unsigned long long* out_bits) {
   using Gm = CurvedGeom<P>;
   constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
