@@ -39,9 +39,10 @@ struct CurvedGeom {
   static_assert(THREADS >= 32 && THREADS <= 256, "block shape");
 };
 
-// Resident CTAs per SM the register budget is sized for: float32 kernels fit 3 (80 registers,
-// no spills); the float64 ones need more registers than 2 CTAs allow without spilling.
-template <typename T> struct CurvedMinBlocks { static constexpr int value = sizeof(T) == 4 ? 3 : 1; };
+// Resident CTAs per SM the register budget is sized for: float32 kernels take 4 (64 registers,
+// a few dozen bytes spilled at p = 3; measured faster than 3 CTAs at 80 registers without
+// spills); the float64 ones need more registers than 2 CTAs allow without spilling.
+template <typename T> struct CurvedMinBlocks { static constexpr int value = sizeof(T) == 4 ? 4 : 1; };
 
 template <int P, class LAW, typename T>
 struct CurvedSmem {
