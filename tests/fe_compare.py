@@ -17,7 +17,7 @@ match to `tol` (normwise).
 import numpy as np
 
 
-def zalesak_ill_conditioned(pb, info, dt, tol=1e-12, kappa=64.0, tau=1e-10):
+def zalesak_ill_conditioned(pb, info, dt, tol=1e-12, kappa=64.0, tau=1e-10, elems=None):
     """Nodes (Ne, n*n) whose limited update the rounding of the Zalesak ratio moves by more
     than `tol` in some field (relative to that field's max |u|).
 
@@ -33,7 +33,7 @@ def zalesak_ill_conditioned(pb, info, dt, tol=1e-12, kappa=64.0, tau=1e-10):
     Pm = -np.sum(np.minimum(c, 0.0), axis=0)
     uL = info["uL"]
     s0 = max(np.max(np.abs(uL[0])), 1e-300)
-    m = pb._mass(None)
+    m = pb._mass(elems)
     eta = tau * m / dt * s0
     Qp = m / dt * np.maximum(info["hi"] - uL[0], 0.0)
     Qm = m / dt * np.maximum(uL[0] - info["lo"], 0.0)
@@ -118,7 +118,7 @@ def elementwise_fe_check(pb, U, dt, got, tol=1e-12, ulp=None, kappa=64.0, tau=1e
     return float(np.mean(width > 0))
 
 
-def euler_fe_check(pb, U, dt, got, tol=1e-12, tau=1e-6):
+def euler_fe_check(pb, U, dt, got, tol=1e-12, tau=1e-6, elems=None):
     """Compare a GPU forward-Euler stage with the oracle's on the entropy-limited Euler path.
 
     The entropy coefficient of node i is the root t* of psi_K(u^L + t w) = min(0, psi_K(u^L)),
@@ -130,8 +130,9 @@ def euler_fe_check(pb, U, dt, got, tol=1e-12, tau=1e-6):
     and their face neighbours (alpha on a subcell face is the min of the two nodes) are checked
     for validity instead: density inside its bounds, sigma >= K_i, and a difference no larger than
     the sum of the node's absolute subcell corrections dt/m sum |r-bar|.  All other nodes must
-    match to `tol` (normwise per field).  Returns the fraction of nodes checked by validity."""
-    exp, info = pb.fe_stage(U, dt, full=True)
+    match to `tol` (normwise per field).  `elems`: check only these elements (`got` holds their
+    values).  Returns the fraction of nodes checked by validity."""
+    exp, info = pb.fe_stage(U, dt, elems=elems, full=True)
     n = pb.n
     got = got.reshape(exp.shape)
     scale = np.max(np.abs(exp), axis=(1, 2))
@@ -139,11 +140,11 @@ def euler_fe_check(pb, U, dt, got, tol=1e-12, tau=1e-6):
     rhoe = pb.law.pressure(uL) / (pb.law.gamma - 1.0)
     ic = pb.law.psi(uL, K) < tau * rhoe
     # plus nodes where Zalesak's density ratio is ill-conditioned (a density plateau on its bound)
-    bad = spread_faces(ic | zalesak_ill_conditioned(pb, info, dt, tol=tol), n)
+    bad = spread_faces(ic | zalesak_ill_conditioned(pb, info, dt, tol=tol, elems=elems), n)
     err = np.abs(got - exp) / scale[:, None, None]
     assert np.all(err[:, ~bad] <= tol), np.max(err[:, ~bad], axis=1)
     xp, xm, yp, ym = pb._node_face_fluxes(info["rbar"])
-    corr = dt / pb._mass(None) * (np.abs(xp) + np.abs(xm) + np.abs(yp) + np.abs(ym)) / scale[:, None, None]
+    corr = dt / pb._mass(elems) * (np.abs(xp) + np.abs(xm) + np.abs(yp) + np.abs(ym)) / scale[:, None, None]
     assert np.all(err[:, bad] <= corr[:, bad] + tol)
     assert np.all(got[0][bad] >= info["lo"][bad] * (1 - 1e-12)) and np.all(got[0][bad] <= info["hi"][bad] * (1 + 1e-12))
     assert np.all(pb.law.sigma(got)[bad] >= K[bad] * (1 - 1e-12))

@@ -188,6 +188,32 @@ def test_rotated_mesh_equals_the_cartesian_kernels(limiter):
     assert np.all(rel(b, ar) <= 1e-9), rel(b, ar)
 
 
+def test_sampled_full_size_curved_blast_fp64():
+    """The bench's curved workload at full size in FP64: the blast on the 1024x1024 p=3 mesh warped
+    by eps = 0.05 (periodic), one limited stage on the GPU; the oracle recomputes a sample of
+    elements (random, the four corners across the periodic seams, the blast centre) one by one."""
+    nel, p = 1024, 3
+    X, Y = scheme.Problem(laws.Euler(G), p, nel, nel).node_coords()
+    Xw, Yw = inputs.warped_coords(X, Y, 0.05)
+    del X, Y
+    pb = CurvedProblem(laws.Euler(G), p, nel, nel, Xw, Yw)
+    sv = sidp.Solver(law="euler", p=p, nx=nel, ny=nel, bc=PER, limiter="subcell", gamma=G)
+    sv.set_geometry(Xw, Yw)
+    U = inputs.blast(Xw, Yw)
+    del Xw, Yw
+    sv.set_state(U.reshape(4, -1))
+    dt = sv.compute_dt()
+    sv.stage(1, dt)
+    got = sv.get_state(1).reshape(4, pb.Ne, -1)
+    rng = np.random.default_rng(1)
+    c = nel // 2
+    sample = np.unique(np.concatenate([
+        rng.integers(0, pb.Ne, 64), [0, nel - 1, pb.Ne - nel, pb.Ne - 1],
+        [(c + dy) * nel + c + dx for dy in range(-3, 3) for dx in range(-3, 3)]]))
+    euler_fe_check(pb, U, dt, got[:, sample], elems=sample)
+    sv.close()
+
+
 def test_mixed_precision_warped_euler():
     """Mixed precision (float32 stages) on the warped mesh: positivity and agreement with FP64."""
     _, s64, X, Y = make("euler", 3, 8, 8, "subcell", L=(1.0, 1.0))
