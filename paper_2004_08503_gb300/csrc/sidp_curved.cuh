@@ -58,6 +58,7 @@ struct CurvedSmem {
   T lam[TH][2];               // Lambda of the x and y subcell faces (time step)
   T sig[TH];
   T alpha[TH];
+  T aK[CurvedGeom<P>::EPB];   // elementwise limiting: alpha_K per element
 };
 
 // Element-face neighbour of node (a, b) of element e on side s (0 W, 1 E, 2 S, 3 N): the global
@@ -208,7 +209,8 @@ __device__ __forceinline__ void curved_load(CurvedSmem<P, LAW, T>& s, const Inst
 
 namespace sidp {
 
-template <int P, class LAW, typename T>
+// ELW: elementwise limiting (Sec. 4.1.2, 4.2.1) instead of the subcell limiter.
+template <int P, class LAW, typename T, bool ELW = false>
 __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::value) k_stage_curved(const StageLaunch<T> A) {
   using Gm = CurvedGeom<P>;
   using V = Vec<T, LAW::NC>;
@@ -280,6 +282,51 @@ __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::va
     const T sl = (b > 0) ? s.sig[t - 1] : FX.sig, sr = (b < P) ? s.sig[t + 1] : FX.sig;
     const T sd = (a > 0) ? s.sig[t - n] : FY.sig, su = (a < P) ? s.sig[t + n] : FY.sig;
     K = tmin(tmin(s.sig[t], tmin(sl, sr)), tmin(sd, su));
+  }
+  if constexpr (ELW) {
+    // ---------------- elementwise: alpha-tilde_i for the nodal flux r_i = r_x + r_y, alpha_K = min
+    T rn[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) rn[q] = rx[q] + ry[q];
+    T at = T(1);
+    if (act && move) {
+      const T mdt = fdiv(m, dt);
+      const T Qp = tmax(T(0), mdt * (hi - uL[0]));
+      const T Qm = tmin(T(0), mdt * (lo - uL[0]));
+      const T Rp = (rn[0] > T(0)) ? tmin(T(1), fdiv(Qp, rn[0])) : T(1);
+      const T Rm = (rn[0] < T(0)) ? tmin(T(1), fdiv(Qm, rn[0])) : T(1);
+      at = tmin(Rp, Rm);
+      if constexpr (LAW::kEntropy) {
+        T w[NC];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) w[q] = dtm * rn[q];
+        int iters = 0, caps = 0;
+        at = entropy_limit_dir<LAW>(uL, K * (T(1) + Prec<T>::entropy_margin), w, at, lp, iters, caps);
+      }
+    }
+    s.alpha[t] = at;
+    if (I.dbg_lo && act) {
+      I.dbg_lo[g] = (double)lo;
+      I.dbg_hi[g] = (double)hi;
+      I.dbg_K[g] = (double)K;
+      I.dbg_alpha[g] = (double)at;
+    }
+    __syncthreads();
+    if (i == 0) {
+      T mn = T(1);
+      for (int j = 0; j < NN; ++j) mn = tmin(mn, s.alpha[le * NN + j]);
+      s.aK[le] = mn;
+    }
+    __syncthreads();
+    if (act) {
+      const T ak = s.aK[le];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        const T fe = uL[q] + ak * dtm * rn[q];
+        I.uout[q * N + g] = (I.c0 == T(0)) ? fe : I.c0 * I.u0[q * N + g] + I.c1 * fe;
+      }
+    }
+    return;
   }
   // ---------------- D: subcell fluxes (line prefix sums) and nodal alpha-tilde
   __syncthreads();  // all reads of the subcell-face fluxes done
@@ -408,6 +455,8 @@ cudaError_t launch_curved(const StageLaunch<T>& a, unsigned long long* dt_bits, 
     if (!attr_set) {
       cudaError_t err = cudaFuncSetAttribute(k_stage_curved<P, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (err != cudaSuccess) return err;
+      err = cudaFuncSetAttribute(k_stage_curved<P, LAW, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
       err = cudaFuncSetAttribute(k_dt_curved<P, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (err != cudaSuccess) return err;
       attr_set = true;
@@ -416,6 +465,7 @@ cudaError_t launch_curved(const StageLaunch<T>& a, unsigned long long* dt_bits, 
     const long long blocks = (Ne + Gm::EPB - 1) / Gm::EPB;
     if (blocks <= 0) return cudaSuccess;
     if (dt_bits) k_dt_curved<P, LAW, T><<<(unsigned)blocks, Gm::THREADS, smem, s>>>(a, dt_bits);
+    else if (a.limiter == SIDP_LIMITER_ELEMENTWISE) k_stage_curved<P, LAW, T, true><<<(unsigned)blocks, Gm::THREADS, smem, s>>>(a);
     else k_stage_curved<P, LAW, T><<<(unsigned)blocks, Gm::THREADS, smem, s>>>(a);
     return cudaGetLastError();
   }

@@ -6,7 +6,7 @@ against the Cartesian kernels."""
 import numpy as np
 import pytest
 
-from fe_compare import euler_fe_check, scalar_fe_check
+from fe_compare import elementwise_fe_check, euler_fe_check, scalar_fe_check
 from oracle import laws, scheme
 from oracle.curved import CurvedProblem
 from paper_2004_08503_gb300 import build, inputs, sidp
@@ -132,6 +132,18 @@ def test_euler_subcell_stage(p, bc):
     np.testing.assert_allclose(K, info["K"].ravel(), rtol=1e-12)
 
 
+@pytest.mark.parametrize("law,p", [("burgers", 3), ("advection", 2), ("euler", 3), ("euler", 5)])
+def test_elementwise_stage(law, p):
+    """Elementwise limiting (Sec. 4.1.2, 4.2.1) on the warped mesh: one stage against the oracle
+    with the comparator that bounds the rounding interval of alpha_K."""
+    pb, sv, X, Y = make(law, p, 6, 5, "elementwise")
+    U = inputs.vortex(X, Y) if law == "euler" else data(law, X, Y)
+    dt = pb.compute_dt(U)
+    sv.set_state(U.reshape(pb.law.nc, -1))
+    sv.stage(1, dt)
+    elementwise_fe_check(pb, U, dt, sv.get_state(1))
+
+
 def test_whole_steps_burgers():
     pb, sv, X, Y = make("burgers", 3, 5, 4, "lo", bc=MIXED_BC)
     U = data("burgers", X, Y)
@@ -229,7 +241,7 @@ def test_mixed_precision_warped_euler():
 
 def test_set_geometry_errors():
     X, Y = scheme.Problem(laws.Burgers(), 2, 3, 3).node_coords()
-    for kw in (dict(law="advection_var"), dict(limiter="elementwise"), dict(bc=("exact",) + ("outflow",) * 3),
+    for kw in (dict(law="advection_var"), dict(bc=("exact",) + ("outflow",) * 3),
                dict(sparsify=False), dict(smoothness=dict(gmin=0.0, gmax=1.0))):
         cfg = dict(law="burgers", p=2, nx=3, ny=3, bc=OUT, limiter="subcell")
         cfg.update(kw)

@@ -190,3 +190,24 @@ def test_high_order_operator_converges_at_the_design_order():
         errs.append(np.sum(cw.mK * np.abs(U[0] - exact)))
     rate = np.log2(errs[0] / errs[1])
     assert rate > 2.6, (errs, rate)
+
+
+@pytest.mark.parametrize("lawname", ["burgers", "euler"])
+def test_elementwise_limiting_on_a_curved_mesh(lawname):
+    """Sec. 4.1.2 / 4.2.1 on mapped elements: one alpha per element in [0, 1], the update inside the
+    bounds (and sigma >= K for Euler), and the element sums of m_i times the correction vanish
+    (conservation with the per-node masses)."""
+    law = laws.Euler(G) if lawname == "euler" else laws.Burgers()
+    cw = _warped(law, 3, 6, 5, L=(1.0, 5.0 / 6.0), limiter="elementwise")
+    X, Y = cw.node_coords()
+    U = inputs.vortex(X, Y) if lawname == "euler" else inputs.burgers_pulse(X, Y)
+    dt = cw.compute_dt(U)
+    out, info = cw.fe_stage(U, dt, full=True)
+    aK = info["alpha_K"]
+    assert np.all((aK >= 0) & (aK <= 1)) and np.any(aK > 0) and np.any(aK < 1)
+    tol = 1e-12 * np.abs(U[0]).max()
+    assert np.all(out[0] >= info["lo"] - tol) and np.all(out[0] <= info["hi"] + tol)
+    if lawname == "euler":
+        assert np.all(law.sigma(out) >= info["K"] * (1 - 1e-10))
+    corr = cw.mK[None] * (out - info["uL"])
+    assert np.abs(corr.sum(axis=2)).max() < 1e-14 * np.abs(U).max() * cw.mK.max() * 10
