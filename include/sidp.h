@@ -194,8 +194,8 @@ sidp_status sidp_curved_metrics(int p, int nx, int ny, const int* bc, const doub
  * computes the metric arrays as sidp_curved_metrics does and keeps them on the device in the
  * stage precision; from then on the time step and the stages use the curved-mesh kernels and
  * sidp_node_coords returns these coordinates.  Supported: laws burgers, advection and euler;
- * limiters none, lo, subcell and elementwise; periodic and outflow sides; without the smoothness
- * indicator and the unsparsified mode (SIDP_ERR_ARG otherwise).  The per-stage violation statistics are not
+ * limiters none, lo, subcell and elementwise, with or without the smoothness indicator (on the
+ * reference element); periodic and outflow sides; not the unsparsified mode (SIDP_ERR_ARG).  The per-stage violation statistics are not
  * collected on curved meshes (sidp_get_diag reports them as 0; mass and extrema use m_i).
  * Synchronous. */
 sidp_status sidp_set_geometry(sidp_ctx* ctx, const double* x, const double* y);

@@ -25,7 +25,10 @@ its own map T_K: the caller gives the physical coordinates (X, Y) of every Gauss
     at node j), d_ij of Eq. (dij) (n_ij = -c_ij/|c_ij|, c21) and the bar states of
     Eq. (bar-states) per ordered pair (on a curved element c_ij != -c_ji, so the two nodes of a
     pair have different bar states); face terms of Eq. (lf-alternative) with the face normals;
-  * limiting, CFL and SSP-RK3 as on Cartesian meshes, with the per-node masses.
+  * limiting, CFL and SSP-RK3 as on Cartesian meshes, with the per-node masses;
+  * the smoothness indicator of Sec. 4.4 on the reference element.
+    reading: the modal expansion and its L2 norms are those of the reference element (the map's
+    Jacobian does not weight them), so s_K measures the polynomial on the reference square.
 
 Boundaries: periodic (the mapped mesh must then be periodic: coordinates across a periodic
 side differ by the period) and outflow.
@@ -42,14 +45,16 @@ class CurvedProblem(Problem):
     """A Problem on the mapped mesh with node coordinates (X, Y).  correct=False keeps the
     uncorrected metric terms in the low-order operator (for the tests of Sec. 3.1)."""
 
-    def __init__(self, law, p, nx, ny, X, Y, bc=("periodic",) * 4, cfl=0.5, limiter="subcell", correct=True):
+    def __init__(self, law, p, nx, ny, X, Y, bc=("periodic",) * 4, cfl=0.5, limiter="subcell", correct=True,
+                 smoothness=None):
         for s in bc:
             if s not in ("periodic", "outflow"):
                 raise ValueError("curved meshes take periodic or outflow boundaries")
         if law.name == "advection_var":
             raise ValueError("variable-velocity advection is defined on Cartesian meshes")
         # reference operators and pair structure of a unit Cartesian mesh (h = 1)
-        super().__init__(law, p, nx, ny, domain=(0.0, float(nx), 0.0, float(ny)), bc=bc, cfl=cfl, limiter=limiter)
+        super().__init__(law, p, nx, ny, domain=(0.0, float(nx), 0.0, float(ny)), bc=bc, cfl=cfl, limiter=limiter,
+                         smoothness=smoothness)
         n, NN, Ne = self.n, self.n * self.n, self.Ne
         self.X = np.asarray(X, dtype=float).reshape(Ne, NN).copy()
         self.Y = np.asarray(Y, dtype=float).reshape(Ne, NN).copy()

@@ -637,8 +637,8 @@ sidp_status sidp_set_geometry(sidp_ctx* c, const double* x, const double* y) {
   const sidp_config& f = c->cfg;
   if (f.law == SIDP_LAW_ADVECTION_VAR2D)
     return fail(c, SIDP_ERR_ARG, "variable-velocity advection is defined on Cartesian meshes only");
-  if (f.smoothness || f.unsparsified)
-    return fail(c, SIDP_ERR_ARG, "curved meshes take no smoothness indicator and no unsparsified mode");
+  if (f.unsparsified)
+    return fail(c, SIDP_ERR_ARG, "curved meshes take no unsparsified mode");
   for (int k = 0; k < 4; ++k)
     if (f.bc[k] != SIDP_BC_PERIODIC && f.bc[k] != SIDP_BC_OUTFLOW)
       return fail(c, SIDP_ERR_ARG, "curved meshes take periodic or outflow sides");

@@ -59,6 +59,7 @@ struct CurvedSmem {
   T sig[TH];
   T alpha[TH];
   T aK[CurvedGeom<P>::EPB];   // elementwise limiting: alpha_K per element
+  T eps[CurvedGeom<P>::EPB];  // smoothness indicator: epsilon_K per element
 };
 
 // Element-face neighbour of node (a, b) of element e on side s (0 W, 1 E, 2 S, 3 N): the global
@@ -232,6 +233,43 @@ __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::va
   bool onx, ony;
   curved_load<P, LAW>(s, I, lp, e, act, t, a, b, u, ax, FX, FY, onx, ony);
 
+  // ---------------- smoothness indicator (Sec. 4.4) on the reference element: Legendre
+  // coefficients of the limited field (separable nodal -> modal transform), s_K =
+  // log10(||u - u-hat||^2 / ||u||^2) with u-hat dropping the modes of degree p in either variable
+  const SmoothnessT<T>& si = A.si;
+  if (si.on && limiter >= 2) {
+    const int base = le * NN;
+    T c1 = T(0);
+#pragma unroll
+    for (int c = 0; c < n; ++c) c1 += A.tab.Vinv[b * n + c] * s.u[base + a * n + c].v[0];
+    s.alpha[t] = c1;
+    __syncthreads();
+    T cc = T(0);
+#pragma unroll
+    for (int c = 0; c < n; ++c) cc += A.tab.Vinv[a * n + c] * s.alpha[base + c * n + b];
+    const T wgt = cc * cc * A.tab.nrm[a] * A.tab.nrm[b];
+    __syncthreads();
+    s.alpha[t] = wgt;
+    __syncthreads();
+    if (i == 0) {
+      T tot = T(0), top = T(0);
+      for (int j = 0; j < NN; ++j) {
+        const T v = s.alpha[base + j];
+        tot += v;
+        if (j / n == P || j % n == P) top += v;
+      }
+      T ek = T(0);
+      if (tot > T(0) && top > T(0)) {
+        const T sk = plog10(top / tot);
+        ek = (sk < si.s0 - si.kappa) ? T(0)
+           : (sk > si.s0 + si.kappa) ? T(1)
+           : T(0.5) + T(0.5) * psin(T(3.14159265358979323846) * (sk - si.s0) / (T(2) * si.kappa));
+      }
+      s.eps[le] = ek;
+    }
+    __syncthreads();
+  }
+
   // ---------------- C: residuals, low-order state, bounds
   const T dt = *I.dtT;
   const bool move = (dt > T(0)) && (dt < T(FLT_MAX));
@@ -275,8 +313,13 @@ __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::va
   if (limiter < 2) return;  // uniform across the CTA
   const T bl = (b > 0) ? s.bar[t - 1][1] : FX.bar, br = (b < P) ? s.bar[t][0] : FX.bar;
   const T bd = (a > 0) ? s.bar[t - n][3] : FY.bar, bu = (a < P) ? s.bar[t][2] : FY.bar;
-  const T lo = tmin(tmin(u[0], tmin(bl, br)), tmin(bd, bu));
-  const T hi = tmax(tmax(u[0], tmax(bl, br)), tmax(bd, bu));
+  T lo = tmin(tmin(u[0], tmin(bl, br)), tmin(bd, bu));
+  T hi = tmax(tmax(u[0], tmax(bl, br)), tmax(bd, bu));
+  if (si.on) {  // Eq. relaxed-bounds
+    const T ek = s.eps[le];
+    lo = ek * lo + (T(1) - ek) * si.gmin;
+    hi = ek * hi + (T(1) - ek) * si.gmax;
+  }
   T K = T(0);
   if constexpr (LAW::kEntropy) {
     const T sl = (b > 0) ? s.sig[t - 1] : FX.sig, sr = (b < P) ? s.sig[t + 1] : FX.sig;

@@ -29,7 +29,7 @@ def _law(name):
     return {"euler": laws.Euler(G), "burgers": laws.Burgers(), "advection": laws.Advection(BETA)}[name]
 
 
-def make(law, p, nx, ny, limiter, bc=PER, eps=0.08, L=None, precision="fp64", theta=None):
+def make(law, p, nx, ny, limiter, bc=PER, eps=0.08, L=None, precision="fp64", theta=None, smooth=None):
     lo = _law(law)
     L = (1.0, ny / nx) if L is None else L   # square elements
     X, Y = scheme.Problem(lo, p, nx, ny, domain=(0.0, L[0], 0.0, L[1])).node_coords()
@@ -37,9 +37,9 @@ def make(law, p, nx, ny, limiter, bc=PER, eps=0.08, L=None, precision="fp64", th
         Xm, Ym = inputs.warped_coords(X, Y, eps, L)
     else:
         Xm, Ym = inputs.rotated_coords(X, Y, theta)
-    pb = CurvedProblem(lo, p, nx, ny, Xm, Ym, bc=bc, limiter=limiter)
+    pb = CurvedProblem(lo, p, nx, ny, Xm, Ym, bc=bc, limiter=limiter, smoothness=smooth)
     sv = sidp.Solver(law=law, p=p, nx=nx, ny=ny, domain=(0.0, L[0], 0.0, L[1]), bc=bc, limiter=limiter, gamma=G,
-                     beta=BETA, precision=precision)
+                     beta=BETA, precision=precision, smoothness=smooth)
     sv.set_geometry(Xm, Ym)
     return pb, sv, Xm, Ym
 
@@ -144,6 +144,30 @@ def test_elementwise_stage(law, p):
     elementwise_fe_check(pb, U, dt, sv.get_state(1))
 
 
+@pytest.mark.parametrize("law,limiter,p", [("burgers", "subcell", 3), ("advection", "subcell", 4),
+                                            ("burgers", "elementwise", 3), ("advection", "elementwise", 2)])
+def test_smoothness_indicator_stage(law, limiter, p):
+    """Sec. 4.4 on mapped elements: the relaxed bounds (captured) and the limited stage."""
+    smooth = dict(gmin=-0.5, gmax=2.5)
+    pb, sv, X, Y = make(law, p, 6, 5, limiter, smooth=smooth)
+    U = data(law, X, Y)
+    dt = pb.compute_dt(U)
+    sv.set_state(U.reshape(1, -1))
+    sv.set_debug(True)
+    sv.stage(1, dt)
+    got = sv.get_state(1)
+    _, info = pb.fe_stage(U, dt, full=True)
+    eps, _ = pb.smoothness_factor(U, np.arange(pb.Ne))
+    assert np.any(eps > 0.05) and np.any(eps < 0.95)   # the indicator is active and partial
+    bd = sv.bounds()
+    np.testing.assert_allclose(bd["lo"], info["lo"].ravel(), rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(bd["hi"], info["hi"].ravel(), rtol=1e-10, atol=1e-12)
+    if limiter == "subcell":
+        scalar_fe_check(pb, U, dt, got)
+    else:
+        elementwise_fe_check(pb, U, dt, got)
+
+
 def test_whole_steps_burgers():
     pb, sv, X, Y = make("burgers", 3, 5, 4, "lo", bc=MIXED_BC)
     U = data("burgers", X, Y)
@@ -241,8 +265,7 @@ def test_mixed_precision_warped_euler():
 
 def test_set_geometry_errors():
     X, Y = scheme.Problem(laws.Burgers(), 2, 3, 3).node_coords()
-    for kw in (dict(law="advection_var"), dict(bc=("exact",) + ("outflow",) * 3),
-               dict(sparsify=False), dict(smoothness=dict(gmin=0.0, gmax=1.0))):
+    for kw in (dict(law="advection_var"), dict(bc=("exact",) + ("outflow",) * 3), dict(sparsify=False)):
         cfg = dict(law="burgers", p=2, nx=3, ny=3, bc=OUT, limiter="subcell")
         cfg.update(kw)
         sv = sidp.Solver(**cfg)

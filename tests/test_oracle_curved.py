@@ -211,3 +211,28 @@ def test_elementwise_limiting_on_a_curved_mesh(lawname):
         assert np.all(law.sigma(out) >= info["K"] * (1 - 1e-10))
     corr = cw.mK[None] * (out - info["uL"])
     assert np.abs(corr.sum(axis=2)).max() < 1e-14 * np.abs(U).max() * cw.mK.max() * 10
+
+
+def test_smoothness_indicator_on_cartesian_coordinates_matches_the_cartesian_oracle():
+    """Sec. 4.4: with Cartesian node coordinates the curved path's indicator, relaxed bounds and
+    limited step equal the Cartesian oracle's; on the warped mesh epsilon_K stays in [0, 1] and the
+    relaxed bounds bracket the unrelaxed ones' convex combination with g^min, g^max."""
+    smooth = dict(gmin=-0.5, gmax=2.5)
+    law = laws.Burgers()
+    pc = _cart(law, 3, 6, 5, L=(1.0, 5.0 / 6.0), smoothness=smooth)
+    X, Y = pc.node_coords()
+    cu = CurvedProblem(law, 3, 6, 5, X, Y, smoothness=smooth)
+    U = inputs.burgers_pulse(X, Y)
+    np.testing.assert_allclose(cu.ssp_rk3_step(U)[0], pc.ssp_rk3_step(U)[0], rtol=0, atol=1e-13)
+    cw = _warped(law, 3, 6, 5, L=(1.0, 5.0 / 6.0), smoothness=smooth)
+    Xw, Yw = cw.node_coords()
+    Uw = inputs.burgers_pulse(Xw, Yw)
+    eps, _ = cw.smoothness_factor(Uw, np.arange(cw.Ne))
+    assert np.all((eps >= 0) & (eps <= 1)) and np.any(eps > 0.05) and np.any(eps < 0.95)
+    dt = cw.compute_dt(Uw)
+    _, info = cw.fe_stage(Uw, dt, full=True)
+    cw.smoothness = None
+    _, raw = cw.fe_stage(Uw, dt, full=True)
+    e = eps[:, None]
+    np.testing.assert_allclose(info["lo"], e * raw["lo"] + (1 - e) * smooth["gmin"], rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(info["hi"], e * raw["hi"] + (1 - e) * smooth["gmax"], rtol=1e-14, atol=1e-15)
