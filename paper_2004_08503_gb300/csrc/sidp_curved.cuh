@@ -21,6 +21,10 @@
 // d_ij = w Lambda / 2 (Eq. dij with n_ij = -c_ij/|c_ij|), and the two nodes of a subcell face
 // have the bar states u-bar = (u_b + u_{b+1})/2 - row_other . (F_{b+1} - F_b) / (2 Lambda)
 // (Eq. bar-states with c_ij != -c_ji).
+//
+// Limiters: none, low-order, subcell (Sec. 4.1.3, 4.3) and, as a compile-time variant, elementwise
+// (Sec. 4.1.2, 4.2.1); the smoothness indicator of Sec. 4.4 relaxes the bounds when it is on (its
+// modal expansion taken on the reference element).
 #pragma once
 #include "sidp_kernels.cuh"
 

@@ -53,3 +53,38 @@ def test_metric_errors():
         sidp.sidp_curved_metrics(2, 3, 3, ("exact",) + ("outflow",) * 3, X, Y)
     with pytest.raises(sidp.SidpError):
         sidp.sidp_curved_metrics(8, 3, 3, ("periodic",) * 4, X, Y)
+
+
+@pytest.mark.parametrize("p", [2, 3, 5, 7])
+def test_library_arrays_satisfy_the_identities(p):
+    """The library's own arrays, checked against the mathematics rather than the oracle: the
+    metric identity Eq. metric for its rows of G J^-1, Eq. idp-sbp for its corrected rows with its
+    face normals, and sum_i m_i = the area of the mapped domain (periodic warp: the area of the
+    undeformed one)."""
+    from oracle import gll
+    nx, ny = 4, 3
+    X, Y = scheme.Problem(laws.Burgers(), p, nx, ny, domain=(0, 1, 0, 0.75)).node_coords()
+    Xw, Yw = inputs.warped_coords(X, Y, 0.08, (1.0, 0.75))
+    g = sidp.sidp_curved_metrics(p, nx, ny, ("periodic",) * 4, Xw, Yw)
+    n, Ne = p + 1, nx * ny
+    xi, w = gll.gll(p)
+    M1 = np.diag(w)
+    D, Dh = gll.diff_matrix(p), gll.sparse_diff_matrix(p)
+    DX, DY = np.kron(M1, D), np.kron(D, M1)
+    DhX, DhY = np.kron(M1, Dh), np.kron(Dh, M1)
+    R = g[0:4].reshape(4, Ne, n * n)
+    Q = g[4:8].reshape(4, Ne, n * n)
+    NXf = g[9:11].reshape(2, Ne, n, n)
+    NYf = g[11:13].reshape(2, Ne, n, n)
+    scale = np.abs(R).max()
+    for j in (0, 1):
+        ident = R[j] @ DX.T + R[2 + j] @ DY.T          # sum_i D_i (G J^-1)_ij 1
+        assert np.abs(ident).max() < 1e-13 * scale
+        bnd = np.zeros((Ne, n, n))                      # sum_e B_e n_{e,j} 1, outward normals
+        bnd[:, :, 0] -= w[None, :] * NXf[j][:, :, 0]
+        bnd[:, :, p] += w[None, :] * NXf[j][:, :, p]
+        bnd[:, 0, :] -= w[None, :] * NYf[j][:, 0, :]
+        bnd[:, p, :] += w[None, :] * NYf[j][:, p, :]
+        lhs = Q[j] @ DhX + Q[2 + j] @ DhY
+        assert np.abs(lhs - bnd.reshape(Ne, -1)).max() < 1e-13 * scale
+    assert np.sum(g[8]) == pytest.approx(0.75, rel=1e-12)
