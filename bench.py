@@ -57,6 +57,14 @@ WORKLOAD_CURVED = ("2D Euler blast on a curved mesh: 1024x1024 elements, p=3, no
 HBM_FALLBACK = 6800.0
 
 
+def workload_label(nel):
+    """The headline workload's description at nel x nel elements."""
+    if nel == 1024:
+        return WORKLOAD
+    nodes = nel * nel * (P + 1) ** 2
+    return WORKLOAD.replace("1024x1024", f"{nel}x{nel}").replace("16.8M nodes", f"{nodes / 1e6:.1f}M nodes")
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -570,7 +578,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD if NEL == 1024 else WORKLOAD.replace("1024x1024", f"{NEL}x{NEL}"),
+                "config": {"workload": workload_label(NEL),
                            "nodes_per_gpu": nodes, "precision": "mixed (f32 state/stage, f64 dt)",
                            "l2": "state >= 151 MB per buffer > L2 (no flush needed)",
                            "parallelism": "independent replica per GPU"},

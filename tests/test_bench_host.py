@@ -14,3 +14,8 @@ def test_other_ceilings_arithmetic():
     assert oc["issue"]["frac"] == pytest.approx(issue / (152 * 4 * 1e9))
     assert bench.other_ceilings(nodes, kt, {}) is None        # no clock sample
     assert bench.other_ceilings(nodes, [0.0, 1e-6, 1e-6], {"sm_mhz": 1.0}) is None
+
+
+def test_workload_label_follows_the_element_count():
+    assert bench.workload_label(1024) == bench.WORKLOAD
+    assert "768x768" in bench.workload_label(768) and "9.4M nodes" in bench.workload_label(768)
