@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -449,7 +450,7 @@ const char* sidp_status_str(sidp_status s) {
 
 const char* sidp_last_error(const sidp_ctx* ctx) { return ctx ? ctx->err.c_str() : g_last_error.c_str(); }
 
-sidp_status sidp_create(sidp_ctx** out, const sidp_config* cfg, void* cuda_stream) {
+sidp_status sidp_create(sidp_ctx** out, const sidp_config* cfg, void* cuda_stream) try {
   if (!out) return fail(nullptr, SIDP_ERR_ARG, "null output pointer");
   *out = nullptr;
   std::string msg;
@@ -502,6 +503,10 @@ sidp_status sidp_create(sidp_ctx** out, const sidp_config* cfg, void* cuda_strea
     return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
   *out = c;
   return SIDP_OK;
+} catch (const std::bad_alloc&) {
+  return fail(nullptr, SIDP_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(nullptr, SIDP_ERR_ARG, "unexpected host exception");
 }
 
 sidp_status sidp_destroy(sidp_ctx* c) {
@@ -552,7 +557,7 @@ sidp_status sidp_node_coords(const sidp_ctx* c, double* x, double* y) {
   return SIDP_OK;
 }
 
-sidp_status sidp_set_state(sidp_ctx* c, const double* u) {
+sidp_status sidp_set_state(sidp_ctx* c, const double* u) try {
   if (!c || !u) return fail(c, SIDP_ERR_ARG, "null argument");
   const long long N = c->N;
   for (long long i = 0; i < c->nc * N; ++i)
@@ -572,12 +577,20 @@ sidp_status sidp_set_state(sidp_ctx* c, const double* u) {
   CUDA_TRY(c, cudaMemcpy(c->d_stats, &zs, sizeof(zs), cudaMemcpyHostToDevice));
   c->stage_done = 0;
   return SIDP_OK;
+} catch (const std::bad_alloc&) {
+  return fail(c, SIDP_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(c, SIDP_ERR_ARG, "unexpected host exception");
 }
 
-sidp_status sidp_get_state(sidp_ctx* c, int which, double* u) {
+sidp_status sidp_get_state(sidp_ctx* c, int which, double* u) try {
   if (!c || !u) return fail(c, SIDP_ERR_ARG, "null argument");
   if (which < 0 || which > 2) return fail(c, SIDP_ERR_ARG, "which must be 0, 1 or 2");
   return c->mixed ? download<float>(c, c->d_u[which], u, c->nc * c->N) : download<double>(c, c->d_u[which], u, c->nc * c->N);
+} catch (const std::bad_alloc&) {
+  return fail(c, SIDP_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(c, SIDP_ERR_ARG, "unexpected host exception");
 }
 
 sidp_status sidp_upload_state(sidp_ctx* c, const void* host) {
@@ -594,7 +607,7 @@ sidp_status sidp_download_state(sidp_ctx* c, int which, void* host) {
   return SIDP_OK;
 }
 
-sidp_status sidp_set_ghost_state(sidp_ctx* c, int side, const double* u) {
+sidp_status sidp_set_ghost_state(sidp_ctx* c, int side, const double* u) try {
   if (!c || !u || side < 0 || side > 3) return fail(c, SIDP_ERR_ARG, "bad argument");
   const long long nside = (side < 2) ? c->cfg.ny : c->cfg.nx;
   const long long count = c->nc * nside * c->n;
@@ -603,6 +616,10 @@ sidp_status sidp_set_ghost_state(sidp_ctx* c, int side, const double* u) {
     drop_graph(c);
   }
   return c->mixed ? upload<float>(c, c->d_ghost[side], u, count) : upload<double>(c, c->d_ghost[side], u, count);
+} catch (const std::bad_alloc&) {
+  return fail(c, SIDP_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(c, SIDP_ERR_ARG, "unexpected host exception");
 }
 
 
@@ -625,14 +642,18 @@ sidp_status sidp_set_split_boundary(sidp_ctx* c, int side, double s0, double spe
 }
 
 sidp_status sidp_curved_metrics(int p, int nx, int ny, const int* bc, const double* x, const double* y,
-                                double* out) {
+                                double* out) try {
   std::string msg;
   const sidp_status st = curved_metrics(p, nx, ny, bc, x, y, out, msg);
   if (st != SIDP_OK) return fail(nullptr, st, msg);
   return SIDP_OK;
+} catch (const std::bad_alloc&) {
+  return fail(nullptr, SIDP_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(nullptr, SIDP_ERR_ARG, "unexpected host exception");
 }
 
-sidp_status sidp_set_geometry(sidp_ctx* c, const double* x, const double* y) {
+sidp_status sidp_set_geometry(sidp_ctx* c, const double* x, const double* y) try {
   if (!c || !x || !y) return fail(c, SIDP_ERR_ARG, "null argument");
   const sidp_config& f = c->cfg;
   if (f.law == SIDP_LAW_ADVECTION_VAR2D)
@@ -662,6 +683,10 @@ sidp_status sidp_set_geometry(sidp_ctx* c, const double* x, const double* y) {
   c->tile = 0;
   drop_graph(c);
   return SIDP_OK;
+} catch (const std::bad_alloc&) {
+  return fail(c, SIDP_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(c, SIDP_ERR_ARG, "unexpected host exception");
 }
 
 sidp_status sidp_set_time(sidp_ctx* c, double t) {
@@ -749,7 +774,7 @@ sidp_status sidp_set_stats(sidp_ctx* c, int on) {
   return SIDP_OK;
 }
 
-sidp_status sidp_set_debug(sidp_ctx* c, int on) {
+sidp_status sidp_set_debug(sidp_ctx* c, int on) try {
   if (!c) return fail(c, SIDP_ERR_ARG, "null context");
   if (on && !c->d_dbg) {
     if (cudaMalloc(&c->d_dbg, 4 * c->N * sizeof(double)) != cudaSuccess) return fail(c, SIDP_ERR_OOM, "debug allocation failed");
@@ -758,9 +783,13 @@ sidp_status sidp_set_debug(sidp_ctx* c, int on) {
   if ((on != 0) != c->debug) drop_graph(c);
   c->debug = on != 0;
   return SIDP_OK;
+} catch (const std::bad_alloc&) {
+  return fail(c, SIDP_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(c, SIDP_ERR_ARG, "unexpected host exception");
 }
 
-sidp_status sidp_get_bounds(sidp_ctx* c, double* lo, double* hi, double* K, double* alpha) {
+sidp_status sidp_get_bounds(sidp_ctx* c, double* lo, double* hi, double* K, double* alpha) try {
   if (!c) return fail(c, SIDP_ERR_ARG, "null context");
   if (!c->d_dbg) return fail(c, SIDP_ERR_STATE, "debug capture was never enabled");
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -768,6 +797,10 @@ sidp_status sidp_get_bounds(sidp_ctx* c, double* lo, double* hi, double* K, doub
   for (int i = 0; i < 4; ++i)
     if (dst[i]) CUDA_TRY(c, cudaMemcpy(dst[i], c->d_dbg + i * c->N, c->N * sizeof(double), cudaMemcpyDeviceToHost));
   return SIDP_OK;
+} catch (const std::bad_alloc&) {
+  return fail(c, SIDP_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return fail(c, SIDP_ERR_ARG, "unexpected host exception");
 }
 
 sidp_status sidp_get_diag(sidp_ctx* c, sidp_diag* out) {

@@ -17,6 +17,7 @@
 #include <cstddef>
 #include <cstring>
 #include <map>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -221,7 +222,7 @@ cudaError_t run_batch_step(sidp_batch* b) {
 
 extern "C" {
 
-sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int count, void* cuda_stream) {
+sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int count, void* cuda_stream) try {
   if (!out) return bfail(nullptr, SIDP_ERR_ARG, "null output pointer");
   *out = nullptr;
   if (!cfgs || count < 1) return bfail(nullptr, SIDP_ERR_ARG, "empty batch");
@@ -325,6 +326,10 @@ sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int cou
   }
   *out = b;
   return SIDP_OK;
+} catch (const std::bad_alloc&) {
+  return bfail(nullptr, SIDP_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return bfail(nullptr, SIDP_ERR_ARG, "unexpected host exception");
 }
 
 sidp_status sidp_batch_destroy(sidp_batch* b) {
@@ -363,7 +368,7 @@ sidp_status sidp_batch_total_nodes(const sidp_batch* b, long long* n_nodes) {
   return SIDP_OK;
 }
 
-sidp_status sidp_batch_node_coords(const sidp_batch* b, int i, double* x, double* y) {
+sidp_status sidp_batch_node_coords(const sidp_batch* b, int i, double* x, double* y) try {
   if (!b || i < 0 || i >= b->n || !x || !y) return bfail(nullptr, SIDP_ERR_ARG, "bad argument");
   const sidp_config& c = b->cfgs[i];
   double xi[kMaxN], w[kMaxN], D[kMaxN * kMaxN];
@@ -379,9 +384,13 @@ sidp_status sidp_batch_node_coords(const sidp_batch* b, int i, double* x, double
       }
   }
   return SIDP_OK;
+} catch (const std::bad_alloc&) {
+  return bfail(nullptr, SIDP_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return bfail(nullptr, SIDP_ERR_ARG, "unexpected host exception");
 }
 
-sidp_status sidp_batch_set_state(sidp_batch* b, int i, const double* u) {
+sidp_status sidp_batch_set_state(sidp_batch* b, int i, const double* u) try {
   if (!b || i < 0 || i >= b->n || !u) return bfail(b, SIDP_ERR_ARG, "bad argument");
   const long long N = b->N[i], cnt = b->nc * N;
   for (long long j = 0; j < cnt; ++j)
@@ -408,9 +417,13 @@ sidp_status sidp_batch_set_state(sidp_batch* b, int i, const double* u) {
     BCUDA(b, cudaStreamSynchronize(b->stream));
   }
   return SIDP_OK;
+} catch (const std::bad_alloc&) {
+  return bfail(b, SIDP_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return bfail(b, SIDP_ERR_ARG, "unexpected host exception");
 }
 
-sidp_status sidp_batch_get_state(sidp_batch* b, int i, double* u) {
+sidp_status sidp_batch_get_state(sidp_batch* b, int i, double* u) try {
   if (!b || i < 0 || i >= b->n || !u) return bfail(b, SIDP_ERR_ARG, "bad argument");
   const long long cnt = b->nc * b->N[i];
   const char* src = static_cast<const char*>(b->d_u[0]) + b->off[i] * b->esize;
@@ -424,6 +437,10 @@ sidp_status sidp_batch_get_state(sidp_batch* b, int i, double* u) {
     BCUDA(b, cudaStreamSynchronize(b->stream));
   }
   return SIDP_OK;
+} catch (const std::bad_alloc&) {
+  return bfail(b, SIDP_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return bfail(b, SIDP_ERR_ARG, "unexpected host exception");
 }
 
 sidp_status sidp_batch_step(sidp_batch* b, int nsteps) {
@@ -452,7 +469,7 @@ sidp_status sidp_batch_step(sidp_batch* b, int nsteps) {
   return SIDP_OK;
 }
 
-sidp_status sidp_batch_get_diag(sidp_batch* b, int i, sidp_diag* out) {
+sidp_status sidp_batch_get_diag(sidp_batch* b, int i, sidp_diag* out) try {
   if (!b || i < 0 || i >= b->n || !out) return bfail(b, SIDP_ERR_ARG, "bad argument");
   std::memset(out, 0, sizeof(*out));
   const sidp_config& c = b->cfgs[i];
@@ -496,6 +513,10 @@ sidp_status sidp_batch_get_diag(sidp_batch* b, int i, sidp_diag* out) {
   out->rootfind_cap_hits = (long long)ss.rootfind_cap_hits;
   if (out->nonfinite) return bfail(b, SIDP_ERR_NONFINITE, "state holds non-finite values");
   return SIDP_OK;
+} catch (const std::bad_alloc&) {
+  return bfail(b, SIDP_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return bfail(b, SIDP_ERR_ARG, "unexpected host exception");
 }
 
 sidp_status sidp_batch_set_stats(sidp_batch* b, int on) {
