@@ -48,3 +48,24 @@ def test_null_arguments(lib):
     assert lib.sidp_set_state(None, None) == 1
     assert lib.sidp_step(None, 1) == 1
     assert lib.sidp_destroy(None) == 0
+
+
+def test_plain_c_client_compiles_links_and_runs(lib, tmp_path):
+    """The header is valid C99 and the library is usable from C without Python: a C client of
+    sidp_curved_metrics (host only) built with gcc -std=c99 -Wall -Werror against libsidp.so."""
+    import os
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    here = os.path.dirname(os.path.abspath(__file__))
+    root = os.path.dirname(here)
+    pkg = os.path.dirname(sidp.LIB_PATH)
+    exe = str(tmp_path / "metrics_client")
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(root, "include"),
+                    os.path.join(here, "c_abi", "metrics_client.c"), "-o", exe, "-L", pkg, "-lsidp",
+                    "-Wl,-rpath," + pkg, "-lm"], check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    area, err = float(out[0].split()[1]), float(out[0].split()[3])
+    assert abs(area - 6.0) < 1e-13 and err < 1e-14, out
+    assert out[1] == "mirrored invalid argument"
