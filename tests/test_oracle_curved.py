@@ -236,3 +236,25 @@ def test_smoothness_indicator_on_cartesian_coordinates_matches_the_cartesian_ora
     e = eps[:, None]
     np.testing.assert_allclose(info["lo"], e * raw["lo"] + (1 - e) * smooth["gmin"], rtol=1e-14, atol=1e-15)
     np.testing.assert_allclose(info["hi"], e * raw["hi"] + (1 - e) * smooth["gmax"], rtol=1e-14, atol=1e-15)
+
+
+def test_no_correction_at_p1():
+    """At p = 1 the sparsified derivative equals the DG-SEM one (Eq. didp), so the strong-form
+    metric identity already gives Eq. idp-sbp: the minimum-norm correction is zero on any mesh."""
+    cw = _warped(laws.Euler(G), 1, 5, 4, eps=0.1, L=(1.0, 0.8))
+    assert np.abs(cw.C).max() < 1e-15 * np.abs(cw.R1).max() * 100
+
+
+@pytest.mark.parametrize("p", [2, 3, 5])
+def test_bar_states_on_curved_elements_are_admissible(p):
+    """Eq. bar-states with the per-ordered-pair c_ij of a mapped element: with d_ij at least the
+    wave-speed bound along n_ij times |c_ij|, every bar state (pairs and element faces) is an
+    average of a Riemann fan, so density and pressure stay positive for strong data."""
+    law = laws.Euler(G)
+    cw = _warped(law, p, 5, 4, eps=0.1, bc=("outflow",) * 4, L=(1.0, 0.8))
+    X, Y = cw.node_coords()
+    for seed in range(4):
+        U = inputs.four_quadrant(X, Y, seed)
+        _, bars, _, _ = cw.lo_residual(U, want_bars=True)
+        for b in [bars["pairs"]] + list(bars["faces"].values()):
+            assert b[0].min() > 0 and law.pressure(b).min() > 0
