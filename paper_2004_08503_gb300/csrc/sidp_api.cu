@@ -106,6 +106,10 @@ thread_local std::string g_last_error;
 
 }  // namespace
 
+namespace sidp {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace sidp
+
 struct sidp_ctx {
   sidp_config cfg{};
   int n = 0, NN = 0, nc = 0;

@@ -174,6 +174,7 @@ inline SmoothnessT<T> make_smoothness(const sidp_config& c) {
 // Host-side helpers shared by the single-instance and batched entry points.
 int tuned_tile(int law, int p, int mixed);  // autotuned tile index, or -1 when not tuned yet
 sidp_status validate_config(const sidp_config* cfg, std::string& msg);
+void set_last_error(const std::string& msg);  // the message sidp_last_error(NULL) returns
 
 // Host tables (float64), computed once.
 void gll_tables(int p, double* xi, double* w, double* D);

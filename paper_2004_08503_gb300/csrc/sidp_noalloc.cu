@@ -17,10 +17,12 @@
 //
 // Set-up: the device address of g_dt_partials is looked up with cudaGetSymbolAddress the first
 // time the entry point runs on a device (with that device current) and cached per device.  Make
-// that first call outside any stream capture.
+// that first call outside any stream capture.  The cached address belongs to the device's primary
+// context: resetting the device (cudaDeviceReset) after the first call is not supported.
 #include <cfloat>
 #include <cmath>
 #include <mutex>
+#include <string>
 
 #include "sidp.h"
 #include "sidp_laws.cuh"
@@ -89,7 +91,7 @@ k_dt_static(const T* __restrict__ u, long long N, int nx, int ny, int4 bc4, doub
     // per-node bound in the stage precision, like the context's time-step kernel
     const T hT = T(h), wa = tab.w[a], wb = tab.w[b];
     const T sumd = T(0.5) * hT * wa * (lam[0] + lam[1]) + T(0.5) * hT * wb * (lam[2] + lam[3]);
-    if (sumd > T(0)) val = (double)(hT * hT * wa * wb / (T(2) * sumd));
+    if (sumd > T(0)) val = (double)fdiv(hT * hT * wa * wb, T(2) * sumd);  // the context kernel's division
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) val = fmin(val, __shfl_xor_sync(0xffffffffu, val, o));
@@ -170,17 +172,26 @@ double* g_static_ptr[64] = {nullptr};
 extern "C" sidp_status sidp_compute_dt_static(const sidp_config* cfg, const void* d_state, double* d_dt,
                                               void* cuda_stream) {
   using namespace sidp;
-  if (!cfg || !d_state || !d_dt) return SIDP_ERR_ARG;
-  if (cfg->law != SIDP_LAW_BURGERS2D && cfg->law != SIDP_LAW_EULER2D && cfg->law != SIDP_LAW_ADVECTION2D) return SIDP_ERR_ARG;
-  if (cfg->p < 1 || cfg->p > kMaxP || cfg->nx < 1 || cfg->ny < 1) return SIDP_ERR_ARG;
-  if (cfg->precision != SIDP_FP64 && cfg->precision != SIDP_MIXED) return SIDP_ERR_ARG;
-  if (!(cfg->cfl > 0.0) || cfg->cfl > 1.0) return SIDP_ERR_ARG;
+  std::string msg;
+  const sidp_status st = validate_config(cfg, msg);  // the context's checks (gamma, periodic pairing, ...)
+  if (st != SIDP_OK) { set_last_error(msg); return st; }
+  if (!d_state || !d_dt) { set_last_error("null device pointer"); return SIDP_ERR_ARG; }
+  if (cfg->law == SIDP_LAW_ADVECTION_VAR2D) { set_last_error("variable-velocity advection is not supported here"); return SIDP_ERR_ARG; }
+  if (cfg->unsparsified) {  // the dense operator's bound (every in-element pair) is smaller: not computed here
+    set_last_error("the unsparsified mode is not supported here");
+    return SIDP_ERR_ARG;
+  }
   for (int s = 0; s < 4; ++s)
-    if (cfg->bc[s] != SIDP_BC_PERIODIC && cfg->bc[s] != SIDP_BC_OUTFLOW) return SIDP_ERR_ARG;  // no ghost traces here
+    if (cfg->bc[s] != SIDP_BC_PERIODIC && cfg->bc[s] != SIDP_BC_OUTFLOW) {  // no ghost traces here
+      set_last_error("periodic and outflow sides only");
+      return SIDP_ERR_ARG;
+    }
   const double h = (cfg->x1 - cfg->x0) / cfg->nx;
-  if (!(h > 0) || std::fabs((cfg->y1 - cfg->y0) / cfg->ny - h) > 1e-12 * h) return SIDP_ERR_ARG;
   const long long N = (long long)cfg->nx * cfg->ny * (cfg->p + 1) * (cfg->p + 1);
-  if ((N + kStaticThreads - 1) / kStaticThreads > kMaxStaticBlocks) return SIDP_ERR_ARG;  // beyond the scratch
+  if ((N + kStaticThreads - 1) / kStaticThreads > kMaxStaticBlocks) {  // beyond the scratch
+    set_last_error("state larger than the fixed scratch allows (16,777,216 nodes)");
+    return SIDP_ERR_ARG;
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SIDP_ERR_CUDA;
   double* partials = nullptr;
