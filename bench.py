@@ -35,8 +35,8 @@ sys.path.insert(0, ROOT)
 METRIC = "node-updates/s per RK stage (Euler 2D p=3), mixed vs FP64; % HBM roofline"
 UNIT = "node-updates/s"
 # dram__bytes (read + write) per node and stage launch, averaged over the three stages, measured by
-# ncu on the 768x768 p=3 blast (profiles/k_stage_euler_mixed_p3.md).  The counters belong to the
-# stage kernel as committed with that profile; a changed kernel needs a new capture.
+# ncu on the 768x768 p=3 blast.  The counters belong to the stage kernel as it was captured; a
+# changed kernel needs a new capture.
 STAGE_DRAM_BYTES_PER_NODE = 39.4
 # Executed FP32 flops (2 x FFMA + FADD + FMUL) and warp instructions per node of stages 1, 2, 3
 # from the InstructionStats counters of the same capture: the two other ceilings of the stage
@@ -45,8 +45,7 @@ STAGE_FP32_FLOP_PER_NODE = (691.0, 449.0, 449.0)
 STAGE_WARP_INSTR_PER_NODE = (36.3, 28.4, 28.4)
 SMS, FP32_LANES_PER_SM, SCHEDULERS_PER_SM = 152, 128, 4
 # The curved-mesh stage kernel's DRAM traffic per node and launch (stages 1-3 averaged), from one
-# ncu capture of the 768x768 curved leg (profiles/k_stage_curved_euler_mixed_p3.md).  The kernel
-# has changed since (the smoothness-indicator block, off in this workload), so the figure is not
+# ncu capture of the 768x768 curved leg.  The kernel has changed since (the smoothness-indicator block, off in this workload), so the figure is not
 # reported as the launch's traffic until it is captured again.
 CURVED_DRAM_BYTES_PER_NODE = 93.4
 CURVED_TRAFFIC_CURRENT = False
@@ -532,7 +531,7 @@ def main():
     s = 4
     bytes_stage = [2 * 4 * s * nodes, 3 * 4 * s * nodes, 3 * 4 * s * nodes]
     # DRAM traffic of the stage kernel per launch (average over stages 1-3), from one ncu capture
-    # of the 768x768 case (profiles/k_stage_euler_mixed_p3.md) scaled to this launch by nodes
+    # of the 768x768 case scaled to this launch by nodes
     traffic = STAGE_DRAM_BYTES_PER_NODE * nodes
     ach = sum(bytes_stage) / sum(kt) / 1e9
     # whole step on the per-node figure 3 * nc * s bytes per node per stage (dt pass included)

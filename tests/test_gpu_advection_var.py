@@ -104,8 +104,9 @@ def test_smoothness_indicator_stage_parity(p):
     cur = U0
     for k in (1, 2, 3):
         sv.set_state(cur.reshape(1, -1))
+        sv.set_debug(True)
         sv.stage(1, dt)
-        frac = fe_compare.scalar_fe_check(pb, cur, dt, sv.get_state(1), tol=TOL)
+        frac = fe_compare.scalar_fe_check(pb, cur, dt, sv.get_state(1), sv.bounds()["alpha"], tol=TOL)
         assert frac < 0.35
         cur = pb.stage(cur, U0, dt, k)
 

@@ -99,8 +99,11 @@ def test_three_stages_parity(lawname, kind, p, bc, lim):
         cur = U0
         for k in (1, 2, 3):
             sv.set_state(cur.reshape(nc, -1))
+            sv.set_debug(True)
             sv.stage(1, dt)  # the forward-Euler operator from the oracle's stage-k input
-            euler_fe_check(pb, cur, dt, sv.get_state(1))
+            # four-quadrant data: constant plateaus, where entropy roots and Zalesak ratios are
+            # rounding-decided (up to about half of the nodes of these small meshes)
+            euler_fe_check(pb, cur, dt, sv.get_state(1), sv.bounds()["alpha"], max_relaxed=0.55)
             cur = pb.stage(cur, U0, dt, k)
         return
     sv.set_state(U0.reshape(nc, -1))
@@ -221,8 +224,9 @@ def test_exact_state_boundaries_vortex():
         else:
             # isentropic data: sigma = K everywhere, so most entropy roots are ill-conditioned
             dt = pb.compute_dt(U)
+            sv.set_debug(True)
             sv.stage(1, dt)
-            euler_fe_check(pb, U, dt, sv.get_state(1))
+            euler_fe_check(pb, U, dt, sv.get_state(1), sv.bounds()["alpha"])
 
 
 def test_sampled_full_size_blast_fp64():

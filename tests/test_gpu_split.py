@@ -73,8 +73,9 @@ def test_limited_stage_parity(t0):
         pb.time = pb.t_eval = ts                # (the oracle's forward-Euler operator reads t_eval)
         sv.set_time(ts)
         sv.set_state(cur.reshape(4, -1))
+        sv.set_debug(True)
         sv.stage(1, dt)
-        euler_fe_check(pb, cur, dt, sv.get_state(1))
+        euler_fe_check(pb, cur, dt, sv.get_state(1), sv.bounds()["alpha"])
         pb.time = t0
         cur = pb.stage(cur, U0, dt, k)
 

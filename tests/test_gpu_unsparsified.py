@@ -58,9 +58,9 @@ def test_stage_parity(lawname, p, limiter):
         sv.stage(1, dt)
         got = sv.get_state(1)
         if limiter == "elementwise":
-            elementwise_fe_check(pb, cur, dt, got)
+            elementwise_fe_check(pb, cur, dt, got, sv.bounds()["alpha"])
         elif limiter == "subcell" and lawname == "euler":
-            euler_fe_check(pb, cur, dt, got)
+            euler_fe_check(pb, cur, dt, got, sv.bounds()["alpha"])
         else:
             exp, info = pb.fe_stage(cur, dt, full=True)
             assert np.all(rel(got, exp) <= 1e-12), rel(got, exp)

@@ -38,13 +38,14 @@ def test_wall_stage_parity(p, bc, limiter):
     dt = pb.compute_dt(U0)
     sv.set_state(U0.reshape(4, -1))
     assert abs(sv.compute_dt() - dt) <= 1e-13 * dt
+    sv.set_debug(True)
     cur = U0
     for k in (1, 2, 3):
         sv.set_state(cur.reshape(4, -1))
         sv.stage(1, dt)
         got = sv.get_state(1)
         if limiter == "subcell":
-            euler_fe_check(pb, cur, dt, got)
+            euler_fe_check(pb, cur, dt, got, sv.bounds()["alpha"])
         else:
             assert np.all(rel(got, pb.fe_stage(cur, dt)) <= 1e-12)
         cur = pb.stage(cur, U0, dt, k)

@@ -150,8 +150,10 @@ def test_elementwise_comparator_accepts_oracle_under_input_noise(lawname, p):
     for seed in range(6):
         rng = np.random.default_rng(seed)
         noisy = U * (1 + 2.2e-16 * rng.standard_normal(U.shape))
-        fe_compare.elementwise_fe_check(pb, U, dt, pb.fe_stage(noisy, dt))
-    bad = pb.fe_stage(U, dt).copy()
+        got, info = pb.fe_stage(noisy, dt, full=True)
+        fe_compare.elementwise_fe_check(pb, U, dt, got, info["alpha_tilde"])
+    exp, info = pb.fe_stage(U, dt, full=True)
+    bad = exp.copy()
     bad[0, 5, 3] += 1e-9 * np.max(np.abs(bad[0]))
     with pytest.raises(AssertionError):
-        fe_compare.elementwise_fe_check(pb, U, dt, bad)
+        fe_compare.elementwise_fe_check(pb, U, dt, bad, info["alpha_tilde"])

@@ -102,8 +102,9 @@ def test_wall_limited_stage_equals_mirrored_problem(p, side):
     dt = full.compute_dt(_mirror(Uw, p, side))
     U0 = Uw
     for k in (1, 2, 3):
-        fe_full = full.fe_stage(_mirror(Uw, p, side), dt)
-        euler_fe_check(wall, Uw, dt, _restrict(fe_full, p, side))
+        fe_full, info = full.fe_stage(_mirror(Uw, p, side), dt, full=True)
+        alpha = _restrict(info["alpha_tilde"][None], p, side)[0]
+        euler_fe_check(wall, Uw, dt, _restrict(fe_full, p, side), alpha)
         Uw = wall.stage(Uw, U0, dt, k)
 
 
@@ -129,7 +130,7 @@ def test_euler_comparator_accepts_oracle_under_input_noise(p, bc):
     for seed in range(6):
         rng = np.random.default_rng(seed)
         noisy = U * (1 + 2.2e-16 * rng.standard_normal(U.shape))
-        got = pb.fe_stage(noisy, dt)
+        got, info = pb.fe_stage(noisy, dt, full=True)
         worst = max(worst, float(np.max(np.abs(got - base) / np.max(np.abs(base), axis=(1, 2))[:, None, None])))
-        euler_fe_check(pb, U, dt, got)
+        euler_fe_check(pb, U, dt, got, info["alpha_tilde"])
     assert worst > 1e-12   # the sensitivity is real
