@@ -59,7 +59,11 @@ class CurvedProblem(Problem):
         self.X = np.asarray(X, dtype=float).reshape(Ne, NN).copy()
         self.Y = np.asarray(Y, dtype=float).reshape(Ne, NN).copy()
         A = _gll.lagrange_derivatives(self.xi)  # A[i, j] = phi_j'(xi_i)
-        Xe, Ye = self.X.reshape(Ne, n, n), self.Y.reshape(Ne, n, n)  # [e, a (eta), b (xi)]
+        # [e, a (eta), b (xi)], relative to each element's first node: the derivative of a constant
+        # vanishes (P1), so this is the same map, and the derivatives keep their relative precision
+        # on fine meshes instead of losing |x|/h of it to the absolute coordinates
+        Xe = (self.X - self.X[:, :1]).reshape(Ne, n, n)
+        Ye = (self.Y - self.Y[:, :1]).reshape(Ne, n, n)
         x_xi = np.einsum("bc,eac->eab", A, Xe)
         y_xi = np.einsum("bc,eac->eab", A, Ye)
         x_eta = np.einsum("ac,ecb->eab", A, Xe)

@@ -118,17 +118,22 @@ sidp_status curved_metrics(int p, int nx, int ny, const int* bc, const double* x
   double* NXx = out + 9 * N; double* NXy = out + 10 * N;
   double* NYx = out + 11 * N; double* NYy = out + 12 * N;
   // metric terms and masses
+  // coordinates relative to the element's first node: the same map (derivatives of constants
+  // vanish), differentiated without the cancellation of absolute coordinates (relative precision of
+  // the derivatives independent of the element size)
+  std::vector<double> xr(NN), yr(NN);
   for (long long e = 0; e < Ne; ++e) {
     const double* xe = x + e * NN;
     const double* ye = y + e * NN;
+    for (int i = 0; i < NN; ++i) { xr[i] = xe[i] - xe[0]; yr[i] = ye[i] - ye[0]; }
     for (int a = 0; a < n; ++a)
       for (int b = 0; b < n; ++b) {
         double x_xi = 0, y_xi = 0, x_eta = 0, y_eta = 0;
         for (int c = 0; c < n; ++c) {
-          x_xi += Ad[b * n + c] * xe[a * n + c];
-          y_xi += Ad[b * n + c] * ye[a * n + c];
-          x_eta += Ad[a * n + c] * xe[c * n + b];
-          y_eta += Ad[a * n + c] * ye[c * n + b];
+          x_xi += Ad[b * n + c] * xr[a * n + c];
+          y_xi += Ad[b * n + c] * yr[a * n + c];
+          x_eta += Ad[a * n + c] * xr[c * n + b];
+          y_eta += Ad[a * n + c] * yr[c * n + b];
         }
         const long long g = e * NN + a * n + b;
         const double G = x_xi * y_eta - x_eta * y_xi;

@@ -88,3 +88,19 @@ def test_library_arrays_satisfy_the_identities(p):
         lhs = Q[j] @ DhX + Q[2 + j] @ DhY
         assert np.abs(lhs - bnd.reshape(Ne, -1)).max() < 1e-13 * scale
     assert np.sum(g[8]) == pytest.approx(0.75, rel=1e-12)
+
+
+def test_metric_arrays_agree_on_a_fine_mesh():
+    """On a 256x256 warped mesh (h = 1/256) the two sides still agree to a few ulp of each array:
+    both differentiate the coordinates relative to the element's first node (the same map, since
+    the derivative of a constant vanishes), so no precision is lost to the absolute coordinates as
+    the elements shrink."""
+    p, nel = 3, 256
+    X, Y = scheme.Problem(laws.Euler(1.4), p, nel, nel).node_coords()
+    Xw, Yw = inputs.warped_coords(X, Y, 0.05)
+    cw = CurvedProblem(laws.Euler(1.4), p, nel, nel, Xw, Yw, bc=("periodic",) * 4)
+    got = sidp.sidp_curved_metrics(p, nel, nel, ("periodic",) * 4, Xw, Yw)
+    ref = _oracle_tables(cw)
+    for k in range(sidp.GEO_FIELDS):
+        scale = np.abs(ref[k]).max()
+        assert np.abs(got[k] - ref[k]).max() <= 2e-14 * scale, k
