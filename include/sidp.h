@@ -214,11 +214,15 @@ sidp_status sidp_compute_dt(sidp_ctx* ctx, double* dt);
  * d_state: device pointer to the [nc][N] state in the storage type of cfg->precision (float64 or
  * float32), library node order; d_dt: device pointer to one double that receives
  * cfl * min_i m_i / (2 sum_{j != i} d-hat_ij) (0 when no wave moves).  Asynchronous on
- * cuda_stream.  Periodic and outflow sides only; Burgers, Euler and constant-velocity advection
- * only (the variable-velocity law is SIDP_ERR_ARG here).  Scratch lives in a fixed 512 KiB device array
- * shared by all calls: at most 65536 * 256 = 16,777,216 nodes (else SIDP_ERR_ARG), and calls that
- * overlap on the GPU race.  The first call on a device looks the array up (cudaGetSymbolAddress);
- * make it before any stream capture. */
+ * cuda_stream.  cfg passes the checks of sidp_create (else SIDP_ERR_ARG, before any device
+ * access); in addition only periodic and outflow sides, only Burgers, Euler and constant-velocity
+ * advection (the variable-velocity law is SIDP_ERR_ARG here) and only the sparsified operator
+ * (cfg->unsparsified != 0 is SIDP_ERR_ARG: its smaller time step is not computed here).  Scratch
+ * lives in a fixed 512 KiB device array shared by all calls: at most 65536 * 256 = 16,777,216
+ * nodes (else SIDP_ERR_ARG), and calls that overlap on the GPU race.  The first call on a device
+ * looks the array up (cudaGetSymbolAddress) and caches its address: make it before any stream
+ * capture; a device reset (cudaDeviceReset) after it is not supported.  Errors set
+ * sidp_last_error(NULL). */
 sidp_status sidp_compute_dt_static(const sidp_config* cfg, const void* d_state, double* d_dt, void* cuda_stream);
 
 /* One SSP-RK3 stage with a given dt (k = 1, 2, 3; Sec. 5):
@@ -276,10 +280,24 @@ sidp_status sidp_batch_total_nodes(const sidp_batch* b, long long* n_nodes);
 sidp_status sidp_batch_node_coords(const sidp_batch* b, int i, double* x, double* y);
 sidp_status sidp_batch_set_state(sidp_batch* b, int i, const double* u);
 sidp_status sidp_batch_get_state(sidp_batch* b, int i, double* u);
+/* Instance i's buffer `which` (0: u^n, 1: u^(1), 2: u^(2)) as float64 [nc][N_i] (caller-owned
+ * host array); synchronises.  sidp_batch_get_state is which = 0. */
+sidp_status sidp_batch_get_buffer(sidp_batch* b, int i, int which, double* u);
+/* SSP-RK3 stage k (1, 2 or 3; Sec. 5) of every instance with the time steps dt[0..count-1]
+ * (caller-owned host array, copied; finite and >= 0, else SIDP_ERR_ARG): stage 1 writes
+ * u^(1) = FE(u^n), stage 2 u^(2) = 3/4 u^n + 1/4 FE(u^(1)), stage 3 u^(n+1) = 1/3 u^n +
+ * 2/3 FE(u^(2)) over u^n.  Eager launches of the same kernels the step graph replays; the clocks
+ * do not advance.  Synchronises.  For tests and for callers that drive the stages themselves. */
+sidp_status sidp_batch_stage(sidp_batch* b, int k, const double* dt);
 sidp_status sidp_batch_step(sidp_batch* b, int nsteps);
 sidp_status sidp_batch_get_diag(sidp_batch* b, int i, sidp_diag* out);
 sidp_status sidp_batch_set_stats(sidp_batch* b, int on);   /* statistics as sidp_set_stats (default on) */
 sidp_status sidp_batch_synchronize(sidp_batch* b);
+/* Debug capture for every instance, as sidp_set_debug (4 float64 per node of the batch on the
+ * device); sidp_batch_get_bounds copies instance i's last-stage local bounds, K and alpha-tilde
+ * into caller-owned arrays of N_i doubles (any may be NULL; SIDP_ERR_STATE before capture). */
+sidp_status sidp_batch_set_debug(sidp_batch* b, int on);
+sidp_status sidp_batch_get_bounds(sidp_batch* b, int i, double* lo, double* hi, double* K, double* alpha);
 const char* sidp_batch_last_error(const sidp_batch* b);
 
 #ifdef __cplusplus

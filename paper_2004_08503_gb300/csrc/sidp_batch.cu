@@ -68,6 +68,9 @@ struct sidp_batch {
   double* d_cfl = nullptr;
   unsigned long long* d_bits = nullptr;
   StageStats* d_stats = nullptr;
+  double* d_dbg = nullptr;  // debug capture: lo, hi, K, alpha-tilde, each [total nodes] (or null)
+  bool debug = false;
+  long long total_nodes = 0;
   std::vector<Group> groups;
   std::vector<cudaStream_t> gstream;  // one stream per degree group (the groups are independent)
   std::vector<cudaEvent_t> gdone;     // a group's work on its stream is done
@@ -117,6 +120,13 @@ cudaError_t build_tables(sidp_batch* b) {
     I.dtT = dtT + i;
     I.stats = b->stats_on ? b->d_stats + i : nullptr;
     const long long o = b->off[i];
+    if (b->debug && b->d_dbg) {  // per-node captures at the instance's node offset
+      const long long no = o / b->nc;
+      I.dbg_lo = b->d_dbg + no;
+      I.dbg_hi = b->d_dbg + b->total_nodes + no;
+      I.dbg_K = b->d_dbg + 2 * b->total_nodes + no;
+      I.dbg_alpha = b->d_dbg + 3 * b->total_nodes + no;
+    }
     // dt launch reads u^n
     Instance<T> d = I;
     d.uin = u[0] + o;
@@ -278,6 +288,7 @@ sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int cou
     for (long long t = 0; t < ntiles; ++t) tasks[{c.p, tile}].push_back(make_int2(i, (int)t));
   }
   b->total_vals = tot;
+  b->total_nodes = tot / b->nc;
   cudaError_t e;
   if (cuda_stream) {
     b->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -345,6 +356,7 @@ sidp_status sidp_batch_destroy(sidp_batch* b) {
   cudaFree(b->d_cfl);
   cudaFree(b->d_bits);
   cudaFree(b->d_stats);
+  cudaFree(b->d_dbg);
   for (cudaStream_t st : b->gstream) cudaStreamDestroy(st);
   for (cudaEvent_t ev : b->gdone) cudaEventDestroy(ev);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -423,10 +435,10 @@ sidp_status sidp_batch_set_state(sidp_batch* b, int i, const double* u) try {
   return bfail(b, SIDP_ERR_ARG, "unexpected host exception");
 }
 
-sidp_status sidp_batch_get_state(sidp_batch* b, int i, double* u) try {
-  if (!b || i < 0 || i >= b->n || !u) return bfail(b, SIDP_ERR_ARG, "bad argument");
+sidp_status sidp_batch_get_buffer(sidp_batch* b, int i, int which, double* u) try {
+  if (!b || i < 0 || i >= b->n || !u || which < 0 || which > 2) return bfail(b, SIDP_ERR_ARG, "bad argument");
   const long long cnt = b->nc * b->N[i];
-  const char* src = static_cast<const char*>(b->d_u[0]) + b->off[i] * b->esize;
+  const char* src = static_cast<const char*>(b->d_u[which]) + b->off[i] * b->esize;
   if (b->mixed) {
     std::vector<float> tmp(cnt);
     BCUDA(b, cudaMemcpyAsync(tmp.data(), src, cnt * sizeof(float), cudaMemcpyDeviceToHost, b->stream));
@@ -441,6 +453,52 @@ sidp_status sidp_batch_get_state(sidp_batch* b, int i, double* u) try {
   return bfail(b, SIDP_ERR_OOM, "host allocation failed");
 } catch (...) {
   return bfail(b, SIDP_ERR_ARG, "unexpected host exception");
+}
+
+sidp_status sidp_batch_get_state(sidp_batch* b, int i, double* u) { return sidp_batch_get_buffer(b, i, 0, u); }
+
+sidp_status sidp_batch_stage(sidp_batch* b, int k, const double* dt) try {
+  if (!b || k < 1 || k > 3 || !dt) return bfail(b, SIDP_ERR_ARG, "bad argument");
+  for (int i = 0; i < b->n; ++i)
+    if (!(dt[i] >= 0.0) || !std::isfinite(dt[i])) return bfail(b, SIDP_ERR_ARG, "time steps must be finite and >= 0");
+  std::vector<float> dtf(dt, dt + b->n);
+  BCUDA(b, cudaStreamSynchronize(b->stream));
+  BCUDA(b, cudaMemcpy(b->d_dt, dt, b->n * sizeof(double), cudaMemcpyHostToDevice));
+  BCUDA(b, cudaMemcpy(b->d_dtf, dtf.data(), b->n * sizeof(float), cudaMemcpyHostToDevice));
+  BCUDA(b, run_groups(b, k, k));
+  BCUDA(b, cudaStreamSynchronize(b->stream));
+  return SIDP_OK;
+} catch (const std::bad_alloc&) {
+  return bfail(b, SIDP_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return bfail(b, SIDP_ERR_ARG, "unexpected host exception");
+}
+
+sidp_status sidp_batch_set_debug(sidp_batch* b, int on) {
+  if (!b) return bfail(nullptr, SIDP_ERR_ARG, "null batch");
+  if (on && !b->d_dbg) {
+    if (cudaMalloc(&b->d_dbg, 4 * b->total_nodes * sizeof(double)) != cudaSuccess)
+      return bfail(b, SIDP_ERR_OOM, "debug allocation failed");
+    BCUDA(b, cudaMemset(b->d_dbg, 0, 4 * b->total_nodes * sizeof(double)));
+  }
+  if ((on != 0) == b->debug) return SIDP_OK;
+  BCUDA(b, cudaStreamSynchronize(b->stream));
+  b->debug = on != 0;
+  if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+  BCUDA(b, b->mixed ? build_tables<float>(b) : build_tables<double>(b));
+  return SIDP_OK;
+}
+
+sidp_status sidp_batch_get_bounds(sidp_batch* b, int i, double* lo, double* hi, double* K, double* alpha) {
+  if (!b || i < 0 || i >= b->n) return bfail(b, SIDP_ERR_ARG, "bad argument");
+  if (!b->d_dbg) return bfail(b, SIDP_ERR_STATE, "debug capture was never enabled");
+  BCUDA(b, cudaStreamSynchronize(b->stream));
+  double* dst[4] = {lo, hi, K, alpha};
+  const long long no = b->off[i] / b->nc;
+  for (int q = 0; q < 4; ++q)
+    if (dst[q])
+      BCUDA(b, cudaMemcpy(dst[q], b->d_dbg + q * b->total_nodes + no, b->N[i] * sizeof(double), cudaMemcpyDeviceToHost));
+  return SIDP_OK;
 }
 
 sidp_status sidp_batch_step(sidp_batch* b, int nsteps) {

@@ -87,6 +87,10 @@ _SIGS = {
     "sidp_batch_node_coords": (ctypes.c_int, [_P, ctypes.c_int, _D, _D]),
     "sidp_batch_set_state": (ctypes.c_int, [_P, ctypes.c_int, _D]),
     "sidp_batch_get_state": (ctypes.c_int, [_P, ctypes.c_int, _D]),
+    "sidp_batch_get_buffer": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _D]),
+    "sidp_batch_stage": (ctypes.c_int, [_P, ctypes.c_int, _D]),
+    "sidp_batch_set_debug": (ctypes.c_int, [_P, ctypes.c_int]),
+    "sidp_batch_get_bounds": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D, _D]),
     "sidp_batch_step": (ctypes.c_int, [_P, ctypes.c_int]),
     "sidp_batch_get_diag": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(sidp_diag)]),
     "sidp_batch_synchronize": (ctypes.c_int, [_P]),
@@ -358,6 +362,29 @@ def sidp_batch_get_state(b, i):
     u = np.empty((nc, n))
     _bcheck(load().sidp_batch_get_state(b, i, _ptr(u)), b)
     return u
+
+
+def sidp_batch_get_buffer(b, i, which):
+    n, nc = sidp_batch_sizes(b, i)
+    u = np.empty((nc, n))
+    _bcheck(load().sidp_batch_get_buffer(b, i, which, _ptr(u)), b)
+    return u
+
+
+def sidp_batch_stage(b, k, dt):
+    dt = np.ascontiguousarray(dt, dtype=np.float64)
+    _bcheck(load().sidp_batch_stage(b, k, _ptr(dt)), b)
+
+
+def sidp_batch_set_debug(b, on):
+    _bcheck(load().sidp_batch_set_debug(b, int(on)), b)
+
+
+def sidp_batch_get_bounds(b, i):
+    n, _ = sidp_batch_sizes(b, i)
+    out = [np.empty(n) for _ in range(4)]
+    _bcheck(load().sidp_batch_get_bounds(b, i, *[_ptr(o) for o in out]), b)
+    return dict(zip(("lo", "hi", "K", "alpha"), out))
 
 
 def sidp_batch_step(b, nsteps=1):

@@ -1,9 +1,15 @@
 """Batched execution (many independent instances, task table per degree, one CUDA graph per
-step): every instance must equal the same instance advanced alone (bit for bit: the batched
-launch runs the same tile code on the same inputs)."""
+step): every instance of a mixed-degree batch against the FP64 oracle, stage by stage (the
+strict 1e-12 bar for the unlimited and low-order updates, the conditioning-aware comparators
+with the batch's captured alpha-tilde for subcell limiting), including a sample of the
+512-instance benchmark mix; and every instance equal to the same instance advanced alone (bit
+for bit: the batched launch runs the same tile code on the same inputs)."""
 import numpy as np
 import pytest
 
+import test_oracle_wall as tw
+from fe_compare import euler_fe_check, scalar_fe_check
+from oracle import laws, scheme
 from paper_2004_08503_gb300 import build, inputs, sidp
 
 pytestmark = pytest.mark.gpu
@@ -92,3 +98,124 @@ def test_batch_rejects_mixed_laws():
     c = sidp.make_config(law="burgers", p=3, nx=2, ny=2)
     with pytest.raises(sidp.SidpError):
         sidp.sidp_batch_create([a, c])
+
+
+# p = 1..7, ragged meshes (partial element tiles), periodic and outflow sides, two instances of
+# p = 3 so that one degree group holds several instances
+ORACLE_SHAPES = [(5, 3, 1, "periodic"), (4, 4, 2, "outflow"), (3, 5, 3, "periodic"), (6, 2, 3, "outflow"),
+                 (3, 3, 4, "outflow"), (2, 3, 5, "periodic"), (3, 2, 6, "outflow"), (2, 2, 7, "periodic")]
+
+
+def _oracle_batch(lawname, limiter):
+    law = laws.Euler(1.4) if lawname == "euler" else laws.Burgers()
+    pbs, cfgs, U0 = [], [], []
+    for i, (nx, ny, p, bc) in enumerate(ORACLE_SHAPES):
+        dom = (0.0, nx / max(nx, ny), 0.0, ny / max(nx, ny))
+        pb = scheme.Problem(law, p, nx, ny, domain=dom, bc=(bc,) * 4, limiter=limiter)
+        pbs.append(pb)
+        cfgs.append(dict(law=lawname, p=p, nx=nx, ny=ny, precision="fp64", domain=dom, bc=(bc,) * 4,
+                         limiter=limiter))
+        X, Y = pb.node_coords()
+        if lawname == "euler":  # a density bump, a contact and a shear layer with a pressure jump
+            U = law.prim_to_cons(*tw._data(X, Y))
+        else:
+            U = inputs.burgers_pulse(X, Y)
+        U0.append(U)
+    b = sidp.sidp_batch_create([sidp.make_config(**c) for c in cfgs])
+    sidp.sidp_batch_set_stats(b, False)  # the timed kernels
+    return pbs, b, U0
+
+
+@pytest.mark.parametrize("limiter", ["none", "lo"])
+def test_batch_stages_match_oracle_strict(limiter):
+    """Stages 1, 2, 3 of every instance of a mixed-degree Euler batch (FP64) against the oracle's
+    SSP-RK3 stages, 1e-12 normwise per field."""
+    pbs, b, U0 = _oracle_batch("euler", limiter)
+    for i, U in enumerate(U0):
+        sidp.sidp_batch_set_state(b, i, U.reshape(4, -1))
+    dts = np.array([pb.compute_dt(U) for pb, U in zip(pbs, U0)])
+    cur = list(U0)
+    for k in (1, 2, 3):
+        sidp.sidp_batch_stage(b, k, dts)
+        for i, pb in enumerate(pbs):
+            exp = pb.stage(cur[i], U0[i], dts[i], k)
+            got = sidp.sidp_batch_get_buffer(b, i, (1, 2, 0)[k - 1])
+            err = np.max(np.abs(got - exp.reshape(4, -1)), axis=1) / np.max(np.abs(exp), axis=(1, 2))
+            assert np.all(err <= 1e-12), (i, k, err)
+            cur[i] = exp
+    sidp.sidp_batch_destroy(b)
+
+
+@pytest.mark.parametrize("lawname", ["euler", "burgers"])
+def test_batch_limited_stages_match_oracle(lawname):
+    """The subcell-limited forward-Euler operator of every instance, from the oracle's SSP-RK3
+    stage-k input, against the oracle with the conditioning-aware comparators (the alpha-tilde
+    of each instance from the batch's debug capture)."""
+    pbs, b, U0 = _oracle_batch(lawname, "subcell")
+    nc = U0[0].shape[0]
+    sidp.sidp_batch_set_debug(b, True)
+    dts = np.array([pb.compute_dt(U) for pb, U in zip(pbs, U0)])
+    cur = list(U0)
+    for k in (1, 2, 3):
+        for i, U in enumerate(cur):
+            sidp.sidp_batch_set_state(b, i, U.reshape(nc, -1))
+        sidp.sidp_batch_stage(b, 1, dts)
+        for i, pb in enumerate(pbs):
+            got = sidp.sidp_batch_get_buffer(b, i, 1)
+            alpha = sidp.sidp_batch_get_bounds(b, i)["alpha"]
+            if lawname == "euler":
+                euler_fe_check(pb, cur[i], dts[i], got, alpha)
+            else:
+                scalar_fe_check(pb, cur[i], dts[i], got, alpha)
+        cur = [pb.stage(cur[i], U0[i], dts[i], k) for i, pb in enumerate(pbs)]
+    # the RK combinations of stages 2 and 3 through the batch, from the same inputs
+    for i, U in enumerate(U0):
+        sidp.sidp_batch_set_state(b, i, U.reshape(nc, -1))
+    sidp.sidp_batch_stage(b, 1, dts)
+    sidp.sidp_batch_stage(b, 2, dts)
+    for i, pb in enumerate(pbs):
+        u1 = sidp.sidp_batch_get_buffer(b, i, 1).reshape(U0[i].shape)
+        exp = 0.75 * U0[i] + 0.25 * pb.fe_stage(u1, dts[i])
+        got = sidp.sidp_batch_get_buffer(b, i, 2).reshape(U0[i].shape)
+        fe_part = (got - 0.75 * U0[i]) / 0.25
+        alpha = sidp.sidp_batch_get_bounds(b, i)["alpha"]
+        check = euler_fe_check if lawname == "euler" else scalar_fe_check
+        check(pb, u1, dts[i], fe_part, alpha, tol=1e-11)
+        assert np.max(np.abs(got - exp)) <= 1e-3 * np.max(np.abs(exp))
+    sidp.sidp_batch_destroy(b)
+
+
+def test_benchmark_batch_mix_sampled_against_oracle():
+    """The 512-instance benchmark mix (elements per side in {8,16,32,64}, p in 2..7, seeded
+    four-quadrant data) in FP64: one limited stage of the whole batch on the GPU; for two
+    instances of every degree, the oracle recomputes a sample of elements (random, corners)."""
+    shapes = inputs.batch_shapes(0, 512)
+    cfgs = [sidp.make_config(law="euler", p=p, nx=nel, ny=nel, precision="fp64", bc=("outflow",) * 4)
+            for nel, p in shapes]
+    b = sidp.sidp_batch_create(cfgs)
+    sidp.sidp_batch_set_stats(b, False)
+    sidp.sidp_batch_set_debug(b, True)
+    states = []
+    for i in range(len(shapes)):
+        x, y = sidp.sidp_batch_node_coords(b, i)
+        states.append(inputs.four_quadrant(x, y, 100003 * 0 + i))
+        sidp.sidp_batch_set_state(b, i, states[i])
+    law = laws.Euler(1.4)
+    picks = []
+    for p in range(2, 8):
+        picks += [i for i, (nel, q) in enumerate(shapes) if q == p][:2]
+    pbs = {i: scheme.Problem(law, shapes[i][1], shapes[i][0], shapes[i][0], bc=("outflow",) * 4) for i in picks}
+    # the sampled instances take their CFL time step; the others a step far below theirs
+    dts = np.array([pbs[i].compute_dt(states[i].reshape(4, shapes[i][0] ** 2, -1)) if i in pbs else 1e-6
+                    for i in range(len(shapes))])
+    sidp.sidp_batch_stage(b, 1, dts)
+    rng = np.random.default_rng(3)
+    for i in picks:
+        pb = pbs[i]
+        nel = shapes[i][0]
+        U = states[i].reshape(4, pb.Ne, -1)
+        sample = np.unique(np.concatenate([rng.integers(0, pb.Ne, 12), [0, nel - 1, pb.Ne - nel, pb.Ne - 1]]))
+        got = sidp.sidp_batch_get_buffer(b, i, 1).reshape(4, pb.Ne, -1)[:, sample]
+        alpha = sidp.sidp_batch_get_bounds(b, i)["alpha"].reshape(pb.Ne, -1)[sample]
+        euler_fe_check(pb, U, dts[i], got, alpha, elems=sample)
+    sidp.sidp_batch_destroy(b)
