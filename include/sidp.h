@@ -113,6 +113,11 @@ typedef struct {
   int rootfind_max_iters;       /* largest iteration count of the entropy line search           */
   long long rootfind_cap_hits;  /* line searches stopped by the iteration cap                   */
   long long nonfinite;          /* number of non-finite values in the current state              */
+  long long bound_nudges;       /* SIDP_MIXED, statistics on: stage results of the limited field
+                                   that float32 rounding left outside their local bounds (by at
+                                   most 8 ulp of the update's operands) and that were set onto the
+                                   bound before the store (the post-round acceptance); counted
+                                   over stages and nodes since the last set_state              */
 } sidp_diag;
 
 typedef struct sidp_ctx sidp_ctx;

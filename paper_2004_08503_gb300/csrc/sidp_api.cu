@@ -842,6 +842,7 @@ sidp_status sidp_get_diag(sidp_ctx* c, sidp_diag* out) {
   out->max_entropy_violation = ev;
   out->rootfind_max_iters = (int)ss.rootfind_max_iters;
   out->rootfind_cap_hits = (long long)ss.rootfind_cap_hits;
+  out->bound_nudges = (long long)ss.bound_nudges;
   if (out->nonfinite) return fail(c, SIDP_ERR_NONFINITE, "state holds non-finite values");
   return SIDP_OK;
 }

@@ -569,6 +569,7 @@ sidp_status sidp_batch_get_diag(sidp_batch* b, int i, sidp_diag* out) try {
   std::memcpy(&out->max_entropy_violation, &ss.max_entropy_violation, sizeof(double));
   out->rootfind_max_iters = (int)ss.rootfind_max_iters;
   out->rootfind_cap_hits = (long long)ss.rootfind_cap_hits;
+  out->bound_nudges = (long long)ss.bound_nudges;
   if (out->nonfinite) return bfail(b, SIDP_ERR_NONFINITE, "state holds non-finite values");
   return SIDP_OK;
 } catch (const std::bad_alloc&) {

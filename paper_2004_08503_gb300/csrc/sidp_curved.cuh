@@ -112,6 +112,7 @@ struct CurvedFace {
   T Fh[LAW::NC];   // flux in +xi (+eta)
   T Fn[LAW::NC];   // own F . n
   T bar, sig, ln;
+  T um;            // |u| of the neighbour's trace, limited field (operand scale of the face)
 };
 
 template <int P, class LAW, typename T>
@@ -135,6 +136,18 @@ __device__ __forceinline__ void curved_element_face(const Instance<T>& I, const 
   for (int q = 0; q < NC; ++q) F.Fn[q] = fx[q] * nvx + fy[q] * nvy;
   if constexpr (LAW::kEntropy) F.sig = LAW::sigma(un, an, lp);
   else F.sig = T(0);
+  F.um = fabs(un[0]);
+}
+
+// Operand scale of the low-order state of node (a, b) in slot t (the limited field): |u_i| +
+// 2 max |u_j| over its four neighbours (within the element from shared memory; across an element
+// face the neighbour's trace, um), as in the Cartesian kernel's stencil_scale.
+template <int P, class S, typename T>
+__device__ __forceinline__ T curved_stencil_scale(const S& s, int t, int a, int b, T u0, T umx, T umy) {
+  constexpr int n = P + 1;
+  const T sl = (b > 0) ? fabs(s.u[t - 1].v[0]) : umx, sr = (b < P) ? fabs(s.u[t + 1].v[0]) : umx;
+  const T sd = (a > 0) ? fabs(s.u[t - n].v[0]) : umy, su = (a < P) ? fabs(s.u[t + n].v[0]) : umy;
+  return fabs(u0) + T(2) * tmax(tmax(sl, sr), tmax(sd, su));
 }
 
 // Internal subcell face between slots L and R (dir 0: x, row 1; dir 1: y, row 2).
@@ -367,11 +380,16 @@ __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::va
     __syncthreads();
     if (act) {
       const T ak = s.aK[le];
+      T fe[NC];
 #pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        const T fe = uL[q] + ak * dtm * rn[q];
-        I.uout[q * N + g] = (I.c0 == T(0)) ? fe : I.c0 * I.u0[q * N + g] + I.c1 * fe;
+      for (int q = 0; q < NC; ++q) fe[q] = uL[q] + ak * dtm * rn[q];
+      if constexpr (sizeof(T) == 4) {
+        if (!(fe[0] >= lo && fe[0] <= hi))  // rare: the rounding scale only where it is needed
+          accept_rounded(fe[0], lo, hi, curved_stencil_scale<P>(s, t, a, b, u[0], FX.um, FY.um) + fabs(uL[0]) +
+                                            fabs(ak * dtm * rn[0]) + tmax(fabs(lo), fabs(hi)));
       }
+#pragma unroll
+      for (int q = 0; q < NC; ++q) I.uout[q * N + g] = (I.c0 == T(0)) ? fe[q] : I.c0 * I.u0[q * N + g] + I.c1 * fe[q];
     }
     return;
   }
@@ -440,11 +458,17 @@ __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::va
     const T axm = (b > 0) ? tmin(at, s.alpha[t - 1]) : T(0);
     const T ayp = (a < P) ? tmin(at, s.alpha[t + n]) : T(0);
     const T aym = (a > 0) ? tmin(at, s.alpha[t - n]) : T(0);
+    T fe[NC];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) {
-      const T fe = uL[q] + dtm * (axp * xp[q] - axm * xm[q] + ayp * yp[q] - aym * ym[q]);
-      I.uout[q * N + g] = (I.c0 == T(0)) ? fe : I.c0 * u0[q] + I.c1 * fe;
+    for (int q = 0; q < NC; ++q) fe[q] = uL[q] + dtm * (axp * xp[q] - axm * xm[q] + ayp * yp[q] - aym * ym[q]);
+    if constexpr (sizeof(T) == 4) {
+      if (!(fe[0] >= lo && fe[0] <= hi))  // rare: the rounding scale only where it is needed
+        accept_rounded(fe[0], lo, hi, curved_stencil_scale<P>(s, t, a, b, u[0], FX.um, FY.um) + fabs(uL[0]) +
+                                          tmax(fabs(lo), fabs(hi)) +
+                                          dtm * (fabs(axp * xp[0]) + fabs(axm * xm[0]) + fabs(ayp * yp[0]) + fabs(aym * ym[0])));
     }
+#pragma unroll
+    for (int q = 0; q < NC; ++q) I.uout[q * N + g] = (I.c0 == T(0)) ? fe[q] : I.c0 * u0[q] + I.c1 * fe[q];
   }
 }
 

@@ -94,6 +94,7 @@ struct StageStats {
   unsigned int pad;
   unsigned long long rootfind_cap_hits;
   double field_scale;  // max |u| of the limited field at the last host set_state (violation floor)
+  unsigned long long bound_nudges;  // float32 results set onto their bound by the post-round acceptance
 };
 
 // Moving two-state ghost of one side (the boundaries of the double Mach reflection, Sec. 5.7): the

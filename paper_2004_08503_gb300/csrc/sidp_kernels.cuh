@@ -38,7 +38,9 @@ template <typename T> struct Prec;
 template <> struct Prec<double> { static constexpr double root_tol = 1e-13; static constexpr double entropy_margin = 0.0; };
 template <> struct Prec<float> { static constexpr float root_tol = 2e-6f; static constexpr float entropy_margin = 1e-6f; };
 
-template <typename T, int NC> struct alignas(NC == 4 ? 4 * sizeof(T) : sizeof(T)) Vec { T v[NC]; };
+template <typename T, int NC> struct alignas(NC == 4 ? 4 * sizeof(T) : NC == 2 ? 2 * sizeof(T) : sizeof(T)) Vec { T v[NC]; };
+
+
 
 template <int P, int TX, int TY>
 struct TileGeom {
@@ -373,6 +375,26 @@ __device__ T entropy_limit(const T* uL, T K, const T* xp, const T* xm, const T* 
   return t;
 }
 
+// Post-round acceptance of the float32 store.  The limited field's forward-Euler result lies in
+// its local bounds [lo, hi] in exact arithmetic (Sec. 4.1.3; Sec. 4.3 for the density); the
+// float32 evaluation of the update can leave it outside by the rounding of its operands, of
+// magnitude `mag` (the low-order state, the limited antidiffusive terms and the bounds).  A result
+// outside by no more than 8 float32 ulp of `mag` is set onto the violated bound, so that the
+// stored state satisfies the bounds exactly; the change is of the order of the update's own
+// rounding, like the rounding of the store itself.  Returns 1 when the value moved.  The float64
+// path keeps its result (no acceptance step: it is held to the float64 oracle).
+template <typename T>
+__device__ __forceinline__ int accept_rounded(T& v, T lo, T hi, T mag) {
+  if constexpr (sizeof(T) == 8) {
+    return 0;
+  } else {
+    const T tol = T(8) * FLT_EPSILON * mag;
+    const bool below = (v < lo) && (v >= lo - tol), above = (v > hi) && (v <= hi + tol);
+    v = below ? lo : (above ? hi : v);
+    return (below || above) ? 1 : 0;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void warp_max_atomic(T v, unsigned long long* dst) {
   double d = (double)v;  // v >= 0
@@ -383,12 +405,14 @@ __device__ __forceinline__ void warp_max_atomic(T v, unsigned long long* dst) {
 
 // Root-search counters of a warp: one atomic per warp (not per thread: on a flow with many
 // limited nodes per-thread atomics on one address serialise).  All 32 lanes call it.
-__device__ __forceinline__ void warp_rootfind_stats(int caps, int iters, StageStats* st) {
+__device__ __forceinline__ void warp_rootfind_stats(int caps, int iters, int nudged, StageStats* st) {
   const unsigned c = __reduce_add_sync(0xffffffffu, (unsigned)caps);
   const unsigned m = __reduce_max_sync(0xffffffffu, (unsigned)iters);
+  const unsigned g = __reduce_add_sync(0xffffffffu, (unsigned)nudged);
   if ((threadIdx.x & 31) == 0) {
     if (c) atomicAdd(&st->rootfind_cap_hits, (unsigned long long)c);
     if (m) atomicMax(&st->rootfind_max_iters, m);
+    if (g) atomicAdd(&st->bound_nudges, (unsigned long long)g);
   }
 }
 
@@ -425,6 +449,27 @@ struct Nbr {
   }
 };
 
+// Operand scale of the low-order state of node slot me (the limited field): |u_i| + 2 max_j |u_j|
+// over its stencil (the four neighbours; with the unsparsified operator also every node of its
+// two element lines).  u^L_i is u_i plus pair terms whose operands are bounded by
+// lambda (|u_i| + |u_j|) (for the limited field |F.e| <= lambda |u|), and the CFL condition gives
+// dt/m_i sum_j d_ij <= 1/2, so its float32 rounding is a few ulp of this scale.  Read from the
+// stage input still in shared memory; called only for a result outside its bounds.
+template <int P, int TX, int TY, bool DENSE, class S>
+__device__ __forceinline__ auto stencil_scale(const S& s, int me, int le, int a, int b, int row, int col) {
+  using N4 = Nbr<P, TX, TY>;
+  constexpr int n = P + 1, NN = n * n;
+  auto S0 = fabs(s.u[N4::left(me, b, row, col)].v[0]);
+  S0 = tmax(S0, fabs(s.u[N4::right(me, b, row, col)].v[0]));
+  S0 = tmax(S0, fabs(s.u[N4::down(me, a, row, col)].v[0]));
+  S0 = tmax(S0, fabs(s.u[N4::up(me, a, row, col)].v[0]));
+  if constexpr (DENSE) {
+#pragma unroll 1
+    for (int c = 0; c < n; ++c) S0 = tmax(S0, tmax(fabs(s.u[le * NN + a * n + c].v[0]), fabs(s.u[le * NN + c * n + b].v[0])));
+  }
+  return fabs(s.u[me].v[0]) + decltype(S0)(2) * S0;
+}
+
 // Entropy-bound violation of a limited result fe at node slot me: max(0, 1 - sigma(fe) / K_i) with
 // K_i = min sigma over the node and its four neighbours of the stage input (still in shared
 // memory).  sigma is evaluated accurately - compensated rho e (a few ulp even where kinetic energy
@@ -450,8 +495,8 @@ __device__ __forceinline__ double entropy_violation64(const S& s, int me, int a,
 // the float32 path), and the root-search counters; warp-reduced, one atomic per warp and quantity.
 template <int P, int TX, int TY, class LAW, typename T, bool DENSE, class S>
 __device__ __forceinline__ void stage_stats(const S& s, const Instance<T>& I, const LawParamsT<T>& lp, bool on,
-                                         Vec<T, LAW::NC> fe, T lo, T hi, T K, int caps, int iters, int me, int a, int b,
-                                         int row, int col) {
+                                         Vec<T, LAW::NC> fe, T lo, T hi, T K, int caps, int iters, int nudged, int me,
+                                         int a, int b, int row, int col) {
   T v = T(0), ev = T(0);
   if (on) {
     // relative to the local bound, floored at the field's magnitude (bounds that are zero up to
@@ -469,7 +514,7 @@ __device__ __forceinline__ void stage_stats(const S& s, const Instance<T>& I, co
       }
     }
   }
-  warp_rootfind_stats(caps, iters, I.stats);
+  warp_rootfind_stats(caps, iters, nudged, I.stats);
   warp_max_atomic(v, &I.stats->max_bound_violation);
   warp_max_atomic(ev, &I.stats->max_entropy_violation);
 }
@@ -521,10 +566,18 @@ __device__ __forceinline__ void elementwise_update(S& s, const Instance<T>& I, c
   }
   __syncthreads();
   T fe[NC];
+  int nudged = 0;
   if (slot) {
     const T ak = s.aK[le];
 #pragma unroll
     for (int q = 0; q < NC; ++q) fe[q] = uL[q] + ak * dtm * rn[q];
+    if constexpr (sizeof(T) == 4) {
+      if (!(fe[0] >= lo && fe[0] <= hi)) {  // rare: the rounding scale only where it is needed
+        const int row = (le / TX) * n + a, col = (le % TX) * n + b;
+        nudged = accept_rounded(fe[0], lo, hi, stencil_scale<P, TX, TY, DENSE>(s, me, le, a, b, row, col) +
+                                                   fabs(uL[0]) + fabs(ak * dtm * rn[0]) + tmax(fabs(lo), fabs(hi)));
+      }
+    }
     if (act) {
 #pragma unroll
       for (int q = 0; q < NC; ++q)
@@ -535,8 +588,8 @@ __device__ __forceinline__ void elementwise_update(S& s, const Instance<T>& I, c
     Vec<T, NC> vf;
 #pragma unroll
     for (int q = 0; q < NC; ++q) vf.v[q] = fe[q];
-    stage_stats<P, TX, TY, LAW, T, DENSE>(s, I, lp, act && move, vf, lo, hi, K, caps, iters, me, a, b,
-                                          (le / TX) * n + a, (le % TX) * n + b);
+    stage_stats<P, TX, TY, LAW, T, DENSE>(s, I, lp, act && move, vf, lo, hi, K, caps, iters, act ? nudged : 0, me,
+                                          a, b, (le / TX) * n + a, (le % TX) * n + b);
   }
 }
 
@@ -876,6 +929,7 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
   __syncthreads();
   // ---------------- E: face coefficients and limited update
   T fe[NC];
+  int nudged = 0;
   if (slot) {
     const T axp = (b < P) ? tmin(at, s.alpha[me + 1]) : T(0);
     const T axm = (b > 0) ? tmin(at, s.alpha[me - 1]) : T(0);
@@ -883,6 +937,14 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
     const T aym = (a > 0) ? tmin(at, s.alpha[me - n]) : T(0);
 #pragma unroll
     for (int q = 0; q < NC; ++q) fe[q] = uL[q] + dtm * (axp * xp[q] - axm * xm[q] + ayp * yp[q] - aym * ym[q]);
+    if constexpr (sizeof(T) == 4) {
+      if (!(fe[0] >= lo && fe[0] <= hi)) {  // rare: the rounding scale only where it is needed
+        const T mag = stencil_scale<P, TX, TY, DENSE>(s, me, le, a, b, row, col) + fabs(uL[0]) +
+                      tmax(fabs(lo), fabs(hi)) +
+                      dtm * (fabs(axp * xp[0]) + fabs(axm * xm[0]) + fabs(ayp * yp[0]) + fabs(aym * ym[0]));
+        nudged = accept_rounded(fe[0], lo, hi, mag);
+      }
+    }
     if (act) {
 #pragma unroll
       for (int q = 0; q < NC; ++q) I.uout[q * N + g] = (I.c0 == T(0)) ? fe[q] : I.c0 * u0[q] + I.c1 * fe[q];
@@ -892,7 +954,8 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
     Vec<T, NC> vf;
 #pragma unroll
     for (int q = 0; q < NC; ++q) vf.v[q] = fe[q];
-    stage_stats<P, TX, TY, LAW, T, DENSE>(s, I, lp, act && move, vf, lo, hi, K, caps, iters, me, a, b, row, col);
+    stage_stats<P, TX, TY, LAW, T, DENSE>(s, I, lp, act && move, vf, lo, hi, K, caps, iters, act ? nudged : 0, me, a,
+                                          b, row, col);
   }
 }
 

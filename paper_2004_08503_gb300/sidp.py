@@ -39,7 +39,7 @@ class sidp_diag(ctypes.Structure):
                 ("rho_min", ctypes.c_double), ("p_min", ctypes.c_double),
                 ("max_bound_violation", ctypes.c_double), ("max_entropy_violation", ctypes.c_double),
                 ("rootfind_max_iters", ctypes.c_int), ("rootfind_cap_hits", ctypes.c_longlong),
-                ("nonfinite", ctypes.c_longlong)]
+                ("nonfinite", ctypes.c_longlong), ("bound_nudges", ctypes.c_longlong)]
 
 
 class SidpError(RuntimeError):

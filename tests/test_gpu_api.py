@@ -95,8 +95,10 @@ def test_device_state_pointer_and_raw_transfer():
 
 @pytest.mark.parametrize("p,nel,kind", [(3, 32, "quad"), (7, 12, "quad"), (3, 48, "blast")])
 def test_mixed_precision_invariants_and_error(p, nel, kind):
-    """Mixed form: positive density and pressure, density bounds and the entropy minimum held to
-    1e-6 relative (measured in float64 on the stored state), and close to the FP64 form."""
+    """Mixed form: positive density and pressure, the density bounds held exactly by the stored
+    float32 state (after the post-round acceptance, which moves only results within rounding of
+    their bound), the entropy minimum held to 1e-6 relative (measured in float64 on the stored
+    state), and close to the FP64 form."""
     res = {}
     for prec in ("fp64", "mixed"):
         sv = sidp.Solver(law="euler", p=p, nx=nel, ny=nel, precision=prec, bc=("outflow",) * 4)
@@ -107,9 +109,13 @@ def test_mixed_precision_invariants_and_error(p, nel, kind):
         res[prec] = (sv.get_state(0), sv.diag())
     d = res["mixed"][1]
     assert d["rho_min"] > 0 and d["p_min"] > 0 and d["nonfinite"] == 0
-    assert d["max_bound_violation"] <= 1e-6
+    assert d["max_bound_violation"] == 0.0
     assert d["max_entropy_violation"] <= 1e-6
     assert d["rootfind_cap_hits"] == 0
+    # the acceptance step is a rounding-level fix-up, not a limiter: few results take it
+    nodes_stages = sv.N * 3 * 30
+    assert 0 <= d["bound_nudges"] <= 0.01 * nodes_stages, d["bound_nudges"]
+    print(f"bound nudges: {d['bound_nudges']} of {nodes_stages} node-stages")
     a, b = res["mixed"][0], res["fp64"][0]
     l1 = np.abs(a - b).mean(axis=1) / np.abs(b).mean(axis=1)
     assert np.all(l1 < 1e-4), l1
@@ -120,3 +126,26 @@ def test_diag_mass_matches_oracle_quadrature():
     sv.set_state(U)
     pb = scheme.Problem(laws.Euler(1.4), 5, 6, 6, bc=("outflow",) * 4)
     np.testing.assert_allclose(sv.diag()["mass"], pb.total_mass(U.reshape(4, pb.Ne, -1)), rtol=1e-14)
+
+
+@pytest.mark.parametrize("p,nel", [(3, 256), (7, 128)])
+def test_mixed_precision_configs_fp64_trajectory_against_oracle(p, nel):
+    """The two mixed-precision workloads' float64 reference trajectory (seeded four-quadrant data,
+    198 SSP-RK3 stages, the leg bench.py compares the float32 path with): from its final state one
+    more limited stage on the GPU, recomputed by the oracle on a seeded sample of elements and
+    compared with the conditioning-aware check (alpha-tilde from the debug capture)."""
+    from fe_compare import euler_fe_check
+    sv = sidp.Solver(law="euler", p=p, nx=nel, ny=nel, precision="fp64", bc=("outflow",) * 4)
+    x, y = sv.node_coords()
+    sv.set_state(inputs.four_quadrant(x, y, 0))
+    sv.step(66)
+    U = sv.get_state(0)
+    dt = sv.compute_dt()
+    sv.set_debug(True)
+    sv.stage(1, dt)
+    pb = scheme.Problem(laws.Euler(1.4), p, nel, nel, bc=("outflow",) * 4)
+    got = sv.get_state(1).reshape(4, pb.Ne, -1)
+    alpha = sv.bounds()["alpha"].reshape(pb.Ne, -1)
+    sample = np.unique(np.random.default_rng(7).integers(0, pb.Ne, 48))
+    euler_fe_check(pb, U.reshape(4, pb.Ne, -1), dt, got[:, sample], alpha[sample], elems=sample)
+    sv.close()
