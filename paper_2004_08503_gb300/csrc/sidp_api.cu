@@ -327,6 +327,9 @@ namespace {
 cudaError_t autotune(sidp_ctx* c) {
   if (c->tuned) return cudaSuccess;
   c->tuned = true;
+  // only subcell limiting without the smoothness indicator has a stage kernel for every shape;
+  // the other modes run the default one
+  if (c->cfg.limiter != 2 || c->cfg.smoothness) { c->tile = 0; return cudaSuccess; }
   if (const char* f = std::getenv("SIDP_TILE")) {
     const int t = std::atoi(f);
     if (t >= 0 && t < kNumTiles) c->tile = t;

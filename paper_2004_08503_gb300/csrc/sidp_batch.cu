@@ -270,9 +270,12 @@ sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int cou
   // one tile shape per degree: the autotuned one when the tuner has run for this (law, p,
   // precision), else the default (fitting the shape to each mesh to cut padding measured slower:
   // more, smaller launches)
+  // (the stage kernels of other limiters and of the smoothness indicator exist for the default
+  // shape only, and a group's task table is built for its shape)
+  const bool any_shape = cfgs[0].limiter == 2 && !cfgs[0].smoothness;
   int ptile[kMaxP + 1];
   for (int p = 1; p <= kMaxP; ++p) {
-    ptile[p] = tuned_tile(cfgs[0].law, p, cfgs[0].precision == SIDP_MIXED ? 1 : 0);
+    ptile[p] = any_shape ? tuned_tile(cfgs[0].law, p, cfgs[0].precision == SIDP_MIXED ? 1 : 0) : 0;
     if (ptile[p] < 0) ptile[p] = 0;
   }
   std::map<std::pair<int, int>, std::vector<int2>> tasks;  // (p, tile) -> tasks

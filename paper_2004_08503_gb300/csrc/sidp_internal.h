@@ -227,11 +227,13 @@ SIDP_DECLARE(LAW_ADVECTION_VAR, float)
       return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, true>(a, bits, s);       \
     if (a.inst.stats && !bits) /* statistics on: the statistics kernel, default tile shape */         \
       return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, false, false, true>(a, bits, s); \
-    switch (tile) {                                                                                    \
-      case 0: return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT>(a, bits, s);     \
-      case 1: return launch_tile<P, kTiles[P][1].tx, kTiles[P][1].ty, LAWTPL<TT>, TT>(a, bits, s);     \
-      case 2: return launch_tile<P, kTiles[P][2].tx, kTiles[P][2].ty, LAWTPL<TT>, TT>(a, bits, s);     \
-      case 3: return launch_tile<P, kTiles[P][3].tx, kTiles[P][3].ty, LAWTPL<TT>, TT>(a, bits, s);     \
+    if (!bits && (a.limiter != 2 || a.si.on)) /* other modes: the general kernel, default tile shape */ \
+      return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT>(a, bits, s);             \
+    switch (tile) { /* subcell limiting without the indicator (and the time step): every tile shape */ \
+      case 0: return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, false, false, false, true>(a, bits, s); \
+      case 1: return launch_tile<P, kTiles[P][1].tx, kTiles[P][1].ty, LAWTPL<TT>, TT, false, false, false, true>(a, bits, s); \
+      case 2: return launch_tile<P, kTiles[P][2].tx, kTiles[P][2].ty, LAWTPL<TT>, TT, false, false, false, true>(a, bits, s); \
+      case 3: return launch_tile<P, kTiles[P][3].tx, kTiles[P][3].ty, LAWTPL<TT>, TT, false, false, false, true>(a, bits, s); \
       default: return cudaErrorInvalidValue;                                                           \
     }                                                                                                  \
   }                                                                                                    \
@@ -241,11 +243,13 @@ SIDP_DECLARE(LAW_ADVECTION_VAR, float)
       return launch_batch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, true>(b, dt, s);  \
     if (b.stats && !dt)                                                                                \
       return launch_batch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, false, true>(b, dt, s); \
+    if (!dt && (b.limiter != 2 || b.si.on))                                                            \
+      return launch_batch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT>(b, dt, s);         \
     switch (tile) {                                                                                    \
-      case 0: return launch_batch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT>(b, dt, s); \
-      case 1: return launch_batch_tile<P, kTiles[P][1].tx, kTiles[P][1].ty, LAWTPL<TT>, TT>(b, dt, s); \
-      case 2: return launch_batch_tile<P, kTiles[P][2].tx, kTiles[P][2].ty, LAWTPL<TT>, TT>(b, dt, s); \
-      case 3: return launch_batch_tile<P, kTiles[P][3].tx, kTiles[P][3].ty, LAWTPL<TT>, TT>(b, dt, s); \
+      case 0: return launch_batch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, false, false, true>(b, dt, s); \
+      case 1: return launch_batch_tile<P, kTiles[P][1].tx, kTiles[P][1].ty, LAWTPL<TT>, TT, false, false, true>(b, dt, s); \
+      case 2: return launch_batch_tile<P, kTiles[P][2].tx, kTiles[P][2].ty, LAWTPL<TT>, TT, false, false, true>(b, dt, s); \
+      case 3: return launch_batch_tile<P, kTiles[P][3].tx, kTiles[P][3].ty, LAWTPL<TT>, TT, false, false, true>(b, dt, s); \
       default: return cudaErrorInvalidValue;                                                           \
     }                                                                                                  \
   }

@@ -49,12 +49,24 @@ struct TileGeom {
   static constexpr int NH = 2 * NX + 2 * NY;  // halo slots: W[NY], E[NY], S[NX], N[NX]
   static constexpr int NS = NT + NH;
   static constexpr int hW = NT, hE = NT + NY, hS = NT + 2 * NY, hN = NT + 2 * NY + NX;
-  static constexpr int NFX = NY * (NX + 1), NFY = NX * (NY + 1);  // x faces [row][c], y faces [r][col]
+  // Faces, indexed by node slot so that a warp's face accesses fall in distinct shared-memory
+  // banks like its node accesses: x face k < NT is the face on the left of node slot k, NT + row the
+  // face on the tile's east edge; y face k < NT is the face below node slot k, NT + col the face on
+  // the tile's north edge.
+  static constexpr int NFX = NT + NY, NFY = NT + NX;
   static constexpr int THREADS = ((NT + 31) / 32) * 32;
   static constexpr int MINB = (THREADS <= 256) ? 4 : 2;  // register budget for 32 resident warps per SM
   __device__ __forceinline__ static int slot(int row, int col) {
     const int ty = row / n, a = row - ty * n, tx = col / n, b = col - tx * n;
     return (ty * TX + tx) * NN + a * n + b;
+  }
+  // the x face on the right of node slot t (b its x index in the element, at tile column col)
+  __device__ __forceinline__ static int xface_right(int t, int b, int row, int col) {
+    return (col == NX - 1) ? NT + row : t + ((b == P) ? NN - P : 1);
+  }
+  // the y face above node slot t (a its y index in the element, at tile row row)
+  __device__ __forceinline__ static int yface_up(int t, int a, int row, int col) {
+    return (row == NY - 1) ? NT + col : t + ((a == P) ? TX * NN - P * n : n);
   }
 };
 
@@ -336,22 +348,42 @@ __device__ T entropy_root(const T* uL, const T* w, T K, T psi0, T target, T tmax
 
 // Euler: largest t in [0, tcap] such that every candidate u^L + t w_c, w_c = gamma_d dt/m (+-r-bar),
 // has rho > 0 and psi_K >= min(0, psi_K(u^L)).  Along each candidate the admissible set is an
-// interval [0, t*], so the candidates are taken in turn with the running cap; all four are first
-// tested at tcap in one pass, and only those that fail there need a root search.
+// interval [0, t*], so the candidates are taken in turn with the running cap.  First all four
+// are tested at tcap against psi_K >= 0 (stricter than the target min(0, psi_K(u^L))) with the
+// cheap certified test, without branches; only when some candidate is undecided are the target
+// and the precise tests evaluated, and only those that fail there need a root search.
 template <class LAW, typename T>
 __device__ T entropy_limit(const T* uL, T K, const T* xp, const T* xm, const T* yp, const T* ym, T sc, T tcap,
                            const LawParamsT<T>& lp, int& iters, int& caps) {
   if (!(tcap > T(0))) return tcap;
-  // target = min(0, psi_K(u^L)); the precise psi is needed only when u^L is not certainly inside
-  const T target = LAW::psi_certainly_ge(uL, K, T(0), lp) ? T(0) : tmin(LAW::psi(uL, K, lp), T(0));
-  unsigned fail = 0;
+  const T ts = tcap * sc;
+  unsigned undecided = 0;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     T ut[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       const T v = (c == 0) ? xp[f] : (c == 1) ? -xm[f] : (c == 2) ? yp[f] : -ym[f];
-      ut[f] = uL[f] + tcap * (sc * v);
+      // float64 keeps the oracle's order of operations, u^L + t (scale r-bar)
+      ut[f] = (sizeof(T) == 8) ? uL[f] + tcap * (sc * v) : uL[f] + ts * v;
+    }
+    const bool ok = (ut[0] > T(0)) && LAW::psi_certainly_ge(ut, K, T(0), lp);
+    undecided |= ok ? 0u : (1u << c);
+  }
+  if (!undecided) return tcap;
+  // target = min(0, psi_K(u^L)); the precise psi is needed only when u^L is not certainly inside
+  const T target = LAW::psi_certainly_ge(uL, K, T(0), lp) ? T(0) : tmin(LAW::psi(uL, K, lp), T(0));
+  unsigned fail = 0;
+#pragma unroll 1
+  while (undecided) {
+    const int c = __ffs(undecided) - 1;
+    undecided &= undecided - 1;
+    T ut[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const T v = (c == 0) ? xp[f] : (c == 1) ? -xm[f] : (c == 2) ? yp[f] : -ym[f];
+      // float64 keeps the oracle's order of operations, u^L + t (scale r-bar)
+      ut[f] = (sizeof(T) == 8) ? uL[f] + tcap * (sc * v) : uL[f] + ts * v;
     }
     if (!(ut[0] > T(0) && (LAW::psi_certainly_ge(ut, K, target, lp) || LAW::psi(ut, K, lp) >= target)))
       fail |= 1u << c;
@@ -657,11 +689,16 @@ __device__ __forceinline__ void dense_line(const S& s, int k, int base, int stri
 }
 
 // ELW selects elementwise limiting at compile time (its kernels are separate instantiations, so
-// the subcell kernels carry none of its code).
-template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool DENSE = false, bool STATS = true>
+// the subcell kernels carry none of its code).  SUBCELL: the configuration of the production runs
+// (subcell limiting, smoothness indicator off) fixed at compile time, so that the kernel carries
+// none of the other modes' branches.
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool DENSE = false, bool STATS = true,
+          bool SUBCELL = false>
 __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const Instance<T>& I, const Tables<T>& tab,
-                                           const LawParamsT<T>& lp, int limiter, const SmoothnessT<T>& si, int tile_x,
+                                           const LawParamsT<T>& lp, int limiter_, const SmoothnessT<T>& si, int tile_x,
                                            int tile_y) {
+  const int limiter = SUBCELL ? 2 : limiter_;
+  const bool si_on = SUBCELL ? false : (si.on != 0);
   using G = TileGeom<P, TX, TY>;
   using V = Vec<T, LAW::NC>;
   constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
@@ -681,18 +718,18 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
     const V uR = s.u[t];
     const typename LAW::Aux aR = s.aux[t];
     const T sR = LAW::kEntropy ? s.sig[t] : T(0);
-    face_eval_r<LAW>(s, 0, Nbr<P, TX, TY>::left(t, b, row, col), uR, s.fx[t], aR, sR, row * (G::NX + 1) + col, lp);
-    face_eval_r<LAW>(s, 1, Nbr<P, TX, TY>::down(t, a, row, col), uR, s.fy[t], aR, sR, row * G::NX + col, lp);
+    face_eval_r<LAW>(s, 0, Nbr<P, TX, TY>::left(t, b, row, col), uR, s.fx[t], aR, sR, t, lp);
+    face_eval_r<LAW>(s, 1, Nbr<P, TX, TY>::down(t, a, row, col), uR, s.fy[t], aR, sR, t, lp);
   }
   for (int e2 = t; e2 < G::NY + G::NX; e2 += G::THREADS) {
     if (e2 < G::NY) {  // east edge: slot (row, NX-1) | halo E
       const int row = e2;
       const int L = G::slot(row, G::NX - 1), R = G::hE + row;
-      face_eval_r<LAW>(s, 0, L, s.u[R], s.fx[R], s.aux[R], LAW::kEntropy ? s.sig[R] : T(0), row * (G::NX + 1) + G::NX, lp);
+      face_eval_r<LAW>(s, 0, L, s.u[R], s.fx[R], s.aux[R], LAW::kEntropy ? s.sig[R] : T(0), G::NT + row, lp);
     } else {  // north edge: slot (NY-1, col) | halo N
       const int col = e2 - G::NY;
       const int L = G::slot(G::NY - 1, col), R = G::hN + col;
-      face_eval_r<LAW>(s, 1, L, s.u[R], s.fy[R], s.aux[R], LAW::kEntropy ? s.sig[R] : T(0), G::NY * G::NX + col, lp);
+      face_eval_r<LAW>(s, 1, L, s.u[R], s.fy[R], s.aux[R], LAW::kEntropy ? s.sig[R] : T(0), G::NT + col, lp);
     }
   }
   __syncthreads();
@@ -701,7 +738,7 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
   // Legendre coefficients of the limited field (separable nodal -> modal transform), s_K =
   // log10(||u - u-hat||^2 / ||u||^2) with u-hat dropping the modes of degree p in either variable
   const bool slot0 = (G::NT == G::THREADS) || (t < G::NT);
-  if (si.on && limiter >= 2) {
+  if (si_on && limiter >= 2) {
     const int base = le * NN;
     if (slot0) {
       T c1 = T(0);
@@ -748,17 +785,15 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
   const T h = I.hT;
   const int row = (le / TX) * n + a, col = (le % TX) * n + b;
   const int me = le * NN + a * n + b;
-  const int ix = row * (G::NX + 1) + col, iy = row * G::NX + col;  // left x face, bottom y face
+  // the node's four faces: left and bottom at its own slot, right and top at the neighbour's (or
+  // on the tile edge)
+  const int ix = me, ixr = G::xface_right(me, b, row, col), iy = me, iyu = G::yface_up(me, a, row, col);
   const long long N = I.N;
   T uL[NC], rx[NC], ry[NC];
   T lo = T(0), hi = T(0), K = T(0), m = T(1), dtm = T(0);
   if (slot) {
-    const V vu = s.u[me], vfx = s.fx[me], vfy = s.fy[me];
-    const V fl = s.fbx[ix], fr = s.fbx[ix + 1], fd = s.fby[iy], fu = s.fby[iy + G::NX];
-    const T wa = s.w[a], wb = s.w[b];
-    const T hwa = h * wa, hwb = h * wb;
-    m = h * h * wa * wb;
-    dtm = move ? fdiv(dt, m) : T(0);
+    // the line contractions first: the node's own fluxes and its face fluxes are loaded after
+    // them, so that fewer values are live at once
     T sx[NC], sy[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) { sx[q] = T(0); sy[q] = T(0); }
@@ -771,6 +806,12 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
 #pragma unroll
       for (int q = 0; q < NC; ++q) { sx[q] += dx * Fxc.v[q]; sy[q] += dy * Fyc.v[q]; }
     }
+    const V vu = s.u[me], vfx = s.fx[me], vfy = s.fy[me];
+    const V fl = s.fbx[ix], fr = s.fbx[ixr], fd = s.fby[iy], fu = s.fby[iyu];
+    const T wa = s.w[a], wb = s.w[b];
+    const T hwa = h * wa, hwb = h * wb;
+    m = h * h * wa * wb;
+    dtm = move ? fdiv(dt, m) : T(0);
     T dvx[NC], dgx[NC], dvy[NC], dgy[NC];
     T dlo = vu.v[0], dhi = vu.v[0], dsig = T(0), dlam = T(0);
     if constexpr (DENSE) {
@@ -804,7 +845,7 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
       for (int q = 0; q < NC; ++q)
         I.uout[q * N + g] = (I.c0 == T(0)) ? out[q] : I.c0 * I.u0[q * N + g] + I.c1 * out[q];
     }
-    const auto bl = s.bbx[ix], br = s.bbx[ix + 1], bd = s.bby[iy], bu = s.bby[iy + G::NX];
+    const auto bl = s.bbx[ix], br = s.bbx[ixr], bd = s.bby[iy], bu = s.bby[iyu];
     if constexpr (DENSE) {  // in-element pairs from the dense lines, plus the element-face pairs
       lo = dlo;
       hi = dhi;
@@ -816,7 +857,7 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
       lo = tmin(tmin(vu.v[0], tmin(bl.v[0], br.v[0])), tmin(bd.v[0], bu.v[0]));
       hi = tmax(tmax(vu.v[0], tmax(bl.v[0], br.v[0])), tmax(bd.v[0], bu.v[0]));
     }
-    if (si.on) {  // Eq. relaxed-bounds
+    if (si_on) {  // Eq. relaxed-bounds
       const T e = s.eps[le];
       lo = e * lo + (T(1) - e) * si.gmin;
       hi = e * hi + (T(1) - e) * si.gmax;
@@ -961,14 +1002,16 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
 
 // STATS: a kernel with the per-stage statistics (launched when they are on); the timed kernels
 // carry none of their code.
-template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool DENSE = false, bool STATS = false>
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool DENSE = false, bool STATS = false,
+          bool SUBCELL = false>
 __global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
 k_stage(const StageLaunch<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   auto& s = *reinterpret_cast<TileSmem<P, TX, TY, LAW, T>*>(smem_raw);
   const int tiles_x = (A.inst.nx + TX - 1) / TX;
   const int tile_y = blockIdx.x / tiles_x, tile_x = blockIdx.x - tile_y * tiles_x;
-  stage_body<P, TX, TY, LAW, T, ELW, DENSE, STATS || ELW || DENSE>(s, A.inst, A.tab, A.lp, A.limiter, A.si, tile_x, tile_y);
+  stage_body<P, TX, TY, LAW, T, ELW, DENSE, STATS || ELW || DENSE, SUBCELL>(s, A.inst, A.tab, A.lp, A.limiter, A.si,
+                                                                              tile_x, tile_y);
 }
 
 // Copy the instance descriptor of this CTA's task into shared memory (all threads help).
@@ -983,7 +1026,7 @@ __device__ __forceinline__ void load_instance(Instance<T>& dst, const Instance<T
 
 // Batched stage: CTA blockIdx.x runs task (instance, tile) of the task table; all tasks of one
 // launch share P, the tile shape, law and precision.
-template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool STATS = false>
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool STATS = false, bool SUBCELL = false>
 __global__ void __launch_bounds__(TileGeom<P, TX, TY>::THREADS, TileGeom<P, TX, TY>::MINB)
 k_stage_batch(const BatchLaunch<T> B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -993,7 +1036,7 @@ k_stage_batch(const BatchLaunch<T> B) {
   load_instance(sI, B.insts + task.x);
   const int tiles_x = (sI.nx + TX - 1) / TX;
   const int tile_y = task.y / tiles_x, tile_x = task.y - tile_y * tiles_x;
-  stage_body<P, TX, TY, LAW, T, ELW, false, STATS || ELW>(s, sI, B.tab, B.lp, B.limiter, B.si, tile_x, tile_y);
+  stage_body<P, TX, TY, LAW, T, ELW, false, STATS || ELW, SUBCELL>(s, sI, B.tab, B.lp, B.limiter, B.si, tile_x, tile_y);
 }
 
 // CFL bound of Eq. cfl-low per node, m_i / (2 sum_{j != i} d-hat_ij) with d-hat = (h w / 2) lambda on
@@ -1018,19 +1061,19 @@ __device__ __forceinline__ void dt_body(DtSmem<P, TX, TY, LAW, T>& s, const Inst
     const typename LAW::Aux aR = s.aux[t];
     const int L = Nbr<P, TX, TY>::left(t, b, row, col), D = Nbr<P, TX, TY>::down(t, a, row, col);
     const V uL = s.u[L], uD = s.u[D];
-    lamx[row * (G::NX + 1) + col] = LAW::lam(0, uL.v, s.aux[L], uR.v, aR, lp);
-    lamy[row * G::NX + col] = LAW::lam(1, uD.v, s.aux[D], uR.v, aR, lp);
+    lamx[t] = LAW::lam(0, uL.v, s.aux[L], uR.v, aR, lp);
+    lamy[t] = LAW::lam(1, uD.v, s.aux[D], uR.v, aR, lp);
   }
   for (int e2 = t; e2 < G::NY + G::NX; e2 += G::THREADS) {
     if (e2 < G::NY) {
       const int L = G::slot(e2, G::NX - 1), R = G::hE + e2;
       const V uL = s.u[L], uR = s.u[R];
-      lamx[e2 * (G::NX + 1) + G::NX] = LAW::lam(0, uL.v, s.aux[L], uR.v, s.aux[R], lp);
+      lamx[G::NT + e2] = LAW::lam(0, uL.v, s.aux[L], uR.v, s.aux[R], lp);
     } else {
       const int col = e2 - G::NY;
       const int L = G::slot(G::NY - 1, col), R = G::hN + col;
       const V uL = s.u[L], uR = s.u[R];
-      lamy[G::NY * G::NX + col] = LAW::lam(1, uL.v, s.aux[L], uR.v, s.aux[R], lp);
+      lamy[G::NT + col] = LAW::lam(1, uL.v, s.aux[L], uR.v, s.aux[R], lp);
     }
   }
   __syncthreads();
@@ -1040,14 +1083,15 @@ __device__ __forceinline__ void dt_body(DtSmem<P, TX, TY, LAW, T>& s, const Inst
   T val = big;
   if (act) {
     const int row = (le / TX) * n + a, col = (le % TX) * n + b;
-    const int ix = row * (G::NX + 1) + col, iy = row * G::NX + col;
+    const int me = le * (n * n) + a * n + b;
+    const int ix = me, ixr = G::xface_right(me, b, row, col), iy = me, iyu = G::yface_up(me, a, row, col);
     const T h = I.hT;
     const T wa = s.w[a], wb = s.w[b];
-    T sumd = T(0.5) * h * wa * (lamx[ix] + lamx[ix + 1]) + T(0.5) * h * wb * (lamy[iy] + lamy[iy + G::NX]);
+    T sumd = T(0.5) * h * wa * (lamx[ix] + lamx[ixr]) + T(0.5) * h * wb * (lamy[iy] + lamy[iyu]);
     if constexpr (DENSE) {  // element-face pairs as above; every in-element pair of the dense lines
       constexpr int NN = n * n;
-      sumd = T(0.5) * h * wa * (((b == 0) ? lamx[ix] : T(0)) + ((b == P) ? lamx[ix + 1] : T(0))) +
-             T(0.5) * h * wb * (((a == 0) ? lamy[iy] : T(0)) + ((a == P) ? lamy[iy + G::NX] : T(0)));
+      sumd = T(0.5) * h * wa * (((b == 0) ? lamx[ix] : T(0)) + ((b == P) ? lamx[ixr] : T(0))) +
+             T(0.5) * h * wb * (((a == 0) ? lamy[iy] : T(0)) + ((a == P) ? lamy[iyu] : T(0)));
       const int me = le * NN + a * n + b;
       const V ui = s.u[me];
       const typename LAW::Aux ai = s.aux[me];
@@ -1107,14 +1151,15 @@ k_dt_batch(const BatchLaunch<T> B) {
   dt_body<P, TX, TY, LAW, T>(s, sI, B.tab, B.lp, tile_x, tile_y, B.bits + task.x);
 }
 
-template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool DENSE = false, bool STATS = false>
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool DENSE = false, bool STATS = false,
+          bool SUBCELL = false>
 cudaError_t launch_tile(const StageLaunch<T>& a, unsigned long long* dt_bits, cudaStream_t s) {
   using G = TileGeom<P, TX, TY>;
   constexpr size_t smem = sizeof(TileSmem<P, TX, TY, LAW, T>);
   constexpr size_t smem_dt = sizeof(DtSmem<P, TX, TY, LAW, T>);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(k_stage<P, TX, TY, LAW, T, ELW, DENSE, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = cudaFuncSetAttribute(k_stage<P, TX, TY, LAW, T, ELW, DENSE, STATS, SUBCELL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(k_dt<P, TX, TY, LAW, T, DENSE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dt);
     if (err != cudaSuccess) return err;
@@ -1123,18 +1168,18 @@ cudaError_t launch_tile(const StageLaunch<T>& a, unsigned long long* dt_bits, cu
   const long long tiles = (long long)((a.inst.nx + TX - 1) / TX) * ((a.inst.ny + TY - 1) / TY);
   if (tiles <= 0) return cudaSuccess;
   if (dt_bits) k_dt<P, TX, TY, LAW, T, DENSE><<<(unsigned)tiles, G::THREADS, smem_dt, s>>>(a, dt_bits);
-  else k_stage<P, TX, TY, LAW, T, ELW, DENSE, STATS><<<(unsigned)tiles, G::THREADS, smem, s>>>(a);
+  else k_stage<P, TX, TY, LAW, T, ELW, DENSE, STATS, SUBCELL><<<(unsigned)tiles, G::THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool STATS = false>
+template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool STATS = false, bool SUBCELL = false>
 cudaError_t launch_batch_tile(const BatchLaunch<T>& B, bool dt, cudaStream_t s) {
   using G = TileGeom<P, TX, TY>;
   constexpr size_t smem = sizeof(TileSmem<P, TX, TY, LAW, T>);
   constexpr size_t smem_dt = sizeof(DtSmem<P, TX, TY, LAW, T>);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(k_stage_batch<P, TX, TY, LAW, T, ELW, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = cudaFuncSetAttribute(k_stage_batch<P, TX, TY, LAW, T, ELW, STATS, SUBCELL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(k_dt_batch<P, TX, TY, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dt);
     if (err != cudaSuccess) return err;
@@ -1142,7 +1187,7 @@ cudaError_t launch_batch_tile(const BatchLaunch<T>& B, bool dt, cudaStream_t s) 
   }
   if (B.ntasks <= 0) return cudaSuccess;
   if (dt) k_dt_batch<P, TX, TY, LAW, T><<<(unsigned)B.ntasks, G::THREADS, smem_dt, s>>>(B);
-  else k_stage_batch<P, TX, TY, LAW, T, ELW, STATS><<<(unsigned)B.ntasks, G::THREADS, smem, s>>>(B);
+  else k_stage_batch<P, TX, TY, LAW, T, ELW, STATS, SUBCELL><<<(unsigned)B.ntasks, G::THREADS, smem, s>>>(B);
   return cudaGetLastError();
 }
 
