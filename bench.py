@@ -35,15 +35,18 @@ sys.path.insert(0, ROOT)
 METRIC = "node-updates/s per RK stage (Euler 2D p=3), mixed vs FP64; % HBM roofline"
 UNIT = "node-updates/s"
 # dram__bytes (read + write) per node and stage launch, averaged over the three stages, measured by
-# ncu on the 768x768 p=3 blast.  The counters belong to the stage kernel as it was captured; a
-# changed kernel needs a new capture.
-STAGE_DRAM_BYTES_PER_NODE = 39.4
+# ncu on the 768x768 p=3 blast (two steps in, stages 1-3 with the tile shape 2x8).  The counters
+# belong to the stage kernel as it was captured; a changed kernel needs a new capture.
+STAGE_DRAM_BYTES_PER_NODE = 39.2
 # Executed FP32 flops (2 x FFMA + FADD + FMUL) and warp instructions per node of stages 1, 2, 3
-# from the InstructionStats counters of the same capture: the two other ceilings of the stage
-# kernel, reported beside the HBM roofline (the kernel is bound by instruction issue).
-STAGE_FP32_FLOP_PER_NODE = (691.0, 449.0, 449.0)
-STAGE_WARP_INSTR_PER_NODE = (36.3, 28.4, 28.4)
-SMS, FP32_LANES_PER_SM, SCHEDULERS_PER_SM = 152, 128, 4
+# from the same capture: the two other ceilings of the stage kernel, reported beside the HBM
+# roofline.
+STAGE_FP32_FLOP_PER_NODE = (363.9, 371.9, 371.9)
+STAGE_WARP_INSTR_PER_NODE = (27.2, 27.2, 27.2)
+# The float64 stage kernel's executed FP64 flops per node (2 x DFMA + DADD + DMUL), stages 1-3,
+# from an ncu capture of the same workload in float64: its FP64-pipe roofline.
+FP64_STAGE_FLOP_PER_NODE = (1197.7, 1196.9, 1197.6)
+SMS, SCHEDULERS_PER_SM = 152, 4
 # The curved-mesh stage kernel's DRAM traffic per node and launch (stages 1-3 averaged), from one
 # ncu capture of the 768x768 curved leg.  The kernel has changed since (the smoothness-indicator block, off in this workload), so the figure is not
 # reported as the launch's traffic until it is captured again.
@@ -173,21 +176,23 @@ def time_steps(torch, sv, stream, steps, warmup, dist=None, clocks_gpu=None):
     return sec, (clk.summary() if clk else None)
 
 
-def other_ceilings(nodes, kt, clk):
-    """FP32 pipe and instruction-issue fractions of the stage kernel at the sampled SM clock."""
+def other_ceilings(nodes, kt, clk, fp32_peak):
+    """FP32 pipe (against the measured FMA throughput) and instruction-issue (nominal: 4
+    schedulers per SM at the sampled SM clock) fractions of the stage kernel."""
     mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz")
     if not mhz or not all(kt):
         return None
     hz = 1e6 * float(mhz)
     flops = sum(f * nodes for f in STAGE_FP32_FLOP_PER_NODE) / sum(kt)
     issue = sum(w * nodes for w in STAGE_WARP_INSTR_PER_NODE) / sum(kt)
-    fp32_peak = SMS * FP32_LANES_PER_SM * 2 * hz
     issue_peak = SMS * SCHEDULERS_PER_SM * hz
     return {"sm_mhz": float(mhz),
             "fp32": {"achieved": flops / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
-                     "frac": flops / fp32_peak, "flop_per_node": list(STAGE_FP32_FLOP_PER_NODE)},
+                     "frac": flops / fp32_peak, "flop_per_node": list(STAGE_FP32_FLOP_PER_NODE),
+                     "peak_kind": "measured (sidp_fma_peak, float32)"},
             "issue": {"achieved": issue / 1e12, "peak": issue_peak / 1e12, "unit": "T warp-instr/s",
-                      "frac": issue / issue_peak, "warp_instr_per_node": list(STAGE_WARP_INSTR_PER_NODE)}}
+                      "frac": issue / issue_peak, "warp_instr_per_node": list(STAGE_WARP_INSTR_PER_NODE),
+                      "peak_kind": "nominal at the sampled clock"}}
 
 
 def stage_kernel_times(torch, sv, stream, reps):
@@ -244,35 +249,53 @@ def run_curved(torch, sidp, stream, steps, warmup, hbm, peak_kind):
             "invariants": {"rho_min": d["rho_min"], "p_min": d["p_min"], "nonfinite": d["nonfinite"]}}
 
 
-def cpu_baseline(seconds_target=12.0):
-    """The oracle as it stands on a bounded random sample of the workload's elements."""
+def _oracle_strip(args):
+    """One worker of cpu_baseline: the oracle's forward-Euler stage on a strip of element rows of
+    the workload (its own blast data and outflow sides; every element of the strip is computed).
+    Returns (nodes, seconds of the stage alone)."""
+    nel, row0, rows, dt = args
     from oracle import laws, scheme
     from paper_2004_08503_gb300 import inputs
-    pb = scheme.Problem(laws.Euler(1.4), P, NEL, NEL, bc=("outflow",) * 4)
+    h = 1.0 / nel
+    pb = scheme.Problem(laws.Euler(1.4), P, nel, rows, domain=(0.0, 1.0, row0 * h, (row0 + rows) * h),
+                        bc=("outflow",) * 4)
     X, Y = pb.node_coords()
     U = inputs.blast(X, Y)
     del X, Y
-    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    pb.fe_stage(U, dt)
+    return pb.Ne * (P + 1) ** 2, time.perf_counter() - t0
+
+
+def cpu_baseline():
+    """The oracle as it stands on all host cores: one forward-Euler stage of the whole workload,
+    its element rows split into one strip per core (a process each, spawned; numpy runs one
+    thread per process here).  Rate = all nodes / the slowest strip's time."""
+    import multiprocessing as mp
+    from oracle import laws, scheme
+    from paper_2004_08503_gb300 import inputs
+    cores = max(1, os.cpu_count() or 1)
+    # the workload's time step: its largest wave speeds sit in the blast centre
+    pb = scheme.Problem(laws.Euler(1.4), P, NEL, NEL, bc=("outflow",) * 4)
     c = NEL // 2
     centre = np.array([(c + dy) * NEL + c + dx for dy in range(-8, 8) for dx in range(-8, 8)])
-    nsel = 1024
-    sel = np.unique(np.concatenate([centre, rng.integers(0, pb.Ne, nsel)]))
-    # dt of the workload: its largest wave speeds sit in the blast centre
+    X, Y = pb.node_coords()
+    U = inputs.blast(X, Y)
+    del X, Y
     tot = pb.sum_dhat(U, centre)
     dt = pb.cfl * float(np.min(pb.mass[None, :] / (2.0 * tot)))
-    t0 = time.perf_counter()
-    stages = 0
-    while True:
-        pb.fe_stage(U, dt, elems=sel)
-        stages += 1
-        if time.perf_counter() - t0 > seconds_target or stages >= 30:
-            break
-    sec = time.perf_counter() - t0
-    nodes = len(sel) * (P + 1) ** 2
-    return {"value": nodes * stages / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{stages} forward-Euler stages of the FP64 numpy oracle on {len(sel)} of the "
-                      f"{pb.Ne} elements ({nodes} nodes: the 256 blast-centre elements plus a seeded random "
-                      f"sample), single thread"}
+    del U, pb
+    bounds = np.linspace(0, NEL, cores + 1).astype(int)
+    jobs = [(NEL, int(a), int(b - a), dt) for a, b in zip(bounds[:-1], bounds[1:]) if b > a]
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        res = pool.map(_oracle_strip, jobs)
+    nodes = sum(r[0] for r in res)
+    sec = max(r[1] for r in res)
+    return {"value": nodes / sec, "unit": UNIT, "cores": len(jobs), "kind": "oracle",
+            "sample": f"one forward-Euler stage of the FP64 numpy oracle over the whole {NEL}x{NEL} p={P} blast "
+                      f"({nodes} nodes), split into {len(jobs)} strips of element rows, one spawned process per "
+                      f"host core (numpy single-threaded); rate = nodes / slowest strip's stage time "
+                      f"({sec:.1f} s)"}
 
 
 def run_reference(args):
@@ -522,6 +545,8 @@ def main():
     sidp.load()
     stream = torch.cuda.Stream()
     hbm, peak_kind = peaks()
+    fp32_peak = sidp.sidp_fma_peak("mixed", stream)
+    fp64_peak = sidp.sidp_fma_peak("fp64", stream)
 
     # ---------------- mixed precision: the headline
     sv = make_solver("mixed", stream)
@@ -562,8 +587,13 @@ def main():
         fp64_value = whole_job_rate(nodes * 3 * args.fp64_steps, world, sec64)
         kt64 = stage_kernel_times(torch, sv64, stream, reps=2)
         sv64.close()
+        fl64 = sum(f * nodes for f in FP64_STAGE_FLOP_PER_NODE) / sum(kt64)
         fp64 = {"value": fp64_value, "unit": UNIT, "steps": args.fp64_steps,
-                "stage_ms": [1e3 * t for t in kt64], "speedup_mixed_over_fp64": value / fp64_value}
+                "stage_ms": [1e3 * t for t in kt64], "speedup_mixed_over_fp64": value / fp64_value,
+                "roofline": {"bound": "fp64", "achieved": fl64 / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+                             "frac": fl64 / fp64_peak, "flop_per_node": list(FP64_STAGE_FLOP_PER_NODE),
+                             "kernel": "k_stage<3, LawEuler<double>, double>",
+                             "peak_kind": "measured (sidp_fma_peak, float64 fused multiply-add)"}}
 
     curved = None
     if not args.no_curved:
@@ -591,7 +621,7 @@ def main():
                              "traffic": traffic, "kernel": "k_stage<3, LawEuler<float>, float>",
                              "stage_ms": [1e3 * t for t in kt], "peak_kind": peak_kind,
                              "whole_step_gbs": step_gbs, "whole_step_frac": step_gbs / hbm,
-                             "other_ceilings": other_ceilings(nodes, kt, clk)},
+                             "other_ceilings": other_ceilings(nodes, kt, clk, fp32_peak)},
                 "fp64": fp64, "curved": curved, "batched": batched, "invariants": diag_stats, "accuracy": accuracy, "dmr": dmr,
                 "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": 5 * args.steps}

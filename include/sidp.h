@@ -212,6 +212,13 @@ sidp_status sidp_device_state(sidp_ctx* ctx, void** dptr, int* dtype, long long*
 /* Eq. cfl-low: dt = cfl * min_i m_i / (2 sum_{j != i} d-hat_ij) on u^n; synchronises. */
 sidp_status sidp_compute_dt(sidp_ctx* ctx, double* dt);
 
+/* Measured fused multiply-add throughput of the current GPU in flop/s (one FMA = 2 flops):
+ * precision SIDP_MIXED for float32, SIDP_FP64 for float64.  The paper has no counterpart: these
+ * are the arithmetic ceilings the float32 and float64 stage kernels are placed against, beside
+ * the HBM bandwidth.  Independent FMA chains in every thread of an occupancy-filling launch, timed
+ * with CUDA events on cuda_stream; runs for a few tens of milliseconds and synchronises. */
+sidp_status sidp_fma_peak(int precision, double* flop_per_s, void* cuda_stream);
+
 /* The time step of sidp_compute_dt for a caller-owned device state, with no device allocation.
  * The paper has no counterpart: this serves callers that cannot allocate device memory where
  * they need a time step (an application whose pool allocator owns all device memory, a real-time

@@ -17,7 +17,7 @@ NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-ftz=true", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
          "-diag-suppress", "177"]
-SOURCES = ["sidp_api.cu", "sidp_batch.cu", "sidp_tables.cpp", "sidp_geometry.cpp", "sidp_noalloc.cu",
+SOURCES = ["sidp_api.cu", "sidp_batch.cu", "sidp_tables.cpp", "sidp_geometry.cpp", "sidp_noalloc.cu", "sidp_peaks.cu",
            "inst_burgers_f64.cu", "inst_burgers_f32.cu", "inst_advection_f64.cu", "inst_advection_f32.cu",
            "inst_advection_var_f64.cu", "inst_advection_var_f32.cu",
            "inst_euler_f64_a.cu", "inst_euler_f64_b.cu", "inst_euler_f64_c.cu",

@@ -88,6 +88,7 @@ _SIGS = {
     "sidp_batch_set_state": (ctypes.c_int, [_P, ctypes.c_int, _D]),
     "sidp_batch_get_state": (ctypes.c_int, [_P, ctypes.c_int, _D]),
     "sidp_batch_get_buffer": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _D]),
+    "sidp_fma_peak": (ctypes.c_int, [ctypes.c_int, _D, _P]),
     "sidp_batch_stage": (ctypes.c_int, [_P, ctypes.c_int, _D]),
     "sidp_batch_set_debug": (ctypes.c_int, [_P, ctypes.c_int]),
     "sidp_batch_get_bounds": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D, _D]),
@@ -385,6 +386,13 @@ def sidp_batch_get_bounds(b, i):
     out = [np.empty(n) for _ in range(4)]
     _bcheck(load().sidp_batch_get_bounds(b, i, *[_ptr(o) for o in out]), b)
     return dict(zip(("lo", "hi", "K", "alpha"), out))
+
+
+def sidp_fma_peak(precision, stream=None):
+    """Measured FMA throughput in flop/s ("mixed": float32, "fp64": float64)."""
+    out = ctypes.c_double()
+    _check(load().sidp_fma_peak(PRECISIONS[precision], ctypes.byref(out), _stream_handle(stream)))
+    return out.value
 
 
 def sidp_batch_step(b, nsteps=1):

@@ -149,3 +149,12 @@ def test_mixed_precision_configs_fp64_trajectory_against_oracle(p, nel):
     sample = np.unique(np.random.default_rng(7).integers(0, pb.Ne, 48))
     euler_fe_check(pb, U.reshape(4, pb.Ne, -1), dt, got[:, sample], alpha[sample], elems=sample)
     sv.close()
+
+
+def test_fma_peak_measurement_is_plausible():
+    """sidp_fma_peak: float32 within a factor of two of the nominal FMA rate of the part (152 SMs x
+    128 lanes x 2 flops at 1-2.1 GHz: 39-81 TFLOP/s), float64 a small positive fraction of it."""
+    f32 = sidp.sidp_fma_peak("mixed")
+    f64 = sidp.sidp_fma_peak("fp64")
+    assert 20e12 < f32 < 100e12, f32
+    assert 0 < f64 < 0.5 * f32, (f64, f32)
