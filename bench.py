@@ -370,17 +370,11 @@ def run_e2e(torch, sidp, sv, U, stream, args, dist, world, nodes):
             "steps": e_steps}
 
 
-def run_batched(torch, sidp, stream, steps, warmup, seed=0, count=512):
-    """Batched workload: `count` independent Euler problems, elements per side from {8,16,32,64}
-    and p from {2..7} (seeded), seeded four-quadrant data, mixed precision, outflow sides."""
-    from paper_2004_08503_gb300 import inputs
-    shapes = inputs.batch_shapes(seed, count)
-    cfgs = [sidp.make_config(law="euler", p=p, nx=nel, ny=nel, precision="mixed", bc=("outflow",) * 4)
-            for nel, p in shapes]
+def _batch_rate(torch, sidp, stream, cfgs, states, steps, warmup):
+    """Create a batch, set the states (a function of (batch, i) or a list), time `steps` steps."""
     b = sidp.sidp_batch_create(cfgs, stream)
-    for i in range(count):
-        x, y = sidp.sidp_batch_node_coords(b, i)
-        sidp.sidp_batch_set_state(b, i, inputs.four_quadrant(x, y, seed * 100003 + i))
+    for i in range(len(cfgs)):
+        sidp.sidp_batch_set_state(b, i, states(b, i) if callable(states) else states[i])
     sidp.sidp_batch_set_stats(b, False)
     nodes = sidp.sidp_batch_total_nodes(b)
     sidp.sidp_batch_step(b, warmup)
@@ -391,7 +385,27 @@ def run_batched(torch, sidp, stream, steps, warmup, seed=0, count=512):
     sidp.sidp_batch_step(b, steps)
     e1.record(stream)
     e1.synchronize()
-    sec = e0.elapsed_time(e1) / 1e3
+    return b, nodes, e0.elapsed_time(e1) / 1e3
+
+
+def run_batched(torch, sidp, stream, steps, warmup, hbm, peak_kind, seed=0, count=512):
+    """Batched workload: `count` independent Euler problems, elements per side from {8,16,32,64}
+    and p from {2..7} (seeded), seeded four-quadrant data, mixed precision, outflow sides.  The
+    default launch structure (one launch per degree group, the groups on concurrent graph
+    branches) is timed, and beside it the single degree-switching launch per stage."""
+    from paper_2004_08503_gb300 import inputs
+    shapes = inputs.batch_shapes(seed, count)
+    cfgs = [sidp.make_config(law="euler", p=p, nx=nel, ny=nel, precision="mixed", bc=("outflow",) * 4)
+            for nel, p in shapes]
+    states = []
+
+    def initial(b, i):
+        x, y = sidp.sidp_batch_node_coords(b, i)
+        states.append(inputs.four_quadrant(x, y, seed * 100003 + i))
+        return states[-1]
+
+    prev = os.environ.pop("SIDP_BATCH_LAUNCH", None)
+    b, nodes, sec = _batch_rate(torch, sidp, stream, cfgs, initial, steps, warmup)
     sidp.sidp_batch_set_stats(b, True)
     sidp.sidp_batch_step(b, 2)
     worst = {"rho_min": 1e300, "p_min": 1e300, "max_bound_violation": 0.0, "max_entropy_violation": 0.0}
@@ -402,8 +416,22 @@ def run_batched(torch, sidp, stream, steps, warmup, seed=0, count=512):
         worst["max_bound_violation"] = max(worst["max_bound_violation"], d["max_bound_violation"])
         worst["max_entropy_violation"] = max(worst["max_entropy_violation"], d["max_entropy_violation"])
     sidp.sidp_batch_destroy(b)
+    os.environ["SIDP_BATCH_LAUNCH"] = "single"
+    bs, _, sec_single = _batch_rate(torch, sidp, stream, cfgs, states, steps, warmup)
+    sidp.sidp_batch_destroy(bs)
+    os.environ.pop("SIDP_BATCH_LAUNCH")
+    if prev is not None:
+        os.environ["SIDP_BATCH_LAUNCH"] = prev
+    # whole step on 3 nc s = 48 bytes per node and stage (state passes of the three stages and the
+    # time step, Euler float32)
+    gbs = 48.0 * nodes * 3 * steps / sec / 1e9
     return {"value": nodes * 3 * steps / sec, "unit": UNIT, "instances": count, "nodes": nodes, "steps": steps,
-            "ms_per_step": 1e3 * sec / steps, "launches_per_step": "4 per (p, tile) group + 1",
+            "ms_per_step": 1e3 * sec / steps, "launches_per_step": "4 per degree group + 1",
+            "single_launch": {"value": nodes * 3 * steps / sec_single, "unit": UNIT,
+                              "ms_per_step": 1e3 * sec_single / steps, "launches_per_step": 5,
+                              "note": "one degree-switching launch per stage (SIDP_BATCH_LAUNCH=single)"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                         "bytes_per_node_stage": 48, "scope": "whole graph-replayed step", "peak_kind": peak_kind},
             "invariants_sampled": worst, "workload": f"{count} Euler instances, elements per side in {{8,16,32,64}}, "
             f"p in {{2..7}} (seed {seed}), four-quadrant data, mixed precision, one CUDA graph per step, degree groups on concurrent graph branches"}
 
@@ -601,7 +629,7 @@ def main():
 
     batched = None
     if not args.no_batched:
-        batched = run_batched(torch, sidp, stream, steps=max(10, args.steps // 4), warmup=2)
+        batched = run_batched(torch, sidp, stream, max(10, args.steps // 4), 2, hbm, peak_kind)
     accuracy = None if args.no_accuracy else run_accuracy(sidp, stream)
     dmr = (run_dmr(sidp, args.dmr, args.dmr_t, args.dmr_image, max_seconds=args.dmr_max_seconds,
                    stats_from=args.dmr_stats_from) if args.dmr else None)

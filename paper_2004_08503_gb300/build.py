@@ -21,7 +21,8 @@ SOURCES = ["sidp_api.cu", "sidp_batch.cu", "sidp_tables.cpp", "sidp_geometry.cpp
            "inst_burgers_f64.cu", "inst_burgers_f32.cu", "inst_advection_f64.cu", "inst_advection_f32.cu",
            "inst_advection_var_f64.cu", "inst_advection_var_f32.cu",
            "inst_euler_f64_a.cu", "inst_euler_f64_b.cu", "inst_euler_f64_c.cu",
-           "inst_euler_f32_a.cu", "inst_euler_f32_b.cu", "inst_euler_f32_c.cu"]
+           "inst_euler_f32_a.cu", "inst_euler_f32_b.cu", "inst_euler_f32_c.cu",
+           "inst_batch_all_f32.cu", "inst_batch_all_f64.cu"]
 
 
 def _headers():

@@ -8,13 +8,16 @@
 //     dt launches (one per degree group) -> per-instance finalisation -> 3 x stage launches per group
 // and is captured once in a CUDA graph that later steps replay.
 //
-// Trade-off: one launch per degree group rather than one launch that switches on p inside: a
-// single kernel holding every degree's code path would carry the register and shared-memory
-// footprint of the largest degree for all tasks.  With the graph, the extra launches cost
-// little next to the per-stage work.
+// Trade-off: one launch per degree group (the groups on concurrent graph branches) rather than
+// one launch that switches on p inside.  Both exist: SIDP_BATCH_LAUNCH=single selects the single
+// degree-switching launch (k_batch_all: default tile shapes, tasks by decreasing degree, the
+// shared memory of the largest degree for every CTA, more register spills); on the 512-instance
+// benchmark mix it measured 15.7 against 16.5 G node-updates/s for the groups, which stay the
+// default.
 #include <cfloat>
 #include <cmath>
 #include <cstddef>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <new>
@@ -45,6 +48,10 @@ struct Group {
   int tile = 0;
   int2* d_tasks = nullptr;
   int ntasks = 0;
+  // the group's task tables for every tile shape (subcell limiting without the smoothness
+  // indicator: the batch autotuner chooses among them at the first step)
+  int2* d_tasks_t[kNumTiles] = {nullptr, nullptr, nullptr, nullptr};
+  int ntasks_t[kNumTiles] = {0, 0, 0, 0};
 };
 
 thread_local std::string g_batch_err;
@@ -72,6 +79,13 @@ struct sidp_batch {
   bool debug = false;
   long long total_nodes = 0;
   std::vector<Group> groups;
+  bool tuned = false;  // the per-group tile shapes have been chosen (or fixed)
+  // single-launch mode (subcell limiting without the smoothness indicator, statistics off): one
+  // launch per stage over the tiles of every degree, default tile shapes, tasks by decreasing degree
+  bool single = false;
+  int4* d_all_tasks = nullptr;
+  int n_all_tasks = 0;
+  void* d_tabs = nullptr;  // Tables<T>[kMaxP + 1]
   std::vector<cudaStream_t> gstream;  // one stream per degree group (the groups are independent)
   std::vector<cudaEvent_t> gdone;     // a group's work on its stream is done
   cudaEvent_t fork = nullptr;         // work so far on the batch stream is done
@@ -166,15 +180,19 @@ cudaError_t launch_batch_law(int p, int tile, const BatchLaunch<T>& bl, bool dt,
 }
 
 // k = 0: time-step launch; k = 1..3: SSP-RK3 stage k (Sec. 5), for degree group gi on stream st.
+// timed: the timed stage kernels whatever the statistics switch (the batch autotuner).
 template <typename T>
-cudaError_t launch_group(sidp_batch* b, int gi, int k, cudaStream_t st) {
+cudaError_t launch_group(sidp_batch* b, int gi, int k, cudaStream_t st, bool timed = false) {
   {
     const Group& gr = b->groups[gi];
+    // the statistics and general stage kernels exist in the default shape only: their launches take
+    // the group's default-shape task table
+    const bool default_shape = k > 0 && ((b->stats_on && !timed) || b->limiter != 2 || b->cfgs[0].smoothness);
     BatchLaunch<T> bl;
     std::memset(&bl, 0, sizeof(bl));
     bl.insts = static_cast<const Instance<T>*>(b->d_inst[k]);
-    bl.tasks = gr.d_tasks;
-    bl.ntasks = gr.ntasks;
+    bl.tasks = default_shape ? gr.d_tasks_t[0] : gr.d_tasks;
+    bl.ntasks = default_shape ? gr.ntasks_t[0] : gr.ntasks;
     double xi[kMaxN], w[kMaxN], D[kMaxN * kMaxN];
     gll_tables(gr.p, xi, w, D);
     const int nn = gr.p + 1;
@@ -192,14 +210,50 @@ cudaError_t launch_group(sidp_batch* b, int gi, int k, cudaStream_t st) {
     }
     bl.limiter = b->limiter;
     bl.bits = b->d_bits;
-    bl.stats = b->stats_on ? 1 : 0;
+    bl.stats = (b->stats_on && !timed) ? 1 : 0;
+    const int tile = default_shape ? 0 : gr.tile;
     switch (b->law) {
-      case LAW_BURGERS: return launch_batch_law<LAW_BURGERS, T>(gr.p, gr.tile, bl, k == 0, st);
-      case LAW_EULER: return launch_batch_law<LAW_EULER, T>(gr.p, gr.tile, bl, k == 0, st);
-      case LAW_ADVECTION_VAR: return launch_batch_law<LAW_ADVECTION_VAR, T>(gr.p, gr.tile, bl, k == 0, st);
-      default: return launch_batch_law<LAW_ADVECTION, T>(gr.p, gr.tile, bl, k == 0, st);
+      case LAW_BURGERS: return launch_batch_law<LAW_BURGERS, T>(gr.p, tile, bl, k == 0, st);
+      case LAW_EULER: return launch_batch_law<LAW_EULER, T>(gr.p, tile, bl, k == 0, st);
+      case LAW_ADVECTION_VAR: return launch_batch_law<LAW_ADVECTION_VAR, T>(gr.p, tile, bl, k == 0, st);
+      default: return launch_batch_law<LAW_ADVECTION, T>(gr.p, tile, bl, k == 0, st);
     }
   }
+}
+
+template <typename T>
+cudaError_t launch_all(sidp_batch* b, int k) {
+  BatchAllLaunch<T> bl;
+  std::memset(&bl, 0, sizeof(bl));
+  bl.insts = static_cast<const Instance<T>*>(b->d_inst[k]);
+  bl.tasks = b->d_all_tasks;
+  bl.ntasks = b->n_all_tasks;
+  bl.tabs = static_cast<const Tables<T>*>(b->d_tabs);
+  bl.lp = make_law_params<T>(b->cfgs[0].gamma, b->cfgs[0].adv_beta, b->cfgs[0].adv_grad);
+  bl.bits = b->d_bits;
+  switch (b->law) {
+    case LAW_BURGERS: return launch_batch_all<LAW_BURGERS, T>(bl, k == 0, b->stream);
+    case LAW_EULER: return launch_batch_all<LAW_EULER, T>(bl, k == 0, b->stream);
+    case LAW_ADVECTION_VAR: return launch_batch_all<LAW_ADVECTION_VAR, T>(bl, k == 0, b->stream);
+    default: return launch_batch_all<LAW_ADVECTION, T>(bl, k == 0, b->stream);
+  }
+}
+
+template <typename T>
+cudaError_t upload_tables(sidp_batch* b) {
+  std::vector<Tables<T>> tabs(kMaxP + 1);
+  std::memset(tabs.data(), 0, tabs.size() * sizeof(Tables<T>));
+  for (int p = 1; p <= kMaxP; ++p) {
+    double xi[kMaxN], w[kMaxN], D[kMaxN * kMaxN], Vinv[kMaxN * kMaxN], nrm[kMaxN];
+    gll_tables(p, xi, w, D);
+    modal_tables(p, Vinv, nrm);
+    const int nn = p + 1;
+    for (int i = 0; i < nn; ++i) { tabs[p].w[i] = T(w[i]); tabs[p].xi[i] = T(xi[i]); tabs[p].nrm[i] = T(nrm[i]); }
+    for (int i = 0; i < nn * nn; ++i) { tabs[p].D[i] = T(D[i]); tabs[p].Vinv[i] = T(Vinv[i]); }
+  }
+  cudaError_t e = cudaMalloc(&b->d_tabs, tabs.size() * sizeof(Tables<T>));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(b->d_tabs, tabs.data(), tabs.size() * sizeof(Tables<T>), cudaMemcpyHostToDevice);
 }
 
 // Launches k0..k1 of every degree group, each group on its own stream forked from the batch stream
@@ -221,11 +275,60 @@ cudaError_t run_groups(sidp_batch* b, int k0, int k1) {
 // One SSP-RK3 step of every instance: per-instance time steps (all groups), their finalize, then
 // the three stages (all groups).
 cudaError_t run_batch_step(sidp_batch* b) {
-  cudaError_t e = run_groups(b, 0, 0);
+  const bool single = b->single && !b->stats_on;
+  cudaError_t e = single ? (b->mixed ? launch_all<float>(b, 0) : launch_all<double>(b, 0)) : run_groups(b, 0, 0);
   if (e != cudaSuccess) return e;
   k_batch_finalize<<<(b->n + 127) / 128, 128, 0, b->stream>>>(b->d_bits, b->d_cfl, b->d_dt, b->d_dtf, b->d_clock, b->n);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return run_groups(b, 1, 3);
+  if (!single) return run_groups(b, 1, 3);
+  for (int k = 1; k <= 3 && e == cudaSuccess; ++k) e = b->mixed ? launch_all<float>(b, k) : launch_all<double>(b, k);
+  return e;
+}
+
+// Batch autotuner: with valid time steps in place (one time-step pass; the clocks are restored
+// afterwards), time stage 1 of each degree group with each tile shape and keep the fastest.
+// Stage 1 writes only u^(1), so the state is untouched.  The groups are tuned one after another
+// on the batch stream.
+cudaError_t tune_batch(sidp_batch* b) {
+  std::vector<double> clock(b->n);
+  cudaError_t e = cudaMemcpy(clock.data(), b->d_clock, b->n * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return e;
+  if ((e = run_groups(b, 0, 0)) != cudaSuccess) return e;
+  k_batch_finalize<<<(b->n + 127) / 128, 128, 0, b->stream>>>(b->d_bits, b->d_cfl, b->d_dt, b->d_dtf, b->d_clock, b->n);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return e; }
+  for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
+    Group& g = b->groups[gi];
+    float best = 1e30f;
+    int best_t = g.tile;
+    for (int t = 0; t < kNumTiles && e == cudaSuccess; ++t) {
+      g.tile = t;
+      g.d_tasks = g.d_tasks_t[t];
+      g.ntasks = g.ntasks_t[t];
+      auto launch = [&]() {
+        return b->mixed ? launch_group<float>(b, (int)gi, 1, b->stream, true)
+                        : launch_group<double>(b, (int)gi, 1, b->stream, true);
+      };
+      if ((e = launch()) != cudaSuccess) break;  // warm-up (and kernel attributes)
+      cudaEventRecord(e0, b->stream);
+      for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch();
+      cudaEventRecord(e1, b->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best) { best = ms; best_t = t; }
+    }
+    g.tile = best_t;
+    g.d_tasks = g.d_tasks_t[best_t];
+    g.ntasks = g.ntasks_t[best_t];
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_clock, clock.data(), b->n * sizeof(double), cudaMemcpyHostToDevice);
+  return e;
 }
 
 }  // namespace
@@ -267,28 +370,29 @@ sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int cou
   b->N.resize(count);
   b->off.resize(count);
   long long tot = 0;
-  // one tile shape per degree: the autotuned one when the tuner has run for this (law, p,
-  // precision), else the default (fitting the shape to each mesh to cut padding measured slower:
-  // more, smaller launches)
-  // (the stage kernels of other limiters and of the smoothness indicator exist for the default
-  // shape only, and a group's task table is built for its shape)
+  // one tile shape per degree, the starting point of the batch autotuner: the single-instance
+  // tuner's choice when it has run for this (law, p, precision), else the default (fitting the
+  // shape to each mesh to cut padding measured slower: more, smaller launches).  The stage kernels
+  // of other limiters, of the smoothness indicator and of the statistics exist for the default
+  // shape only; every group keeps a task table for that shape.
   const bool any_shape = cfgs[0].limiter == 2 && !cfgs[0].smoothness;
   int ptile[kMaxP + 1];
   for (int p = 1; p <= kMaxP; ++p) {
     ptile[p] = any_shape ? tuned_tile(cfgs[0].law, p, cfgs[0].precision == SIDP_MIXED ? 1 : 0) : 0;
     if (ptile[p] < 0) ptile[p] = 0;
   }
-  std::map<std::pair<int, int>, std::vector<int2>> tasks;  // (p, tile) -> tasks
+  std::map<int, std::vector<int2>> tasks[kNumTiles];  // per tile shape: p -> tasks
   for (int i = 0; i < count; ++i) {
     const sidp_config& c = cfgs[i];
     const int nn = (c.p + 1) * (c.p + 1);
     b->N[i] = (long long)c.nx * c.ny * nn;
     b->off[i] = tot;
     tot += b->nc * b->N[i];
-    const int tile = ptile[c.p];
-    const TileShape ts = kTiles[c.p][tile];
-    const long long ntiles = (long long)((c.nx + ts.tx - 1) / ts.tx) * ((c.ny + ts.ty - 1) / ts.ty);
-    for (long long t = 0; t < ntiles; ++t) tasks[{c.p, tile}].push_back(make_int2(i, (int)t));
+    for (int tile = 0; tile < (any_shape ? kNumTiles : 1); ++tile) {
+      const TileShape ts = kTiles[c.p][tile];
+      const long long ntiles = (long long)((c.nx + ts.tx - 1) / ts.tx) * ((c.ny + ts.ty - 1) / ts.ty);
+      for (long long t = 0; t < ntiles; ++t) tasks[tile][c.p].push_back(make_int2(i, (int)t));
+    }
   }
   b->total_vals = tot;
   b->total_nodes = tot / b->nc;
@@ -319,14 +423,45 @@ sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int cou
       (e = cudaMemset(b->d_u[0], 0, tot * b->esize)) != cudaSuccess)
     return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
   if ((e = b->mixed ? build_tables<float>(b) : build_tables<double>(b)) != cudaSuccess) return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
-  for (auto& kv : tasks) {
+  for (auto& kv : tasks[0]) {
     Group g;
-    g.p = kv.first.first;
-    g.tile = kv.first.second;
-    g.ntasks = (int)kv.second.size();
-    if (cudaMalloc(&g.d_tasks, sizeof(int2) * g.ntasks) != cudaSuccess) return bail(SIDP_ERR_OOM, "task table allocation failed");
+    g.p = kv.first;
     b->groups.push_back(g);
-    if ((e = cudaMemcpy(g.d_tasks, kv.second.data(), sizeof(int2) * g.ntasks, cudaMemcpyHostToDevice)) != cudaSuccess)
+    Group& gr = b->groups.back();
+    for (int tile = 0; tile < (any_shape ? kNumTiles : 1); ++tile) {
+      const std::vector<int2>& v = tasks[tile][g.p];
+      gr.ntasks_t[tile] = (int)v.size();
+      if (cudaMalloc(&gr.d_tasks_t[tile], sizeof(int2) * v.size()) != cudaSuccess)
+        return bail(SIDP_ERR_OOM, "task table allocation failed");
+      if ((e = cudaMemcpy(gr.d_tasks_t[tile], v.data(), sizeof(int2) * v.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
+    }
+    gr.tile = ptile[g.p];
+    gr.d_tasks = gr.d_tasks_t[gr.tile];
+    gr.ntasks = gr.ntasks_t[gr.tile];
+  }
+  // the batch autotuner runs at the first step unless a shape is forced or the table knows them
+  b->tuned = !any_shape || std::getenv("SIDP_TILE") != nullptr ||
+             (std::getenv("SIDP_AUTOTUNE") && std::getenv("SIDP_AUTOTUNE")[0] == '0');
+  {  // SIDP_BATCH_LAUNCH=single: one launch per stage over every degree (measured slower than the
+     // concurrent degree groups on the benchmark mix, so not the default)
+    const char* mode = std::getenv("SIDP_BATCH_LAUNCH");
+    b->single = any_shape && mode && std::string(mode) == "single";
+  }
+  if (b->single) {
+    std::vector<int4> all;
+    for (int p = kMaxP; p >= 1; --p)
+      for (int i = 0; i < count; ++i) {
+        if (cfgs[i].p != p) continue;
+        const TileShape ts = kTiles[p][0];
+        const long long ntiles = (long long)((cfgs[i].nx + ts.tx - 1) / ts.tx) * ((cfgs[i].ny + ts.ty - 1) / ts.ty);
+        for (long long t = 0; t < ntiles; ++t) all.push_back(make_int4(i, (int)t, p, 0));
+      }
+    b->n_all_tasks = (int)all.size();
+    if (cudaMalloc(&b->d_all_tasks, sizeof(int4) * all.size()) != cudaSuccess) return bail(SIDP_ERR_OOM, "task table allocation failed");
+    if ((e = cudaMemcpy(b->d_all_tasks, all.data(), sizeof(int4) * all.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+      return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
+    if ((e = b->mixed ? upload_tables<float>(b) : upload_tables<double>(b)) != cudaSuccess)
       return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
   }
   if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess) return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
@@ -352,7 +487,10 @@ sidp_status sidp_batch_destroy(sidp_batch* b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
   for (int k = 0; k < 3; ++k) cudaFree(b->d_u[k]);
   for (int k = 0; k < 4; ++k) cudaFree(b->d_inst[k]);
-  for (auto& g : b->groups) cudaFree(g.d_tasks);
+  for (auto& g : b->groups)
+    for (int t = 0; t < kNumTiles; ++t) cudaFree(g.d_tasks_t[t]);
+  cudaFree(b->d_all_tasks);
+  cudaFree(b->d_tabs);
   cudaFree(b->d_dt);
   cudaFree(b->d_dtf);
   cudaFree(b->d_clock);
@@ -468,7 +606,8 @@ sidp_status sidp_batch_stage(sidp_batch* b, int k, const double* dt) try {
   BCUDA(b, cudaStreamSynchronize(b->stream));
   BCUDA(b, cudaMemcpy(b->d_dt, dt, b->n * sizeof(double), cudaMemcpyHostToDevice));
   BCUDA(b, cudaMemcpy(b->d_dtf, dtf.data(), b->n * sizeof(float), cudaMemcpyHostToDevice));
-  BCUDA(b, run_groups(b, k, k));
+  if (b->single && !b->stats_on) BCUDA(b, b->mixed ? launch_all<float>(b, k) : launch_all<double>(b, k));
+  else BCUDA(b, run_groups(b, k, k));
   BCUDA(b, cudaStreamSynchronize(b->stream));
   return SIDP_OK;
 } catch (const std::bad_alloc&) {
@@ -506,6 +645,10 @@ sidp_status sidp_batch_get_bounds(sidp_batch* b, int i, double* lo, double* hi, 
 
 sidp_status sidp_batch_step(sidp_batch* b, int nsteps) {
   if (!b || nsteps < 0) return bfail(b, SIDP_ERR_ARG, "bad argument");
+  if (!b->tuned && nsteps > 0 && !(b->single && !b->stats_on)) {
+    BCUDA(b, tune_batch(b));
+    b->tuned = true;
+  }
   int done = 0;
   if (!b->warm && nsteps > 0) {  // first step eagerly: kernel attributes are set outside capture
     BCUDA(b, run_batch_step(b));

@@ -151,6 +151,21 @@ struct BatchLaunch {
   unsigned long long* bits;  // per-instance time-step accumulators (dt launches)
 };
 
+// A launch over every degree group at once (the single-launch batch mode): CTA i runs
+// tasks[i] = (instance, linear tile index, degree p, 0) with the default tile shape of p; the
+// reference tables of degree p are tabs[p] (device array, entries 1..kMaxP).  Subcell limiting
+// without the smoothness indicator only.
+template <typename T>
+struct BatchAllLaunch {
+  const Instance<T>* insts;
+  const int4* tasks;
+  int ntasks;
+  const Tables<T>* tabs;
+  LawParamsT<T> lp;
+  SmoothnessT<T> si;         // off
+  unsigned long long* bits;  // per-instance time-step accumulators (time-step launch)
+};
+
 template <typename T>
 struct StageLaunch {
   Instance<T> inst;
@@ -210,6 +225,21 @@ SIDP_DECLARE(LAW_ADVECTION_VAR, double)
 SIDP_DECLARE(LAW_ADVECTION_VAR, float)
 #undef SIDP_DECLARE
 #undef SIDP_DECLARE_P
+// The single-launch batch kernels of one law and precision (inst_batch_all_*.cu) and their
+// shared-memory size.
+template <int LAW, typename T>
+cudaError_t launch_batch_all(const BatchAllLaunch<T>& b, bool dt, cudaStream_t s);
+#define SIDP_DECLARE_ALL(LAWID, TT) \
+  template <> cudaError_t launch_batch_all<LAWID, TT>(const BatchAllLaunch<TT>&, bool, cudaStream_t);
+SIDP_DECLARE_ALL(LAW_BURGERS, double)
+SIDP_DECLARE_ALL(LAW_BURGERS, float)
+SIDP_DECLARE_ALL(LAW_EULER, double)
+SIDP_DECLARE_ALL(LAW_EULER, float)
+SIDP_DECLARE_ALL(LAW_ADVECTION, double)
+SIDP_DECLARE_ALL(LAW_ADVECTION, float)
+SIDP_DECLARE_ALL(LAW_ADVECTION_VAR, double)
+SIDP_DECLARE_ALL(LAW_ADVECTION_VAR, float)
+#undef SIDP_DECLARE_ALL
 
 // Instantiate launch_p for one law/precision/degree (used by the inst_*.cu files).
 #define SIDP_INSTANTIATE_P(LAWID, LAWTPL, TT, P)                                                       \

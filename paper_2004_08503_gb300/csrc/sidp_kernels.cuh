@@ -1151,6 +1151,81 @@ k_dt_batch(const BatchLaunch<T> B) {
   dt_body<P, TX, TY, LAW, T>(s, sI, B.tab, B.lp, tile_x, tile_y, B.bits + task.x);
 }
 
+// ---------------------------------------------------------------- single-launch batches
+// One launch over the tiles of every instance of a batch, whatever their degree: each CTA switches
+// on its task's degree into the stage (or time-step) body of that degree with its default tile
+// shape.  Every default shape has at most 256 nodes, so one block size and one register budget
+// (64 registers, 4 CTAs per SM) serve all degrees; the dynamic shared memory is the largest
+// degree's.  Tasks are ordered by decreasing degree (the costliest tiles first).
+template <int P>
+struct DefaultTile {
+  static constexpr int TX = kTiles[P][0].tx, TY = kTiles[P][0].ty;
+  static_assert(TileGeom<P, TX, TY>::THREADS == 256, "single-launch batches need 256-thread default tiles");
+};
+
+template <int P, class LAW, typename T, bool DT>
+__device__ __forceinline__ void batch_all_body(unsigned char* smem_raw, const Instance<T>& I, const BatchAllLaunch<T>& B,
+                                               int tile, int inst) {
+  constexpr int TX = DefaultTile<P>::TX, TY = DefaultTile<P>::TY;
+  const int tiles_x = (I.nx + TX - 1) / TX;
+  const int tile_y = tile / tiles_x, tile_x = tile - tile_y * tiles_x;
+  if constexpr (DT) {
+    dt_body<P, TX, TY, LAW, T>(*reinterpret_cast<DtSmem<P, TX, TY, LAW, T>*>(smem_raw), I, B.tabs[P], B.lp, tile_x, tile_y,
+                               B.bits + inst);
+  } else {
+    stage_body<P, TX, TY, LAW, T, false, false, false, true>(*reinterpret_cast<TileSmem<P, TX, TY, LAW, T>*>(smem_raw), I,
+                                                             B.tabs[P], B.lp, 2, B.si, tile_x, tile_y);
+  }
+}
+
+template <class LAW, typename T, bool DT>
+__global__ void __launch_bounds__(256, 4) k_batch_all(const BatchAllLaunch<T> B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Instance<T> sI;
+  const int4 task = B.tasks[blockIdx.x];
+  load_instance(sI, B.insts + task.x);
+  switch (task.z) {
+    case 1: batch_all_body<1, LAW, T, DT>(smem_raw, sI, B, task.y, task.x); break;
+    case 2: batch_all_body<2, LAW, T, DT>(smem_raw, sI, B, task.y, task.x); break;
+    case 3: batch_all_body<3, LAW, T, DT>(smem_raw, sI, B, task.y, task.x); break;
+    case 4: batch_all_body<4, LAW, T, DT>(smem_raw, sI, B, task.y, task.x); break;
+    case 5: batch_all_body<5, LAW, T, DT>(smem_raw, sI, B, task.y, task.x); break;
+    case 6: batch_all_body<6, LAW, T, DT>(smem_raw, sI, B, task.y, task.x); break;
+    default: batch_all_body<7, LAW, T, DT>(smem_raw, sI, B, task.y, task.x); break;
+  }
+}
+
+template <class LAW, typename T, bool DT>
+constexpr size_t batch_all_smem() {
+  size_t m = 0;
+#define SIDP_SMEM_P(P)                                                                                       \
+  {                                                                                                          \
+    const size_t v = DT ? sizeof(DtSmem<P, DefaultTile<P>::TX, DefaultTile<P>::TY, LAW, T>)                  \
+                        : sizeof(TileSmem<P, DefaultTile<P>::TX, DefaultTile<P>::TY, LAW, T>);               \
+    m = v > m ? v : m;                                                                                       \
+  }
+  SIDP_SMEM_P(1) SIDP_SMEM_P(2) SIDP_SMEM_P(3) SIDP_SMEM_P(4) SIDP_SMEM_P(5) SIDP_SMEM_P(6) SIDP_SMEM_P(7)
+#undef SIDP_SMEM_P
+  return m;
+}
+
+template <class LAW, typename T>
+cudaError_t launch_batch_all_law(const BatchAllLaunch<T>& B, bool dt, cudaStream_t s) {
+  constexpr size_t smem = batch_all_smem<LAW, T, false>(), smem_dt = batch_all_smem<LAW, T, true>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t err = cudaFuncSetAttribute(k_batch_all<LAW, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(k_batch_all<LAW, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_dt);
+    if (err != cudaSuccess) return err;
+    attr_set = true;
+  }
+  if (B.ntasks <= 0) return cudaSuccess;
+  if (dt) k_batch_all<LAW, T, true><<<(unsigned)B.ntasks, 256, smem_dt, s>>>(B);
+  else k_batch_all<LAW, T, false><<<(unsigned)B.ntasks, 256, smem, s>>>(B);
+  return cudaGetLastError();
+}
+
 template <int P, int TX, int TY, class LAW, typename T, bool ELW = false, bool DENSE = false, bool STATS = false,
           bool SUBCELL = false>
 cudaError_t launch_tile(const StageLaunch<T>& a, unsigned long long* dt_bits, cudaStream_t s) {
