@@ -35,9 +35,9 @@ sys.path.insert(0, ROOT)
 METRIC = "node-updates/s per RK stage (Euler 2D p=3), mixed vs FP64; % HBM roofline"
 UNIT = "node-updates/s"
 # dram__bytes (read + write) per node and stage launch, averaged over the three stages, measured by
-# ncu on the 768x768 p=3 blast (two steps in, stages 1-3 with the tile shape 2x8).  The counters
-# belong to the stage kernel as it was captured; a changed kernel needs a new capture.
-STAGE_DRAM_BYTES_PER_NODE = 39.2
+# ncu on the 768x768 p=3 blast (the second step's stages 1-3 with the tile shape 2x8).  The
+# counters belong to the stage kernel as it was captured; a changed kernel needs a new capture.
+STAGE_DRAM_BYTES_PER_NODE = 39.3
 # Executed FP32 flops (2 x FFMA + FADD + FMUL) and warp instructions per node of stages 1, 2, 3
 # from the same capture: the two other ceilings of the stage kernel, reported beside the HBM
 # roofline.
@@ -45,7 +45,7 @@ STAGE_FP32_FLOP_PER_NODE = (363.9, 371.9, 371.9)
 STAGE_WARP_INSTR_PER_NODE = (27.2, 27.2, 27.2)
 # The float64 stage kernel's executed FP64 flops per node (2 x DFMA + DADD + DMUL), stages 1-3,
 # from an ncu capture of the same workload in float64: its FP64-pipe roofline.
-FP64_STAGE_FLOP_PER_NODE = (1197.7, 1196.9, 1197.6)
+FP64_STAGE_FLOP_PER_NODE = (1198.0, 1197.6, 1197.8)
 SMS, SCHEDULERS_PER_SM = 152, 4
 # The curved-mesh stage kernel's DRAM traffic per node and launch (stages 1-3 averaged), from one
 # ncu capture of the 768x768 curved leg.  The kernel has changed since (the smoothness-indicator block, off in this workload), so the figure is not
