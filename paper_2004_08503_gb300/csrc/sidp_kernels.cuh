@@ -172,8 +172,17 @@ __device__ __forceinline__ void neighbor_trace(const Instance<T>& I, int side, i
 template <class L, class = void> struct HasPosition { static constexpr bool value = false; };
 template <class L> struct HasPosition<L, decltype(void(L::kPosition))> { static constexpr bool value = L::kPosition; };
 
+// The quantities of a thread's own node slot, kept in registers from phase A to phase B.
+template <class LAW, typename T>
+struct NodeRec {
+  Vec<T, LAW::NC> u, fx, fy;
+  typename LAW::Aux ax;
+  T sig;
+};
+
 template <class LAW, bool LEAN, typename T, class S>
-__device__ __forceinline__ void fill_slot(S& s, int slot, const T* uu, T x, T y, const LawParamsT<T>& lp) {
+__device__ __forceinline__ void fill_slot(S& s, int slot, const T* uu, T x, T y, const LawParamsT<T>& lp,
+                                          NodeRec<LAW, T>* rec = nullptr) {
   constexpr int NC = LAW::NC;
   typename LAW::Aux ax;
   if constexpr (HasPosition<LAW>::value) LAW::aux_at(uu, x, y, ax, lp);
@@ -189,7 +198,9 @@ __device__ __forceinline__ void fill_slot(S& s, int slot, const T* uu, T x, T y,
     LAW::flux(uu, ax, 1, vy.v, lp);
     s.fx[slot] = vx;
     s.fy[slot] = vy;
-    if constexpr (LAW::kEntropy) s.sig[slot] = LAW::sigma(uu, ax, lp);
+    T sg = T(0);
+    if constexpr (LAW::kEntropy) { sg = LAW::sigma(uu, ax, lp); s.sig[slot] = sg; }
+    if (rec) { rec->u = vu; rec->fx = vx; rec->fy = vy; rec->ax = ax; rec->sig = sg; }
   }
 }
 
@@ -226,7 +237,8 @@ __device__ __forceinline__ void halo_load(const Instance<T>& I, const Tables<T>&
 
 template <int P, int TX, int TY, class LAW, bool LEAN, typename T, class S>
 __device__ __forceinline__ bool load_tile(S& s, const Instance<T>& I, const Tables<T>& tab, const LawParamsT<T>& lp,
-                                          int tile_x, int tile_y, int& le, int& a, int& b, long long& g) {
+                                          int tile_x, int tile_y, int& le, int& a, int& b, long long& g,
+                                          NodeRec<LAW, T>* rec = nullptr) {
   using G = TileGeom<P, TX, TY>;
   constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
   const int t = threadIdx.x;
@@ -263,7 +275,7 @@ __device__ __forceinline__ bool load_tile(S& s, const Instance<T>& I, const Tabl
     // global-load latencies overlap instead of adding up on the threads that own halo slots
     T uh[NC], hx = T(0), hy = T(0);
     if (t < G::NH) halo_load<P, TX, TY, NC>(I, tab, t, ex0, ey0, hh, uh, hx, hy);
-    fill_slot<LAW, LEAN>(s, t, uu, px, py, lp);
+    fill_slot<LAW, LEAN>(s, t, uu, px, py, lp, rec);
     if (t < G::NH) fill_slot<LAW, LEAN>(s, G::NT + t, uh, hx, hy, lp);
   }
   for (int h = (t < G::NT) ? t + G::THREADS : t; h < G::NH; h += G::THREADS) {
@@ -707,7 +719,8 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
   // ---------------- A
   int le, a, b;
   long long g;
-  const bool act = load_tile<P, TX, TY, LAW, false>(s, I, tab, lp, tile_x, tile_y, le, a, b, g);
+  NodeRec<LAW, T> own;
+  const bool act = load_tile<P, TX, TY, LAW, false>(s, I, tab, lp, tile_x, tile_y, le, a, b, g, &own);
   __syncthreads();
 
   // ---------------- B: every face once.  Each node slot's thread evaluates the x face on its left
@@ -715,11 +728,9 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
   // and north edges of the tile follow in one extra pass.
   if (t < G::NT) {
     const int row = (le / TX) * n + a, col = (le % TX) * n + b;
-    const V uR = s.u[t];
-    const typename LAW::Aux aR = s.aux[t];
-    const T sR = LAW::kEntropy ? s.sig[t] : T(0);
-    face_eval_r<LAW>(s, 0, Nbr<P, TX, TY>::left(t, b, row, col), uR, s.fx[t], aR, sR, t, lp);
-    face_eval_r<LAW>(s, 1, Nbr<P, TX, TY>::down(t, a, row, col), uR, s.fy[t], aR, sR, t, lp);
+    // the node's own quantities are still in registers from phase A
+    face_eval_r<LAW>(s, 0, Nbr<P, TX, TY>::left(t, b, row, col), own.u, own.fx, own.ax, own.sig, t, lp);
+    face_eval_r<LAW>(s, 1, Nbr<P, TX, TY>::down(t, a, row, col), own.u, own.fy, own.ax, own.sig, t, lp);
   }
   for (int e2 = t; e2 < G::NY + G::NX; e2 += G::THREADS) {
     if (e2 < G::NY) {  // east edge: slot (row, NX-1) | halo E
