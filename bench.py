@@ -230,6 +230,9 @@ def run_curved(torch, sidp, stream, steps, warmup, hbm, peak_kind):
     sec, _ = time_steps(torch, sv, stream, steps, warmup)
     value = nodes * 3 * steps / sec
     kt = stage_kernel_times(torch, sv, stream, reps=10)
+    # untimed: three steps with the statistics variant of the curved stage kernel
+    sv.set_stats(True)
+    sv.step(3)
     d = sv.diag()
     sv.close()
     # algorithmic bytes per node and launch: state (u_in, u_out; u^n in stages 2-3) plus the
@@ -246,7 +249,9 @@ def run_curved(torch, sidp, stream, steps, warmup, hbm, peak_kind):
                          "traffic": CURVED_DRAM_BYTES_PER_NODE * nodes if CURVED_TRAFFIC_CURRENT else None,
                          "kernel": "k_stage_curved<3, LawEuler<float>, float>",
                          "bytes_per_node": per_node, "peak_kind": peak_kind},
-            "invariants": {"rho_min": d["rho_min"], "p_min": d["p_min"], "nonfinite": d["nonfinite"]}}
+            "invariants": {k: d[k] for k in ("rho_min", "p_min", "nonfinite", "max_bound_violation",
+                                             "max_entropy_violation", "rootfind_max_iters", "rootfind_cap_hits",
+                                             "bound_nudges")}}
 
 
 def _oracle_strip(args):

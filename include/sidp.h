@@ -182,7 +182,8 @@ sidp_status sidp_set_time(sidp_ctx* ctx, double t);
 
 /* Metric arrays of the curved mesh whose nodes sit at (x[g], y[g]), float64 [N] each in library
  * node order (the two elements of a face give its nodes the same coordinates; across a periodic
- * side they differ by the period).  bc: the four side conditions, periodic or outflow.  Computed
+ * side they differ by the period).  bc: the four side conditions, periodic, outflow or slip wall
+ * (a wall face, like an outflow face, takes the element's own row as its normal).  Computed
  * on the host in float64; needs no GPU.  out: float64 [SIDP_GEO_FIELDS][N], caller-owned:
  *   0-1 row 1 of G J^-1 = (y_eta, -x_eta);  2-3 row 2 = (-y_xi, x_xi)
  *       (reference derivatives of the interpolated map, xi along b, eta along a);
@@ -200,9 +201,11 @@ sidp_status sidp_curved_metrics(int p, int nx, int ny, const int* bc, const doub
  * stage precision; from then on the time step and the stages use the curved-mesh kernels and
  * sidp_node_coords returns these coordinates.  Supported: laws burgers, advection and euler;
  * limiters none, lo, subcell and elementwise, with or without the smoothness indicator (on the
- * reference element); periodic and outflow sides; not the unsparsified mode (SIDP_ERR_ARG).  The per-stage violation statistics are not
- * collected on curved meshes (sidp_get_diag reports them as 0; mass and extrema use m_i).
- * Synchronous. */
+ * reference element); periodic, outflow and (Euler) slip-wall sides, a wall ghost being the
+ * trace with its momentum reflected about the face's unit normal, m - 2 (m . n) n (Sec. 5.7 on
+ * mapped faces); not the unsparsified mode (SIDP_ERR_ARG).  The per-stage violation statistics
+ * are collected as on Cartesian meshes, by a statistics variant of the curved stage kernel
+ * launched while they are on; mass and extrema use m_i.  Synchronous. */
 sidp_status sidp_set_geometry(sidp_ctx* ctx, const double* x, const double* y);
 
 /* Lend the device buffer of u^n: *dptr = device pointer of [nc][N] values of type *dtype

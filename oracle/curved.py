@@ -31,7 +31,12 @@ its own map T_K: the caller gives the physical coordinates (X, Y) of every Gauss
     Jacobian does not weight them), so s_K measures the polynomial on the reference square.
 
 Boundaries: periodic (the mapped mesh must then be periodic: coordinates across a periodic
-side differ by the period) and outflow.
+side differ by the period), outflow, and slip walls for the Euler equations (Sec. 5.7):
+    reading: the ghost state is the mirror image of the interior trace across the face, the
+    momentum reflected about the face's unit normal, m - 2 (m . n) n (n the face node's normal,
+    the row of G J^-1 normal to the face); on a Cartesian face this negates the normal
+    component, as on Cartesian meshes.  Density and energy are unchanged, so no mass or energy
+    crosses the wall.
 """
 import numpy as np
 
@@ -48,8 +53,10 @@ class CurvedProblem(Problem):
     def __init__(self, law, p, nx, ny, X, Y, bc=("periodic",) * 4, cfl=0.5, limiter="subcell", correct=True,
                  smoothness=None):
         for s in bc:
-            if s not in ("periodic", "outflow"):
-                raise ValueError("curved meshes take periodic or outflow boundaries")
+            if s not in ("periodic", "outflow", "wall"):
+                raise ValueError("curved meshes take periodic, outflow or slip-wall boundaries")
+            if s == "wall" and law.name != "euler":
+                raise ValueError("slip walls are defined for the Euler equations")
         if law.name == "advection_var":
             raise ValueError("variable-velocity advection is defined on Cartesian meshes")
         # reference operators and pair structure of a unit Cartesian mesh (h = 1)
@@ -138,6 +145,23 @@ class CurvedProblem(Problem):
             sol = rhs @ Apinv.T
             C[0, j], C[1, j] = sol[:, :NN], sol[:, NN:]
         return self.R1 + C[0], self.R2 + C[1], C
+
+    def neighbor_trace(self, U, side, elems):
+        """u^+ at the face nodes of `side`: as on Cartesian meshes, except that a slip wall mirrors
+        the interior trace across the face's own normal (the module's reading)."""
+        out = super().neighbor_trace(U, side, elems)
+        if self.bc[side] != "wall":
+            return out
+        nbe, shared = self._neighbour(side)
+        wall = ~shared[elems]
+        own = U[:, elems][:, :, self.fnodes[side]]
+        nv = self.nface[side][:, elems]
+        nh = nv / np.sqrt(nv[0] ** 2 + nv[1] ** 2)[None]
+        mn = own[1] * nh[0] + own[2] * nh[1]
+        ghost = own.copy()
+        ghost[1] = own[1] - 2.0 * mn * nh[0]
+        ghost[2] = own[2] - 2.0 * mn * nh[1]
+        return np.where(wall[None, :, None], ghost, out)
 
     # ------------------------------------------------------------------ residuals
     def _face_data(self, U, s, elems):

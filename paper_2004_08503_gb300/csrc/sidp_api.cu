@@ -668,8 +668,8 @@ sidp_status sidp_set_geometry(sidp_ctx* c, const double* x, const double* y) try
   if (f.unsparsified)
     return fail(c, SIDP_ERR_ARG, "curved meshes take no unsparsified mode");
   for (int k = 0; k < 4; ++k)
-    if (f.bc[k] != SIDP_BC_PERIODIC && f.bc[k] != SIDP_BC_OUTFLOW)
-      return fail(c, SIDP_ERR_ARG, "curved meshes take periodic or outflow sides");
+    if (f.bc[k] != SIDP_BC_PERIODIC && f.bc[k] != SIDP_BC_OUTFLOW && f.bc[k] != SIDP_BC_SLIP_WALL)
+      return fail(c, SIDP_ERR_ARG, "curved meshes take periodic, outflow or slip-wall sides");
   std::vector<double> geo((size_t)kGeoFields * c->N);
   std::string msg;
   const sidp_status st = curved_metrics(f.p, f.nx, f.ny, f.bc, x, y, geo.data(), msg);

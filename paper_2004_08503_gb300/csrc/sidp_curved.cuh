@@ -48,6 +48,18 @@ struct CurvedGeom {
 // spills); the float64 ones need more registers than 2 CTAs allow without spilling.
 template <typename T> struct CurvedMinBlocks { static constexpr int value = sizeof(T) == 4 ? 4 : 1; };
 
+// One element face as seen from one of its nodes: the face flux, the node's own F . n (the
+// high-order face term), the bar state of the limited field, sigma of the neighbour's trace,
+// lambda |n| (time step) and |u| of the neighbour's trace (operand scale of the face).  dir 0:
+// x face (b = 0 or p), dir 1: y face (a = 0 or p).
+template <int P, class LAW, typename T>
+struct CurvedFace {
+  T Fh[LAW::NC];   // flux in +xi (+eta)
+  T Fn[LAW::NC];   // own F . n
+  T bar, sig, ln;
+  T um;
+};
+
 template <int P, class LAW, typename T>
 struct CurvedSmem {
   static constexpr int NC = LAW::NC, TH = CurvedGeom<P>::THREADS;
@@ -64,6 +76,7 @@ struct CurvedSmem {
   T alpha[TH];
   T aK[CurvedGeom<P>::EPB];   // elementwise limiting: alpha_K per element
   T eps[CurvedGeom<P>::EPB];  // smoothness indicator: epsilon_K per element
+  CurvedFace<P, LAW, T> cy[CurvedGeom<P>::EPB][4];  // the corners' y faces, evaluated by interior nodes
 };
 
 // Element-face neighbour of node (a, b) of element e on side s (0 W, 1 E, 2 S, 3 N): the global
@@ -81,14 +94,93 @@ __device__ __forceinline__ long long curved_nbr(const int* bc, int nx, int ny, l
   return ((long long)ey * nx + ex) * NN + na * n + nb;
 }
 
-// Lax-Friedrichs flux across an element face with scaled normal nv (pointing from L to R):
-// 1/2 (F_L + F_R) . nv - 1/2 lambda |nv| (u_R - u_L); also the limited field's bar state and
-// lambda |nv|.
-template <class LAW, typename T>
-__device__ __forceinline__ void curved_face(const T* uL, const typename LAW::Aux& aL, const T* uR,
-                                            const typename LAW::Aux& aR, T nvx, T nvy, const LawParamsT<T>& lp,
-                                            T* Fh, T& bar0, T& ln) {
-  constexpr int NC = LAW::NC;
+// Element-face work of a thread.  An element has 4 (p+1) (node, direction) face evaluations: one
+// for each edge node and two for each corner.  Each edge node and each corner's x face is
+// evaluated by the node itself, each corner's y face by one of the first four interior nodes
+// (p >= 3; for p < 3, where there are too few, by the corner in a second pass).  Every thread
+// then runs one evaluation of the same code (no branch per direction or side), and its loads
+// of the neighbour's trace and of the face normal are issued with the node's own loads.
+template <int P>
+struct FaceItem {
+  int a, b, dir, side;
+  int corner;  // an interior node's corner (0..3: (0,0), (0,p), (p,0), (p,p)), else -1
+  bool on;
+};
+
+template <int P>
+__device__ __forceinline__ FaceItem<P> face_item(int a, int b, bool act) {
+  FaceItem<P> it{a, b, 0, 0, -1, act};
+  if (b == 0 || b == P) {
+    it.dir = 0;
+  } else if (a == 0 || a == P) {
+    it.dir = 1;
+  } else {
+    const int k = (a - 1) * (P - 1) + (b - 1);
+    if (k < 4) {
+      it.a = (k >> 1) ? P : 0;
+      it.b = (k & 1) ? P : 0;
+      it.dir = 1;
+      it.corner = k;
+    } else {
+      it.on = false;
+    }
+  }
+  it.side = 2 * it.dir + (((it.dir == 0) ? it.b : it.a) == 0 ? 0 : 1);
+  return it;
+}
+
+// Global loads of a face evaluation: the face normal of the item's node and, across a shared face,
+// the neighbour's trace (ext false at an outflow or wall side: the ghost is built from the own
+// trace once it is in shared memory).
+template <int P, class LAW, typename T>
+__device__ __forceinline__ void face_prefetch(const Instance<T>& I, long long e, const FaceItem<P>& it, T* un,
+                                              T& nvx, T& nvy, bool& ext) {
+  constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
+  const long long N = I.N, gi = e * NN + it.a * n + it.b;
+  nvx = I.geo[(it.dir == 0 ? GEO_NXX : GEO_NYX) * N + gi];
+  nvy = I.geo[(it.dir == 0 ? GEO_NXY : GEO_NYY) * N + gi];
+  const long long gn = curved_nbr<P>(I.bc, I.nx, I.ny, e, it.a, it.b, it.side);
+  ext = gn >= 0;
+#pragma unroll
+  for (int q = 0; q < NC; ++q) un[q] = ext ? I.uin[q * N + gn] : T(0);
+}
+
+// One face evaluation (after the node states are in shared memory): the ghost at a boundary
+// (outflow: the own trace; slip wall, Sec. 5.7: the own trace with its momentum reflected about
+// the face's unit normal, m - 2 (m . n) n), then the flux with the -xi/-eta side as the left state.
+template <int P, class LAW, typename T>
+__device__ __forceinline__ void face_eval(const CurvedSmem<P, LAW, T>& s, const Instance<T>& I,
+                                          const LawParamsT<T>& lp, const FaceItem<P>& it, int le, T* un, T nvx,
+                                          T nvy, bool ext, CurvedFace<P, LAW, T>& F) {
+  constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
+  using Aux = typename LAW::Aux;
+  const int slot = le * NN + it.a * n + it.b;
+  const Vec<T, NC> uo = s.u[slot];
+  const Aux ao = s.aux[slot];
+  if (!ext) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) un[q] = uo.v[q];
+    if constexpr (NC == 4) {
+      if (I.bc[it.side] == SIDP_BC_SLIP_WALL) {
+        const T inn = frcp(psqrt(nvx * nvx + nvy * nvy));
+        const T nx = nvx * inn, ny = nvy * inn;
+        const T mn = uo.v[1] * nx + uo.v[2] * ny;
+        un[1] = uo.v[1] - T(2) * mn * nx;
+        un[2] = uo.v[2] - T(2) * mn * ny;
+      }
+    }
+  }
+  Aux an;
+  LAW::aux(un, an, lp);
+  // operands ordered by selects, not by a branch per side
+  const bool low = (it.side & 1) == 0;  // the neighbour is the left state
+  T uL[NC], uR[NC];
+#pragma unroll
+  for (int q = 0; q < NC; ++q) {
+    uL[q] = low ? un[q] : uo.v[q];
+    uR[q] = low ? uo.v[q] : un[q];
+  }
+  const Aux aL = low ? an : ao, aR = low ? ao : an;
   T fLx[NC], fLy[NC], fRx[NC], fRy[NC];
   LAW::flux(uL, aL, 0, fLx, lp);
   LAW::flux(uL, aL, 1, fLy, lp);
@@ -96,44 +188,14 @@ __device__ __forceinline__ void curved_face(const T* uL, const typename LAW::Aux
   LAW::flux(uR, aR, 1, fRy, lp);
   const T nn = psqrt(nvx * nvx + nvy * nvy);
   const T lam = LAW::lam_n(uL, aL, uR, aR, fdiv(nvx, nn), fdiv(nvy, nn), lp);
-  ln = lam * nn;
+  F.ln = lam * nn;
 #pragma unroll
-  for (int q = 0; q < NC; ++q)
-    Fh[q] = T(0.5) * ((fLx[q] + fRx[q]) * nvx + (fLy[q] + fRy[q]) * nvy) - T(0.5) * ln * (uR[q] - uL[q]);
+  for (int q = 0; q < NC; ++q) {
+    F.Fh[q] = T(0.5) * ((fLx[q] + fRx[q]) * nvx + (fLy[q] + fRy[q]) * nvy) - T(0.5) * F.ln * (uR[q] - uL[q]);
+    F.Fn[q] = (low ? fRx[q] : fLx[q]) * nvx + (low ? fRy[q] : fLy[q]) * nvy;
+  }
   const T dF = (fRx[0] - fLx[0]) * nvx + (fRy[0] - fLy[0]) * nvy;
-  bar0 = T(0.5) * (uL[0] + uR[0]) - ((ln > T(0)) ? fdiv(dF, T(2) * ln) : T(0));
-}
-
-// The node's element faces: trace of the neighbour, face flux, bar state, sigma of the neighbour,
-// lambda |n|, and the node's own F . n (high-order face term).  dir 0: x face (b = 0 or p),
-// dir 1: y face (a = 0 or p).
-template <int P, class LAW, typename T>
-struct CurvedFace {
-  T Fh[LAW::NC];   // flux in +xi (+eta)
-  T Fn[LAW::NC];   // own F . n
-  T bar, sig, ln;
-  T um;            // |u| of the neighbour's trace, limited field (operand scale of the face)
-};
-
-template <int P, class LAW, typename T>
-__device__ __forceinline__ void curved_element_face(const Instance<T>& I, const LawParamsT<T>& lp, long long e,
-                                                    int a, int b, int dir, const T* u, const typename LAW::Aux& ax,
-                                                    const T* fx, const T* fy, CurvedFace<P, LAW, T>& F) {
-  constexpr int NC = LAW::NC;
-  const long long N = I.N, g = e * (P + 1) * (P + 1) + a * (P + 1) + b;
-  const bool low = (dir == 0) ? (b == 0) : (a == 0);
-  const int side = dir * 2 + (low ? 0 : 1);
-  const T nvx = I.geo[(dir == 0 ? GEO_NXX : GEO_NYX) * N + g], nvy = I.geo[(dir == 0 ? GEO_NXY : GEO_NYY) * N + g];
-  const long long gn = curved_nbr<P>(I.bc, I.nx, I.ny, e, a, b, side);
-  T un[NC];
-#pragma unroll
-  for (int q = 0; q < NC; ++q) un[q] = (gn >= 0) ? I.uin[q * N + gn] : u[q];
-  typename LAW::Aux an;
-  LAW::aux(un, an, lp);
-  if (low) curved_face<LAW>(un, an, u, ax, nvx, nvy, lp, F.Fh, F.bar, F.ln);
-  else curved_face<LAW>(u, ax, un, an, nvx, nvy, lp, F.Fh, F.bar, F.ln);
-#pragma unroll
-  for (int q = 0; q < NC; ++q) F.Fn[q] = fx[q] * nvx + fy[q] * nvy;
+  F.bar = T(0.5) * (uL[0] + uR[0]) - ((F.ln > T(0)) ? fdiv(dF, T(2) * F.ln) : T(0));
   if constexpr (LAW::kEntropy) F.sig = LAW::sigma(un, an, lp);
   else F.sig = T(0);
   F.um = fabs(un[0]);
@@ -185,6 +247,11 @@ __device__ __forceinline__ void curved_load(CurvedSmem<P, LAW, T>& s, const Inst
   constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
   const long long N = I.N, g = act ? e * NN + a * n + b : 0;
   const T* geo = I.geo;
+  // this thread's element-face evaluation: its global loads go out with the node's own
+  const FaceItem<P> it = face_item<P>(a, b, act);
+  T un[NC], nvx = T(0), nvy = T(0);
+  bool ext = false;
+  if (it.on) face_prefetch<P, LAW>(I, e, it, un, nvx, nvy, ext);
 #pragma unroll
   for (int q = 0; q < NC; ++q) u[q] = I.uin[q * N + g];
   LAW::aux(u, ax, lp);
@@ -215,20 +282,133 @@ __device__ __forceinline__ void curved_load(CurvedSmem<P, LAW, T>& s, const Inst
   else s.sig[t] = T(0);
   onx = act && (b == 0 || b == P);
   ony = act && (a == 0 || a == P);
-  if (onx) curved_element_face<P, LAW>(I, lp, e, a, b, 0, u, ax, fx, fy, FX);
-  if (ony) curved_element_face<P, LAW>(I, lp, e, a, b, 1, u, ax, fx, fy, FY);
+  const int le = t / NN;
   __syncthreads();
-  if (b < P) curved_internal_face<P, LAW>(s, t, t + 1, 0, lp);
-  if (a < P) curved_internal_face<P, LAW>(s, t, t + n, 1, lp);
+  // subcell faces as one list over the CTA, all x faces (b < p) and then all y faces (a < p): the
+  // last round leaves whole warps idle instead of every warp running both directions
+  {
+    constexpr int FPE = P * n;                        // faces per element and direction
+    constexpr int NXF = CurvedGeom<P>::EPB * FPE;     // x faces of the CTA
+#pragma unroll
+    for (int f = t; f < 2 * NXF; f += CurvedGeom<P>::THREADS) {
+      const int dir = f >= NXF ? 1 : 0;
+      const int r = f - dir * NXF;
+      const int fe = r / FPE, j = r - fe * FPE;
+      const int L = fe * NN + (dir ? j : (j / P) * n + j % P);
+      curved_internal_face<P, LAW>(s, L, L + (dir ? n : 1), dir, lp);
+    }
+  }
+  CurvedFace<P, LAW, T> R{};
+  if (it.on) face_eval<P, LAW>(s, I, lp, it, le, un, nvx, nvy, ext, R);
+  if (it.corner >= 0) s.cy[le][it.corner] = R;
+  FX = R;  // the node's own item is its x face wherever it has one (edges W/E and corners)
+  FY = R;  // and its y face on the S/N edges; corners take theirs below
+  const int k = (a == P ? 2 : 0) + (b == P ? 1 : 0);  // corner index, when onx && ony
+  constexpr int kHelped = (P - 1) * (P - 1) < 4 ? (P - 1) * (P - 1) : 4;  // corners with a helper
+  if constexpr (kHelped < 4) {
+    // p < 3: too few interior nodes; the remaining corners evaluate their y face themselves
+    if (onx && ony && k >= kHelped) {
+      const FaceItem<P> iy{a, b, 1, 2 + (a == 0 ? 0 : 1), -1, true};
+      T un2[NC], nx2, ny2;
+      bool ext2;
+      face_prefetch<P, LAW>(I, e, iy, un2, nx2, ny2, ext2);
+      face_eval<P, LAW>(s, I, lp, iy, le, un2, nx2, ny2, ext2, FY);
+    }
+  }
   __syncthreads();
+  if (onx && ony && k < kHelped) FY = s.cy[le][k];
+}
+
+
+// Entropy-bound violation of a limited float32 result fe at node (a, b) of element e, slot t:
+// max(0, 1 - sigma(fe) / K_i) with K_i = min sigma over the node and its four neighbours of the
+// stage input, sigma evaluated accurately (compensated rho e, the ratio in float64) as in the
+// Cartesian statistics.  In-element neighbours come from shared memory, the neighbour across an
+// element face from global memory; an outflow or slip-wall ghost has the node's own sigma (the
+// mirrored momentum keeps |m|).  Statistics kernels only.
+template <int P, class LAW, typename T>
+__device__ double curved_entropy_violation64(const CurvedSmem<P, LAW, T>& s, const Instance<T>& I,
+                                             const LawParamsT<T>& lp, long long e, int t, int a, int b,
+                                             const T* fe) {
+  constexpr int n = P + 1, NC = LAW::NC;
+  auto sig = [&](const T* u) { return (double)LAW::rhoe(u) * (double)powf(u[0], -lp.gamma); };
+  double K = sig(s.u[t].v);
+  if (b > 0) K = fmin(K, sig(s.u[t - 1].v));
+  if (b < P) K = fmin(K, sig(s.u[t + 1].v));
+  if (a > 0) K = fmin(K, sig(s.u[t - n].v));
+  if (a < P) K = fmin(K, sig(s.u[t + n].v));
+  const int sides[2] = {b == 0 ? 0 : (b == P ? 1 : -1), a == 0 ? 2 : (a == P ? 3 : -1)};
+  for (int k = 0; k < 2; ++k) {
+    if (sides[k] < 0) continue;
+    const long long gn = curved_nbr<P>(I.bc, I.nx, I.ny, e, a, b, sides[k]);
+    if (gn < 0) continue;
+    T un[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) un[q] = I.uin[q * I.N + gn];
+    K = fmin(K, sig(un));
+  }
+  if (!((double)fe[0] > 0.0)) return 1.0;
+  return fmax(0.0, 1.0 - sig(fe) / K);
+}
+
+// Bound and entropy violations of one limited result (statistics kernels only), as in the
+// Cartesian stage statistics: the excess over [lo, hi] relative to max(|bound|, field scale), and
+// max(0, 1 - sigma(fe)/K).
+template <int P, class LAW, typename T>
+__device__ __forceinline__ void curved_violations(const CurvedSmem<P, LAW, T>& s, const Instance<T>& I,
+                                                  const LawParamsT<T>& lp, long long e, int t, int a, int b,
+                                                  const T* fe, T lo, T hi, T K, T& v, T& ev) {
+  const T scale = tmax(tmax(fabs(lo), fabs(hi)), T(I.stats->field_scale));
+  v = tmax(lo - fe[0], fe[0] - hi);
+  v = (v > T(0)) ? fdiv(v, scale > T(0) ? scale : T(1)) : T(0);
+  ev = T(0);
+  if constexpr (LAW::kEntropy) {
+    if constexpr (sizeof(T) == 4) {
+      ev = T(curved_entropy_violation64<P, LAW, T>(s, I, lp, e, t, a, b, fe));
+    } else {
+      ev = tmax(T(0), T(1) - LAW::sigma_of(fe, lp) / K);
+      if (!(fe[0] > T(0))) ev = T(1);
+    }
+  }
+}
+
+// Stage statistics of a curved CTA (all threads call it; statistics kernels only).  The CTA need
+// not be a whole number of warps, so the per-node values go through shared memory (the rows and
+// fluxes of phase B, read for the last time before phase C) and the first, always complete, warp
+// reduces them: one atomic per CTA and quantity.
+template <int P, class LAW, typename T>
+__device__ void curved_stats(CurvedSmem<P, LAW, T>& s, StageStats* st, T v, T ev, int caps, int iters, int nudged) {
+  constexpr int TH = CurvedGeom<P>::THREADS;
+  const int t = threadIdx.x;
+  s.q[t][0] = v;
+  s.q[t][1] = ev;
+  s.q[t][2] = T(caps);
+  s.q[t][3] = T(iters);
+  s.F0[t][0] = T(nudged);
+  __syncthreads();
+  if (t < 32) {
+    double mv = 0.0, me = 0.0;
+    int c = 0, m = 0, gs = 0;
+    for (int j = t; j < TH; j += 32) {
+      mv = fmax(mv, (double)s.q[j][0]);
+      me = fmax(me, (double)s.q[j][1]);
+      c += (int)s.q[j][2];
+      m = max(m, (int)s.q[j][3]);
+      gs += (int)s.F0[j][0];
+    }
+    warp_rootfind_stats(c, m, gs, st);
+    warp_max_atomic(mv, &st->max_bound_violation);
+    warp_max_atomic(me, &st->max_entropy_violation);
+  }
 }
 
 }  // namespace sidp
 
 namespace sidp {
 
-// ELW: elementwise limiting (Sec. 4.1.2, 4.2.1) instead of the subcell limiter.
-template <int P, class LAW, typename T, bool ELW = false>
+// ELW: elementwise limiting (Sec. 4.1.2, 4.2.1) instead of the subcell limiter.  STATS: the
+// variant with the per-stage statistics (launched when they are on).
+template <int P, class LAW, typename T, bool ELW = false, bool STATS = false>
 __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::value) k_stage_curved(const StageLaunch<T> A) {
   using Gm = CurvedGeom<P>;
   using V = Vec<T, LAW::NC>;
@@ -349,6 +529,7 @@ __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::va
 #pragma unroll
     for (int q = 0; q < NC; ++q) rn[q] = rx[q] + ry[q];
     T at = T(1);
+    int iters = 0, caps = 0;
     if (act && move) {
       const T mdt = fdiv(m, dt);
       const T Qp = tmax(T(0), mdt * (hi - uL[0]));
@@ -360,7 +541,6 @@ __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::va
         T w[NC];
 #pragma unroll
         for (int q = 0; q < NC; ++q) w[q] = dtm * rn[q];
-        int iters = 0, caps = 0;
         at = entropy_limit_dir<LAW>(uL, K * (T(1) + Prec<T>::entropy_margin), w, at, lp, iters, caps);
       }
     }
@@ -378,6 +558,8 @@ __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::va
       s.aK[le] = mn;
     }
     __syncthreads();
+    T v = T(0), ev = T(0);
+    int nudged = 0;
     if (act) {
       const T ak = s.aK[le];
       T fe[NC];
@@ -385,11 +567,17 @@ __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::va
       for (int q = 0; q < NC; ++q) fe[q] = uL[q] + ak * dtm * rn[q];
       if constexpr (sizeof(T) == 4) {
         if (!(fe[0] >= lo && fe[0] <= hi))  // rare: the rounding scale only where it is needed
-          accept_rounded(fe[0], lo, hi, curved_stencil_scale<P>(s, t, a, b, u[0], FX.um, FY.um) + fabs(uL[0]) +
-                                            fabs(ak * dtm * rn[0]) + tmax(fabs(lo), fabs(hi)));
+          nudged = accept_rounded(fe[0], lo, hi, curved_stencil_scale<P>(s, t, a, b, u[0], FX.um, FY.um) +
+                                                     fabs(uL[0]) + fabs(ak * dtm * rn[0]) + tmax(fabs(lo), fabs(hi)));
       }
 #pragma unroll
       for (int q = 0; q < NC; ++q) I.uout[q * N + g] = (I.c0 == T(0)) ? fe[q] : I.c0 * I.u0[q * N + g] + I.c1 * fe[q];
+      if constexpr (STATS) {
+        if (I.stats && move) curved_violations<P, LAW, T>(s, I, lp, e, t, a, b, fe, lo, hi, K, v, ev);
+      }
+    }
+    if constexpr (STATS) {
+      if (I.stats) curved_stats<P, LAW, T>(s, I.stats, v, ev, caps, iters, nudged);
     }
     return;
   }
@@ -453,6 +641,8 @@ __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::va
   }
   __syncthreads();
   // ---------------- E: face coefficients and limited update
+  T v = T(0), ev = T(0);
+  int nudged = 0;
   if (act) {
     const T axp = (b < P) ? tmin(at, s.alpha[t + 1]) : T(0);
     const T axm = (b > 0) ? tmin(at, s.alpha[t - 1]) : T(0);
@@ -463,12 +653,19 @@ __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::va
     for (int q = 0; q < NC; ++q) fe[q] = uL[q] + dtm * (axp * xp[q] - axm * xm[q] + ayp * yp[q] - aym * ym[q]);
     if constexpr (sizeof(T) == 4) {
       if (!(fe[0] >= lo && fe[0] <= hi))  // rare: the rounding scale only where it is needed
-        accept_rounded(fe[0], lo, hi, curved_stencil_scale<P>(s, t, a, b, u[0], FX.um, FY.um) + fabs(uL[0]) +
-                                          tmax(fabs(lo), fabs(hi)) +
-                                          dtm * (fabs(axp * xp[0]) + fabs(axm * xm[0]) + fabs(ayp * yp[0]) + fabs(aym * ym[0])));
+        nudged = accept_rounded(fe[0], lo, hi, curved_stencil_scale<P>(s, t, a, b, u[0], FX.um, FY.um) +
+                                                   fabs(uL[0]) + tmax(fabs(lo), fabs(hi)) +
+                                                   dtm * (fabs(axp * xp[0]) + fabs(axm * xm[0]) + fabs(ayp * yp[0]) +
+                                                          fabs(aym * ym[0])));
     }
 #pragma unroll
     for (int q = 0; q < NC; ++q) I.uout[q * N + g] = (I.c0 == T(0)) ? fe[q] : I.c0 * u0[q] + I.c1 * fe[q];
+    if constexpr (STATS) {
+      if (I.stats && move) curved_violations<P, LAW, T>(s, I, lp, e, t, a, b, fe, lo, hi, K, v, ev);
+    }
+  }
+  if constexpr (STATS) {
+    if (I.stats) curved_stats<P, LAW, T>(s, I.stats, v, ev, caps, iters, nudged);
   }
 }
 
@@ -528,6 +725,10 @@ cudaError_t launch_curved(const StageLaunch<T>& a, unsigned long long* dt_bits, 
       if (err != cudaSuccess) return err;
       err = cudaFuncSetAttribute(k_stage_curved<P, LAW, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (err != cudaSuccess) return err;
+      err = cudaFuncSetAttribute(k_stage_curved<P, LAW, T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
+      err = cudaFuncSetAttribute(k_stage_curved<P, LAW, T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
       err = cudaFuncSetAttribute(k_dt_curved<P, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (err != cudaSuccess) return err;
       attr_set = true;
@@ -535,8 +736,11 @@ cudaError_t launch_curved(const StageLaunch<T>& a, unsigned long long* dt_bits, 
     const long long Ne = (long long)a.inst.nx * a.inst.ny;
     const long long blocks = (Ne + Gm::EPB - 1) / Gm::EPB;
     if (blocks <= 0) return cudaSuccess;
+    const bool elw = a.limiter == SIDP_LIMITER_ELEMENTWISE, stats = a.inst.stats && a.limiter >= 2;
     if (dt_bits) k_dt_curved<P, LAW, T><<<(unsigned)blocks, Gm::THREADS, smem, s>>>(a, dt_bits);
-    else if (a.limiter == SIDP_LIMITER_ELEMENTWISE) k_stage_curved<P, LAW, T, true><<<(unsigned)blocks, Gm::THREADS, smem, s>>>(a);
+    else if (elw && stats) k_stage_curved<P, LAW, T, true, true><<<(unsigned)blocks, Gm::THREADS, smem, s>>>(a);
+    else if (elw) k_stage_curved<P, LAW, T, true><<<(unsigned)blocks, Gm::THREADS, smem, s>>>(a);
+    else if (stats) k_stage_curved<P, LAW, T, false, true><<<(unsigned)blocks, Gm::THREADS, smem, s>>>(a);
     else k_stage_curved<P, LAW, T><<<(unsigned)blocks, Gm::THREADS, smem, s>>>(a);
     return cudaGetLastError();
   }

@@ -94,8 +94,8 @@ sidp_status curved_metrics(int p, int nx, int ny, const int* bc, const double* x
     return SIDP_ERR_ARG;
   }
   for (int s = 0; s < 4; ++s)
-    if (bc[s] != SIDP_BC_PERIODIC && bc[s] != SIDP_BC_OUTFLOW) {
-      msg = "curved meshes take periodic or outflow sides";
+    if (bc[s] != SIDP_BC_PERIODIC && bc[s] != SIDP_BC_OUTFLOW && bc[s] != SIDP_BC_SLIP_WALL) {
+      msg = "curved meshes take periodic, outflow or slip-wall sides";
       return SIDP_ERR_ARG;
     }
   const int n = p + 1, NN = n * n;

@@ -288,3 +288,146 @@ def test_set_geometry_errors():
     sv = sidp.Solver(law="burgers", p=2, nx=3, ny=3, bc=OUT)
     with pytest.raises(sidp.SidpError):
         sv.set_geometry(-X, Y)
+
+
+# ---------------------------------------------------------------- slip walls on curved meshes
+WALL_CHANNEL = ("periodic", "periodic", "wall", "wall")
+ROT_WALLS = ("wall", "outflow", "wall", "wall")
+
+
+def wavy_channel(p, nel, amp=0.06):
+    """A channel periodic in x with a wavy lower wall y = amp sin(2 pi x) and a straight upper one:
+    the nodes of the unit square moved by y += amp (1 - y) sin(2 pi x)."""
+    X, Y = scheme.Problem(laws.Euler(G), p, nel, nel).node_coords()
+    return X, Y + amp * (1.0 - Y) * np.sin(2.0 * np.pi * X)
+
+
+def channel_data(X, Y):
+    law = laws.Euler(G)
+    rho = 1.0 + 0.3 * np.exp(-((X - 0.4) ** 2 + (Y - 0.5) ** 2) / 0.02)
+    return law.prim_to_cons(rho, 0.5 + 0.2 * Y, 0.3 * np.sin(2 * np.pi * X), 1.0 + 0.2 * rho)
+
+
+def wall_case(mesh, p, limiter, precision="fp64"):
+    """(oracle, solver, U): the wavy channel (6x6) or the rotated square (4x4, theta = 0.3) with
+    three walls and one outflow side, with smooth data."""
+    law = laws.Euler(G)
+    if mesh == "wavy":
+        nel, bc = 6, WALL_CHANNEL
+        X, Y = wavy_channel(p, nel)
+        U = channel_data(X, Y)
+    else:
+        nel, bc = 4, ROT_WALLS
+        X, Y = inputs.rotated_coords(*scheme.Problem(law, p, nel, nel).node_coords(), 0.3)
+        U = law.prim_to_cons(*tw._data(X, Y))
+    pb = CurvedProblem(law, p, nel, nel, X, Y, bc=bc, limiter=limiter)
+    sv = sidp.Solver(law="euler", p=p, nx=nel, ny=nel, bc=bc, limiter=limiter, gamma=G, precision=precision)
+    sv.set_geometry(X, Y)
+    return pb, sv, U
+
+
+@pytest.mark.parametrize("mesh", ["wavy", "rotated"])
+@pytest.mark.parametrize("limiter", ["none", "lo"])
+@pytest.mark.parametrize("p", [2, 3, 5])
+def test_slip_wall_stages_match_the_oracle(p, limiter, mesh):
+    """Slip walls on mapped faces (the ghost is the trace with its momentum reflected about the
+    face's unit normal): dt and the three stages, element by element, FP64."""
+    pb, sv, U0 = wall_case(mesh, p, limiter)
+    dt = pb.compute_dt(U0)
+    sv.set_state(U0.reshape(4, -1))
+    assert abs(sv.compute_dt() - dt) <= 1e-13 * dt
+    cur = U0
+    for k in (1, 2, 3):
+        expect = pb.stage(cur, U0, dt, k)
+        sv.stage(k, dt)
+        got = sv.get_state({1: 1, 2: 2, 3: 0}[k])
+        assert np.all(rel(got, expect) <= 1e-12), (k, rel(got, expect))
+        cur = expect
+
+
+@pytest.mark.parametrize("mesh,max_relaxed", [("wavy", 0.15), ("rotated", 0.02)])
+@pytest.mark.parametrize("p", [3, 4])
+def test_slip_wall_subcell_stage(p, mesh, max_relaxed):
+    """One limited stage next to curved walls, with the conditioning-aware comparator, and the
+    bounds (bar states of the wall faces included) against the oracle's."""
+    pb, sv, U = wall_case(mesh, p, "subcell")
+    dt = pb.compute_dt(U)
+    sv.set_state(U.reshape(4, -1))
+    sv.set_debug(True)
+    sv.stage(1, dt)
+    euler_fe_check(pb, U, dt, sv.get_state(1), sv.bounds()["alpha"], max_relaxed=max_relaxed)
+    _, info = pb.fe_stage(U, dt, full=True)
+    bd = sv.bounds()
+    np.testing.assert_allclose(bd["lo"], info["lo"].ravel(), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(bd["hi"], info["hi"].ravel(), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(bd["K"], info["K"].ravel(), rtol=1e-12)
+
+
+def test_slip_wall_whole_steps_low_order():
+    """Five whole steps (dt on the device) in the wavy channel against the oracle."""
+    pb, sv, U = wall_case("wavy", 3, "lo")
+    sv.set_state(U.reshape(4, -1))
+    for _ in range(5):
+        U, dt = pb.ssp_rk3_step(U)
+        sv.step()
+        assert abs(sv.diag()["last_dt"] - dt) <= 1e-13 * dt
+    assert np.all(rel(sv.get_state(0), U) <= 1e-11)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_wavy_channel_conservation_and_rest_state(precision):
+    """No mass and no energy cross a curved wall: both conserved over 30 limited steps (the
+    vertical momentum is not: the walls push), positivity, the violation statistics of the curved
+    statistics kernel (density bounds held exactly, the entropy minimum to the float32 measure's
+    rounding), and a gas at rest staying at rest to order sqrt(eps) of the stage precision: on
+    mapped elements the per-direction momentum fluxes of a rest state are not zero, its u^L sits
+    on the entropy bound to rounding, and kinetic energy is quadratic in the momentum, so the line
+    search admits a coefficient of order sqrt(eps) (measured: 2.5e-8 in FP64, 1.8e-4 in float32
+    after three steps, both below sqrt(eps))."""
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    _, sv, U = wall_case("wavy", 3, "subcell", precision=precision)
+    sv.set_state(U.reshape(4, -1))
+    m0 = sv.diag()["mass"]
+    sv.step(30)
+    d = sv.diag()
+    assert abs(d["mass"][0] - m0[0]) <= tol * abs(m0[0])
+    assert abs(d["mass"][3] - m0[3]) <= tol * abs(m0[3])
+    assert abs(d["mass"][2] - m0[2]) > 1e-5
+    assert d["rho_min"] > 0 and d["p_min"] > 0 and d["nonfinite"] == 0
+    assert d["max_bound_violation"] <= (1e-12 if precision == "fp64" else 0.0)
+    assert d["max_entropy_violation"] <= (1e-12 if precision == "fp64" else 1e-6)
+    assert d["rootfind_max_iters"] > 0   # the statistics are collected (entropy root searches ran)
+    X, Y = sv.node_coords()
+    rest = laws.Euler(G).prim_to_cons(1.0 + 0.0 * X, 0.0 * X, 0.0 * X, 1.0 + 0.0 * X)
+    sv.set_state(rest)
+    sv.step(3)
+    print(f"rest state, {precision}: max deviation {np.abs(sv.get_state(0) - rest).max():.3e}")
+    eps = np.finfo(np.float64 if precision == "fp64" else np.float32).eps
+    np.testing.assert_allclose(sv.get_state(0), rest, rtol=0, atol=4.0 * np.sqrt(eps))
+
+
+@pytest.mark.parametrize("limiter", ["subcell", "elementwise"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_curved_statistics_kernel_computes_the_same_state(precision, limiter):
+    """The statistics variant of the curved stage kernel (launched while statistics are on) gives
+    the state of the timed variant (FP64: bit for bit; float32: to rounding, the compiler being
+    free to contract the two variants' arithmetic differently), and reports the root-search
+    counters and the violation maxima (zero density-bound excess; the entropy minimum to
+    rounding)."""
+    res = {}
+    for on in (False, True):
+        pb, sv, X, Y = make("euler", 3, 8, 8, limiter, L=(1.0, 1.0), precision=precision)
+        sv.set_state(inputs.blast(X, Y).reshape(4, -1))
+        sv.set_stats(on)
+        sv.step(5)
+        res[on] = (sv.get_state(0), sv.diag())
+    if precision == "fp64":
+        np.testing.assert_array_equal(res[True][0], res[False][0])
+    else:
+        assert np.all(rel(res[True][0], res[False][0]) <= 1e-6), rel(res[True][0], res[False][0])
+    d = res[True][1]
+    assert d["rootfind_max_iters"] > 0 and d["rootfind_cap_hits"] == 0
+    assert d["max_bound_violation"] <= (1e-12 if precision == "fp64" else 0.0)
+    assert d["max_entropy_violation"] <= (1e-12 if precision == "fp64" else 1e-6)
+    off = res[False][1]
+    assert off["rootfind_max_iters"] == 0 and off["max_bound_violation"] == 0.0
