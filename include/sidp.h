@@ -292,7 +292,16 @@ sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int cou
 sidp_status sidp_batch_destroy(sidp_batch* b);
 sidp_status sidp_batch_sizes(const sidp_batch* b, int i, long long* n_nodes, int* nc);
 sidp_status sidp_batch_total_nodes(const sidp_batch* b, long long* n_nodes);
+/* Node coordinates of instance i (float64 [N_i] each, caller-owned): the Cartesian nodes, or the
+ * coordinates given to sidp_batch_set_geometry. */
 sidp_status sidp_batch_node_coords(const sidp_batch* b, int i, double* x, double* y);
+/* Move instance i onto the curved mesh with node coordinates x, y (float64 [N_i] each, copied),
+ * as sidp_set_geometry does for a context (Sec. 2.3 metric terms, Sec. 3.1 correction; the same
+ * laws, limiters and sides; SIDP_ERR_ARG otherwise or for a mesh with det J <= 0).  The instance
+ * joins the curved group of its degree: one launch per stage over tasks of (instance, block of
+ * elements) with the curved-mesh kernels.  Mass and extrema in sidp_batch_get_diag use m_i.
+ * Drops the captured step graph and turns the single-launch mode off.  Synchronous. */
+sidp_status sidp_batch_set_geometry(sidp_batch* b, int i, const double* x, const double* y);
 sidp_status sidp_batch_set_state(sidp_batch* b, int i, const double* u);
 sidp_status sidp_batch_get_state(sidp_batch* b, int i, double* u);
 /* Instance i's buffer `which` (0: u^n, 1: u^(1), 2: u^(2)) as float64 [nc][N_i] (caller-owned

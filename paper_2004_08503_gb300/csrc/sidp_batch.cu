@@ -8,6 +8,9 @@
 //     dt launches (one per degree group) -> per-instance finalisation -> 3 x stage launches per group
 // and is captured once in a CUDA graph that later steps replay.
 //
+// Instances moved onto curved meshes (sidp_batch_set_geometry) form degree groups of their own,
+// launched with the curved-mesh kernels over tasks of (instance, block of EPB elements).
+//
 // Trade-off: one launch per degree group (the groups on concurrent graph branches) rather than
 // one launch that switches on p inside.  Both exist: SIDP_BATCH_LAUNCH=single selects the single
 // degree-switching launch (k_batch_all: default tile shapes, tasks by decreasing degree, the
@@ -45,6 +48,7 @@ __global__ void k_batch_finalize(unsigned long long* bits, const double* cfl, do
 
 struct Group {
   int p = 0;  // degree and tile shape shared by the group's tasks
+  bool curved = false;  // curved-mesh instances: tasks are (instance, element block), one shape
   int tile = 0;
   int2* d_tasks = nullptr;
   int ntasks = 0;
@@ -66,6 +70,11 @@ struct sidp_batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<long long> N, off;  // nodes and value offset of each instance
+  // curved meshes (sidp_batch_set_geometry): per instance the device metric arrays (null while the
+  // instance is Cartesian) and host copies of its node coordinates and masses
+  std::vector<void*> d_geo;
+  std::vector<std::vector<double>> hx, hy, hmass;
+  bool any_shape = false;  // the groups keep task tables for every tile shape
   long long total_vals = 0;
   void* d_u[3] = {nullptr, nullptr, nullptr};
   void* d_inst[4] = {nullptr, nullptr, nullptr, nullptr};  // instance tables: dt, stage 1, 2, 3
@@ -133,6 +142,7 @@ cudaError_t build_tables(sidp_batch* b) {
     I.dt = b->d_dt + i;
     I.dtT = dtT + i;
     I.stats = b->stats_on ? b->d_stats + i : nullptr;
+    I.geo = static_cast<const T*>(b->d_geo[i]);
     const long long o = b->off[i];
     if (b->debug && b->d_dbg) {  // per-node captures at the instance's node offset
       const long long no = o / b->nc;
@@ -211,6 +221,7 @@ cudaError_t launch_group(sidp_batch* b, int gi, int k, cudaStream_t st, bool tim
     bl.limiter = b->limiter;
     bl.bits = b->d_bits;
     bl.stats = (b->stats_on && !timed) ? 1 : 0;
+    bl.curved = gr.curved ? 1 : 0;
     const int tile = default_shape ? 0 : gr.tile;
     switch (b->law) {
       case LAW_BURGERS: return launch_batch_law<LAW_BURGERS, T>(gr.p, tile, bl, k == 0, st);
@@ -285,6 +296,70 @@ cudaError_t run_batch_step(sidp_batch* b) {
   return e;
 }
 
+// Degree groups and their task tables: Cartesian instances of degree p, (instance, tile) for every
+// tile shape (one tile shape per degree, the starting point of the batch autotuner: the
+// single-instance tuner's choice when it has run for this (law, p, precision), else the default;
+// the stage kernels of other limiters, of the smoothness indicator and of the statistics exist
+// for the default shape only, so every group keeps a task table for that shape); curved-mesh
+// instances of degree p, (instance, block of EPB elements).  A regrouping keeps the tile shape a
+// Cartesian degree had.  One stream and one event per group.
+cudaError_t build_groups(sidp_batch* b) {
+  std::map<int, int> keep;
+  for (Group& g : b->groups) {
+    if (!g.curved) keep[g.p] = g.tile;
+    for (int t = 0; t < kNumTiles; ++t) cudaFree(g.d_tasks_t[t]);
+  }
+  b->groups.clear();
+  std::map<std::pair<int, int>, std::vector<int2>> tasks[kNumTiles];  // per tile shape: (curved, p) -> tasks
+  for (int i = 0; i < b->n; ++i) {
+    const sidp_config& c = b->cfgs[i];
+    if (b->d_geo[i]) {
+      const int nn = (c.p + 1) * (c.p + 1), epb = (256 / nn) > 0 ? 256 / nn : 1;  // CurvedGeom<p>::EPB
+      const long long nb = ((long long)c.nx * c.ny + epb - 1) / epb;
+      for (long long k = 0; k < nb; ++k) tasks[0][{1, c.p}].push_back(make_int2(i, (int)k));
+      continue;
+    }
+    for (int tile = 0; tile < (b->any_shape ? kNumTiles : 1); ++tile) {
+      const TileShape ts = kTiles[c.p][tile];
+      const long long ntiles = (long long)((c.nx + ts.tx - 1) / ts.tx) * ((c.ny + ts.ty - 1) / ts.ty);
+      for (long long t = 0; t < ntiles; ++t) tasks[tile][{0, c.p}].push_back(make_int2(i, (int)t));
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  for (auto& kv : tasks[0]) {
+    Group g;
+    g.curved = kv.first.first != 0;
+    g.p = kv.first.second;
+    b->groups.push_back(g);
+    Group& gr = b->groups.back();
+    const int tables = (!gr.curved && b->any_shape) ? kNumTiles : 1;
+    for (int tile = 0; tile < tables; ++tile) {
+      const std::vector<int2>& v = tasks[tile][kv.first];
+      gr.ntasks_t[tile] = (int)v.size();
+      if ((e = cudaMalloc(&gr.d_tasks_t[tile], sizeof(int2) * v.size())) != cudaSuccess) return e;
+      if ((e = cudaMemcpy(gr.d_tasks_t[tile], v.data(), sizeof(int2) * v.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    }
+    int tile = 0;
+    if (!gr.curved && b->any_shape) {
+      tile = keep.count(gr.p) ? keep[gr.p] : tuned_tile(b->law, gr.p, b->mixed ? 1 : 0);
+      if (tile < 0) tile = 0;
+    }
+    gr.tile = tile;
+    gr.d_tasks = gr.d_tasks_t[tile];
+    gr.ntasks = gr.ntasks_t[tile];
+  }
+  while (b->gstream.size() < b->groups.size()) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    b->gstream.push_back(st);
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+    b->gdone.push_back(ev);
+  }
+  return cudaSuccess;
+}
+
 // Batch autotuner: with valid time steps in place (one time-step pass; the clocks are restored
 // afterwards), time stage 1 of each degree group with each tile shape and keep the fastest.
 // Stage 1 writes only u^(1), so the state is untouched.  The groups are tuned one after another
@@ -301,6 +376,7 @@ cudaError_t tune_batch(sidp_batch* b) {
   if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return e; }
   for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
     Group& g = b->groups[gi];
+    if (g.curved) continue;  // one kernel shape on curved meshes
     float best = 1e30f;
     int best_t = g.tile;
     for (int t = 0; t < kNumTiles && e == cudaSuccess; ++t) {
@@ -369,30 +445,19 @@ sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int cou
   };
   b->N.resize(count);
   b->off.resize(count);
+  b->d_geo.assign(count, nullptr);
+  b->hx.resize(count);
+  b->hy.resize(count);
+  b->hmass.resize(count);
   long long tot = 0;
-  // one tile shape per degree, the starting point of the batch autotuner: the single-instance
-  // tuner's choice when it has run for this (law, p, precision), else the default (fitting the
-  // shape to each mesh to cut padding measured slower: more, smaller launches).  The stage kernels
-  // of other limiters, of the smoothness indicator and of the statistics exist for the default
-  // shape only; every group keeps a task table for that shape.
   const bool any_shape = cfgs[0].limiter == 2 && !cfgs[0].smoothness;
-  int ptile[kMaxP + 1];
-  for (int p = 1; p <= kMaxP; ++p) {
-    ptile[p] = any_shape ? tuned_tile(cfgs[0].law, p, cfgs[0].precision == SIDP_MIXED ? 1 : 0) : 0;
-    if (ptile[p] < 0) ptile[p] = 0;
-  }
-  std::map<int, std::vector<int2>> tasks[kNumTiles];  // per tile shape: p -> tasks
+  b->any_shape = any_shape;
   for (int i = 0; i < count; ++i) {
     const sidp_config& c = cfgs[i];
     const int nn = (c.p + 1) * (c.p + 1);
     b->N[i] = (long long)c.nx * c.ny * nn;
     b->off[i] = tot;
     tot += b->nc * b->N[i];
-    for (int tile = 0; tile < (any_shape ? kNumTiles : 1); ++tile) {
-      const TileShape ts = kTiles[c.p][tile];
-      const long long ntiles = (long long)((c.nx + ts.tx - 1) / ts.tx) * ((c.ny + ts.ty - 1) / ts.ty);
-      for (long long t = 0; t < ntiles; ++t) tasks[tile][c.p].push_back(make_int2(i, (int)t));
-    }
   }
   b->total_vals = tot;
   b->total_nodes = tot / b->nc;
@@ -423,23 +488,7 @@ sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int cou
       (e = cudaMemset(b->d_u[0], 0, tot * b->esize)) != cudaSuccess)
     return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
   if ((e = b->mixed ? build_tables<float>(b) : build_tables<double>(b)) != cudaSuccess) return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
-  for (auto& kv : tasks[0]) {
-    Group g;
-    g.p = kv.first;
-    b->groups.push_back(g);
-    Group& gr = b->groups.back();
-    for (int tile = 0; tile < (any_shape ? kNumTiles : 1); ++tile) {
-      const std::vector<int2>& v = tasks[tile][g.p];
-      gr.ntasks_t[tile] = (int)v.size();
-      if (cudaMalloc(&gr.d_tasks_t[tile], sizeof(int2) * v.size()) != cudaSuccess)
-        return bail(SIDP_ERR_OOM, "task table allocation failed");
-      if ((e = cudaMemcpy(gr.d_tasks_t[tile], v.data(), sizeof(int2) * v.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
-        return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
-    }
-    gr.tile = ptile[g.p];
-    gr.d_tasks = gr.d_tasks_t[gr.tile];
-    gr.ntasks = gr.ntasks_t[gr.tile];
-  }
+  if ((e = build_groups(b)) != cudaSuccess) return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
   // the batch autotuner runs at the first step unless a shape is forced or the table knows them
   b->tuned = !any_shape || std::getenv("SIDP_TILE") != nullptr ||
              (std::getenv("SIDP_AUTOTUNE") && std::getenv("SIDP_AUTOTUNE")[0] == '0');
@@ -465,14 +514,6 @@ sidp_status sidp_batch_create(sidp_batch** out, const sidp_config* cfgs, int cou
       return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
   }
   if ((e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)) != cudaSuccess) return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
-  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
-    cudaStream_t st = nullptr;
-    cudaEvent_t ev = nullptr;
-    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
-    b->gstream.push_back(st);
-    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return bail(SIDP_ERR_CUDA, cudaGetErrorString(e));
-    b->gdone.push_back(ev);
-  }
   *out = b;
   return SIDP_OK;
 } catch (const std::bad_alloc&) {
@@ -498,6 +539,7 @@ sidp_status sidp_batch_destroy(sidp_batch* b) {
   cudaFree(b->d_bits);
   cudaFree(b->d_stats);
   cudaFree(b->d_dbg);
+  for (void* gp : b->d_geo) cudaFree(gp);
   for (cudaStream_t st : b->gstream) cudaStreamDestroy(st);
   for (cudaEvent_t ev : b->gdone) cudaEventDestroy(ev);
   if (b->fork) cudaEventDestroy(b->fork);
@@ -523,6 +565,11 @@ sidp_status sidp_batch_total_nodes(const sidp_batch* b, long long* n_nodes) {
 
 sidp_status sidp_batch_node_coords(const sidp_batch* b, int i, double* x, double* y) try {
   if (!b || i < 0 || i >= b->n || !x || !y) return bfail(nullptr, SIDP_ERR_ARG, "bad argument");
+  if (b->d_geo[i]) {  // curved mesh: the coordinates it was given
+    std::memcpy(x, b->hx[i].data(), b->N[i] * sizeof(double));
+    std::memcpy(y, b->hy[i].data(), b->N[i] * sizeof(double));
+    return SIDP_OK;
+  }
   const sidp_config& c = b->cfgs[i];
   double xi[kMaxN], w[kMaxN], D[kMaxN * kMaxN];
   gll_tables(c.p, xi, w, D);
@@ -541,6 +588,47 @@ sidp_status sidp_batch_node_coords(const sidp_batch* b, int i, double* x, double
   return bfail(nullptr, SIDP_ERR_OOM, "host allocation failed");
 } catch (...) {
   return bfail(nullptr, SIDP_ERR_ARG, "unexpected host exception");
+}
+
+sidp_status sidp_batch_set_geometry(sidp_batch* b, int i, const double* x, const double* y) try {
+  if (!b || i < 0 || i >= b->n || !x || !y) return bfail(b, SIDP_ERR_ARG, "bad argument");
+  const sidp_config& c = b->cfgs[i];
+  if (c.law == SIDP_LAW_ADVECTION_VAR2D)
+    return bfail(b, SIDP_ERR_ARG, "variable-velocity advection is defined on Cartesian meshes only");
+  for (int k = 0; k < 4; ++k)
+    if (c.bc[k] != SIDP_BC_PERIODIC && c.bc[k] != SIDP_BC_OUTFLOW && c.bc[k] != SIDP_BC_SLIP_WALL)
+      return bfail(b, SIDP_ERR_ARG, "curved meshes take periodic, outflow or slip-wall sides");
+  const long long N = b->N[i];
+  std::vector<double> geo((size_t)kGeoFields * N);
+  std::string msg;
+  const sidp_status st = curved_metrics(c.p, c.nx, c.ny, c.bc, x, y, geo.data(), msg);
+  if (st != SIDP_OK) return bfail(b, st, msg);
+  BCUDA(b, cudaStreamSynchronize(b->stream));
+  if (!b->d_geo[i] && cudaMalloc(&b->d_geo[i], (size_t)kGeoFields * N * b->esize) != cudaSuccess) {
+    b->d_geo[i] = nullptr;
+    return bfail(b, SIDP_ERR_OOM, "geometry allocation failed");
+  }
+  if (b->mixed) {
+    std::vector<float> tmp(geo.begin(), geo.end());
+    BCUDA(b, cudaMemcpy(b->d_geo[i], tmp.data(), tmp.size() * sizeof(float), cudaMemcpyHostToDevice));
+  } else {
+    BCUDA(b, cudaMemcpy(b->d_geo[i], geo.data(), geo.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  b->hx[i].assign(x, x + N);
+  b->hy[i].assign(y, y + N);
+  b->hmass[i].assign(geo.begin() + (size_t)GEO_MASS_FIELD * N, geo.begin() + (size_t)(GEO_MASS_FIELD + 1) * N);
+  // regroup (the instance joins the curved group of its degree), new instance tables, a new graph;
+  // the single-launch mode has no curved kernels
+  if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+  b->warm = false;
+  b->single = false;
+  BCUDA(b, b->mixed ? build_tables<float>(b) : build_tables<double>(b));
+  BCUDA(b, build_groups(b));
+  return SIDP_OK;
+} catch (const std::bad_alloc&) {
+  return bfail(b, SIDP_ERR_OOM, "host allocation failed");
+} catch (...) {
+  return bfail(b, SIDP_ERR_ARG, "unexpected host exception");
 }
 
 sidp_status sidp_batch_set_state(sidp_batch* b, int i, const double* u) try {
@@ -687,9 +775,10 @@ sidp_status sidp_batch_get_diag(sidp_batch* b, int i, sidp_diag* out) try {
   const double h = (c.x1 - c.x0) / c.nx;
   for (int f = 0; f < 4; ++f) { out->umin[f] = f < b->nc ? DBL_MAX : 0.0; out->umax[f] = f < b->nc ? -DBL_MAX : 0.0; }
   out->rho_min = out->p_min = (b->law == SIDP_LAW_EULER2D) ? DBL_MAX : 0.0;
+  const bool curved = b->d_geo[i] != nullptr;
   for (long long j = 0; j < N; ++j) {
     const int node = (int)(j % NN);
-    const double m = h * h * w[node / n] * w[node % n];
+    const double m = curved ? b->hmass[i][j] : h * h * w[node / n] * w[node % n];
     for (int f = 0; f < b->nc; ++f) {
       const double v = u[f * N + j];
       if (!std::isfinite(v)) { ++out->nonfinite; continue; }

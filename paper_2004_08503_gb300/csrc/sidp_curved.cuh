@@ -406,22 +406,20 @@ __device__ void curved_stats(CurvedSmem<P, LAW, T>& s, StageStats* st, T v, T ev
 
 namespace sidp {
 
-// ELW: elementwise limiting (Sec. 4.1.2, 4.2.1) instead of the subcell limiter.  STATS: the
-// variant with the per-stage statistics (launched when they are on).
-template <int P, class LAW, typename T, bool ELW = false, bool STATS = false>
-__global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::value) k_stage_curved(const StageLaunch<T> A) {
+// One stage on element block eb (elements eb * EPB ...) of instance I.  ELW: elementwise limiting
+// (Sec. 4.1.2, 4.2.1) instead of the subcell limiter.  STATS: the variant with the per-stage
+// statistics (launched when they are on).
+template <int P, class LAW, typename T, bool ELW, bool STATS>
+__device__ __forceinline__ void curved_stage_body(CurvedSmem<P, LAW, T>& s, const Instance<T>& I, const Tables<T>& tab,
+                                                  const LawParamsT<T>& lp, const SmoothnessT<T>& si, int limiter,
+                                                  long long eb) {
   using Gm = CurvedGeom<P>;
   using V = Vec<T, LAW::NC>;
   constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  auto& s = *reinterpret_cast<CurvedSmem<P, LAW, T>*>(smem_raw);
-  const Instance<T>& I = A.inst;
-  const LawParamsT<T>& lp = A.lp;
   const int t = threadIdx.x, le = t / NN, i = t - le * NN, a = i / n, b = i - a * n;
-  const long long e = (long long)blockIdx.x * Gm::EPB + le;
+  const long long e = eb * Gm::EPB + le;
   const bool act = e < (long long)I.nx * I.ny;
   const long long N = I.N, g = act ? e * NN + i : 0;
-  const int limiter = A.limiter;
 
   // ---------------- A, B: node data, element faces, subcell faces
   T u[NC];
@@ -433,18 +431,17 @@ __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::va
   // ---------------- smoothness indicator (Sec. 4.4) on the reference element: Legendre
   // coefficients of the limited field (separable nodal -> modal transform), s_K =
   // log10(||u - u-hat||^2 / ||u||^2) with u-hat dropping the modes of degree p in either variable
-  const SmoothnessT<T>& si = A.si;
   if (si.on && limiter >= 2) {
     const int base = le * NN;
     T c1 = T(0);
 #pragma unroll
-    for (int c = 0; c < n; ++c) c1 += A.tab.Vinv[b * n + c] * s.u[base + a * n + c].v[0];
+    for (int c = 0; c < n; ++c) c1 += tab.Vinv[b * n + c] * s.u[base + a * n + c].v[0];
     s.alpha[t] = c1;
     __syncthreads();
     T cc = T(0);
 #pragma unroll
-    for (int c = 0; c < n; ++c) cc += A.tab.Vinv[a * n + c] * s.alpha[base + c * n + b];
-    const T wgt = cc * cc * A.tab.nrm[a] * A.tab.nrm[b];
+    for (int c = 0; c < n; ++c) cc += tab.Vinv[a * n + c] * s.alpha[base + c * n + b];
+    const T wgt = cc * cc * tab.nrm[a] * tab.nrm[b];
     __syncthreads();
     s.alpha[t] = wgt;
     __syncthreads();
@@ -470,7 +467,7 @@ __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::va
   // ---------------- C: residuals, low-order state, bounds
   const T dt = *I.dtT;
   const bool move = (dt > T(0)) && (dt < T(FLT_MAX));
-  const T wa = A.tab.w[a], wb = A.tab.w[b];
+  const T wa = tab.w[a], wb = tab.w[b];
   const T m = I.geo[GEO_MASS * N + g];
   const T dtm = move ? fdiv(dt, m) : T(0);
   T sx[NC], sy[NC];
@@ -480,7 +477,7 @@ __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::va
 #pragma unroll
   for (int c = 0; c < n; ++c) {
     const V F1c = s.f1[lx + c], F2c = s.f2[ly + c * n];
-    const T dx = A.tab.D[b * n + c], dy = A.tab.D[a * n + c];
+    const T dx = tab.D[b * n + c], dy = tab.D[a * n + c];
 #pragma unroll
     for (int q = 0; q < NC; ++q) { sx[q] += dx * F1c.v[q]; sy[q] += dy * F2c.v[q]; }
   }
@@ -669,27 +666,44 @@ __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::va
   }
 }
 
+template <int P, class LAW, typename T, bool ELW = false, bool STATS = false>
+__global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::value) k_stage_curved(const StageLaunch<T> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& s = *reinterpret_cast<CurvedSmem<P, LAW, T>*>(smem_raw);
+  curved_stage_body<P, LAW, T, ELW, STATS>(s, A.inst, A.tab, A.lp, A.si, A.limiter, blockIdx.x);
+}
+
+// Batched stage on curved meshes: CTA blockIdx.x runs task (instance, element block) of the task
+// table; all tasks of one launch share P, law and precision.
+template <int P, class LAW, typename T, bool ELW = false, bool STATS = false>
+__global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::value) k_stage_curved_batch(const BatchLaunch<T> B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& s = *reinterpret_cast<CurvedSmem<P, LAW, T>*>(smem_raw);
+  __shared__ Instance<T> sI;
+  const int2 task = B.tasks[blockIdx.x];
+  load_instance(sI, B.insts + task.x);
+  curved_stage_body<P, LAW, T, ELW, STATS>(s, sI, B.tab, B.lp, B.si, B.limiter, task.y);
+}
+
 // CFL bound of Eq. cfl-low per node on a curved mesh, m_i / (2 sum_{j != i} d_ij): subcell faces
 // d = w Lambda / 2, element faces d = w lambda |n| / 2; min-reduced into *out_bits.
 template <int P, class LAW, typename T>
-__global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::value) k_dt_curved(const StageLaunch<T> A, unsigned long long* out_bits) {
+__device__ __forceinline__ void curved_dt_body(CurvedSmem<P, LAW, T>& s, const Instance<T>& I, const Tables<T>& tab,
+                                               const LawParamsT<T>& lp, long long eb, unsigned long long* out_bits) {
   using Gm = CurvedGeom<P>;
   constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  auto& s = *reinterpret_cast<CurvedSmem<P, LAW, T>*>(smem_raw);
-  const Instance<T>& I = A.inst;
   const int t = threadIdx.x, le = t / NN, i = t - le * NN, a = i / n, b = i - a * n;
-  const long long e = (long long)blockIdx.x * Gm::EPB + le;
+  const long long e = eb * Gm::EPB + le;
   const bool act = e < (long long)I.nx * I.ny;
   T u[NC];
   typename LAW::Aux ax;
   CurvedFace<P, LAW, T> FX{}, FY{};
   bool onx, ony;
-  curved_load<P, LAW>(s, I, A.lp, e, act, t, a, b, u, ax, FX, FY, onx, ony);
+  curved_load<P, LAW>(s, I, lp, e, act, t, a, b, u, ax, FX, FY, onx, ony);
   const T big = T(FLT_MAX);
   T val = big;
   if (act) {
-    const T wa = A.tab.w[a], wb = A.tab.w[b];
+    const T wa = tab.w[a], wb = tab.w[b];
     const T half = T(0.5);
     T sumd = T(0);
     sumd += (b > 0) ? half * wa * s.lam[t - 1][0] : half * wa * FX.ln;
@@ -710,6 +724,24 @@ __global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::va
     for (int o = 16; o > 0; o >>= 1) val = tmin(val, __shfl_xor_sync(0xffffffffu, val, o));
     if (t == 0 && val < big) atomicMin(out_bits, (unsigned long long)__double_as_longlong((double)val));
   }
+}
+
+template <int P, class LAW, typename T>
+__global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::value) k_dt_curved(const StageLaunch<T> A, unsigned long long* out_bits) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& s = *reinterpret_cast<CurvedSmem<P, LAW, T>*>(smem_raw);
+  curved_dt_body<P, LAW, T>(s, A.inst, A.tab, A.lp, blockIdx.x, out_bits);
+}
+
+// Batched time step on curved meshes: task (instance, element block), into the instance's accumulator.
+template <int P, class LAW, typename T>
+__global__ void __launch_bounds__(CurvedGeom<P>::THREADS, CurvedMinBlocks<T>::value) k_dt_curved_batch(const BatchLaunch<T> B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& s = *reinterpret_cast<CurvedSmem<P, LAW, T>*>(smem_raw);
+  __shared__ Instance<T> sI;
+  const int2 task = B.tasks[blockIdx.x];
+  load_instance(sI, B.insts + task.x);
+  curved_dt_body<P, LAW, T>(s, sI, B.tab, B.lp, task.y, B.bits + task.x);
 }
 
 template <int P, class LAW, typename T>
@@ -742,6 +774,40 @@ cudaError_t launch_curved(const StageLaunch<T>& a, unsigned long long* dt_bits, 
     else if (elw) k_stage_curved<P, LAW, T, true><<<(unsigned)blocks, Gm::THREADS, smem, s>>>(a);
     else if (stats) k_stage_curved<P, LAW, T, false, true><<<(unsigned)blocks, Gm::THREADS, smem, s>>>(a);
     else k_stage_curved<P, LAW, T><<<(unsigned)blocks, Gm::THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+  }
+}
+
+// Batched launches on curved meshes: the tasks are (instance, element block of EPB elements).
+template <int P, class LAW, typename T>
+cudaError_t launch_curved_batch(const BatchLaunch<T>& B, bool dt, cudaStream_t s) {
+  if constexpr (HasPosition<LAW>::value) {
+    return cudaErrorInvalidValue;  // position-dependent laws are defined on Cartesian meshes only
+  } else {
+    using Gm = CurvedGeom<P>;
+    constexpr size_t smem = sizeof(CurvedSmem<P, LAW, T>);
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaError_t err = cudaSuccess;
+      auto set = [&](const void* f) {
+        if (err == cudaSuccess) err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      };
+      set((const void*)k_stage_curved_batch<P, LAW, T>);
+      set((const void*)k_stage_curved_batch<P, LAW, T, true>);
+      set((const void*)k_stage_curved_batch<P, LAW, T, false, true>);
+      set((const void*)k_stage_curved_batch<P, LAW, T, true, true>);
+      set((const void*)k_dt_curved_batch<P, LAW, T>);
+      if (err != cudaSuccess) return err;
+      attr_set = true;
+    }
+    if (B.ntasks <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)B.ntasks;
+    const bool elw = B.limiter == SIDP_LIMITER_ELEMENTWISE, stats = B.stats && B.limiter >= 2;
+    if (dt) k_dt_curved_batch<P, LAW, T><<<grid, Gm::THREADS, smem, s>>>(B);
+    else if (elw && stats) k_stage_curved_batch<P, LAW, T, true, true><<<grid, Gm::THREADS, smem, s>>>(B);
+    else if (elw) k_stage_curved_batch<P, LAW, T, true><<<grid, Gm::THREADS, smem, s>>>(B);
+    else if (stats) k_stage_curved_batch<P, LAW, T, false, true><<<grid, Gm::THREADS, smem, s>>>(B);
+    else k_stage_curved_batch<P, LAW, T><<<grid, Gm::THREADS, smem, s>>>(B);
     return cudaGetLastError();
   }
 }

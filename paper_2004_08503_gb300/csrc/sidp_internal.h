@@ -149,6 +149,7 @@ struct BatchLaunch {
   int limiter;
   SmoothnessT<T> si;
   unsigned long long* bits;  // per-instance time-step accumulators (dt launches)
+  int curved;                // the instances are on curved meshes: tasks are (instance, element block)
 };
 
 // A launch over every degree group at once (the single-launch batch mode): CTA i runs
@@ -269,6 +270,8 @@ SIDP_DECLARE_ALL(LAW_ADVECTION_VAR, float)
   }                                                                                                    \
   template <>                                                                                          \
   cudaError_t launch_batch_p<LAWID, TT, P>(int tile, const BatchLaunch<TT>& b, bool dt, cudaStream_t s) { \
+    if (b.curved) /* curved meshes: their own kernels */                                              \
+      return launch_curved_batch<P, LAWTPL<TT>, TT>(b, dt, s);                                         \
     if (b.limiter == 3 && !dt)                                                                         \
       return launch_batch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, true>(b, dt, s);  \
     if (b.stats && !dt)                                                                                \

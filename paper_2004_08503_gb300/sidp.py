@@ -86,6 +86,7 @@ _SIGS = {
     "sidp_batch_total_nodes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     "sidp_batch_node_coords": (ctypes.c_int, [_P, ctypes.c_int, _D, _D]),
     "sidp_batch_set_state": (ctypes.c_int, [_P, ctypes.c_int, _D]),
+    "sidp_batch_set_geometry": (ctypes.c_int, [_P, ctypes.c_int, _D, _D]),
     "sidp_batch_get_state": (ctypes.c_int, [_P, ctypes.c_int, _D]),
     "sidp_batch_get_buffer": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _D]),
     "sidp_fma_peak": (ctypes.c_int, [ctypes.c_int, _D, _P]),
@@ -351,6 +352,15 @@ def sidp_batch_node_coords(b, i):
     x, y = np.empty(n), np.empty(n)
     _bcheck(load().sidp_batch_node_coords(b, i, _ptr(x), _ptr(y)), b)
     return x, y
+
+
+def sidp_batch_set_geometry(b, i, x, y):
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    y = np.ascontiguousarray(y, dtype=np.float64).ravel()
+    n, _ = sidp_batch_sizes(b, i)
+    if x.size != n or y.size != n:
+        raise ValueError(f"instance {i} has {n} nodes; got {x.size} and {y.size} coordinates")
+    _bcheck(load().sidp_batch_set_geometry(b, i, _ptr(x), _ptr(y)), b)
 
 
 def sidp_batch_set_state(b, i, u):
