@@ -75,7 +75,7 @@ typedef struct {
                        adv_beta[1] + adv_grad[1] x), divergence-free (Sec. 3.3; the solid body
                        rotation of Sec. 5.4 is adv_beta = (pi, -pi), adv_grad = (-2 pi, 2 pi))    */
   int p;            /* polynomial degree, 1..7                                                   */
-  int nx, ny;       /* elements per direction, >= 1                                              */
+  int nx, ny;       /* elements per direction, >= 1, nx * ny < 2^31                              */
   int precision;    /* SIDP_FP64: everything in float64.  SIDP_MIXED: float32 state and stage
                        arithmetic, float64 time step reduction                                   */
   double x0, x1, y0, y1;  /* domain; elements must be square                                     */

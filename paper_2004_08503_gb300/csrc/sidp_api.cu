@@ -383,6 +383,7 @@ sidp_status validate_config(const sidp_config* cfg, std::string& msg) {
       cfg->law != SIDP_LAW_ADVECTION_VAR2D) { msg = "unknown law"; return SIDP_ERR_ARG; }
   if (cfg->p < 1 || cfg->p > kMaxP) { msg = "p must be in 1..7"; return SIDP_ERR_ARG; }
   if (cfg->nx < 1 || cfg->ny < 1) { msg = "nx, ny must be >= 1"; return SIDP_ERR_ARG; }
+  if ((long long)cfg->nx * cfg->ny > 2147483647LL) { msg = "a mesh has fewer than 2^31 elements"; return SIDP_ERR_ARG; }
   if (cfg->precision != SIDP_FP64 && cfg->precision != SIDP_MIXED) { msg = "unknown precision"; return SIDP_ERR_ARG; }
   const double hx = (cfg->x1 - cfg->x0) / cfg->nx, hy = (cfg->y1 - cfg->y0) / cfg->ny;
   if (!(hx > 0) || !(hy > 0) || std::fabs(hx - hy) > 1e-12 * hx) { msg = "elements must be square with positive size"; return SIDP_ERR_ARG; }

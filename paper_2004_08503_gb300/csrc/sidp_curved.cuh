@@ -85,7 +85,8 @@ struct CurvedSmem {
 template <int P>
 __device__ __forceinline__ long long curved_nbr(const int* bc, int nx, int ny, long long e, int a, int b, int s) {
   constexpr int n = P + 1, NN = n * n;
-  int ex = (int)(e % nx), ey = (int)(e / nx);
+  const int ei = (int)e;  // element indices fit in int (a mesh has fewer than 2^31 elements)
+  int ey = ei / nx, ex = ei - ey * nx;
   int na = a, nb = b;
   if (s == 0) { if (ex == 0 && bc[0] != SIDP_BC_PERIODIC) return -1; ex = (ex == 0) ? nx - 1 : ex - 1; nb = P; }
   else if (s == 1) { if (ex == nx - 1 && bc[1] != SIDP_BC_PERIODIC) return -1; ex = (ex == nx - 1) ? 0 : ex + 1; nb = 0; }
@@ -189,10 +190,22 @@ __device__ __forceinline__ void face_eval(const CurvedSmem<P, LAW, T>& s, const 
   const T nn = psqrt(nvx * nvx + nvy * nvy);
   const T lam = LAW::lam_n(uL, aL, uR, aR, fdiv(nvx, nn), fdiv(nvy, nn), lp);
   F.ln = lam * nn;
+  {
+    T sx[NC], sy[NC], du[NC], ox[NC], oy[NC];
+    v_add<NC>(sx, fLx, fRx);
+    v_add<NC>(sy, fLy, fRy);
+    v_scale<NC>(sx, nvx, sx);
+    v_fma<NC>(sx, nvy, sy, sx);  // (F_L + F_R) . n
+    v_scale<NC>(sx, T(0.5), sx);
+    v_sub<NC>(du, uR, uL);
+    v_fma<NC>(F.Fh, T(-0.5) * F.ln, du, sx);
 #pragma unroll
-  for (int q = 0; q < NC; ++q) {
-    F.Fh[q] = T(0.5) * ((fLx[q] + fRx[q]) * nvx + (fLy[q] + fRy[q]) * nvy) - T(0.5) * F.ln * (uR[q] - uL[q]);
-    F.Fn[q] = (low ? fRx[q] : fLx[q]) * nvx + (low ? fRy[q] : fLy[q]) * nvy;
+    for (int q = 0; q < NC; ++q) {
+      ox[q] = low ? fRx[q] : fLx[q];
+      oy[q] = low ? fRy[q] : fLy[q];
+    }
+    v_scale<NC>(F.Fn, nvx, ox);
+    v_fma<NC>(F.Fn, nvy, oy, F.Fn);
   }
   const T dF = (fRx[0] - fLx[0]) * nvx + (fRy[0] - fLy[0]) * nvy;
   F.bar = T(0.5) * (uL[0] + uR[0]) - ((F.ln > T(0)) ? fdiv(dF, T(2) * F.ln) : T(0));
@@ -226,9 +239,11 @@ __device__ __forceinline__ void curved_internal_face(CurvedSmem<P, LAW, T>& s, i
   const T lL = LAW::lam_n(uL.v, aL, uR.v, aR, fdiv(qLx, nL), fdiv(qLy, nL), lp) * nL;
   const T Lam = tmax(lR, lL);
   const Vec<T, NC> gL = dir == 0 ? s.g1[L] : s.g2[L], gR = dir == 0 ? s.g1[R] : s.g2[R];
-  Vec<T, NC> G;
-#pragma unroll
-  for (int q = 0; q < NC; ++q) G.v[q] = T(0.5) * (gL.v[q] + gR.v[q]) - T(0.5) * Lam * (uR.v[q] - uL.v[q]);
+  Vec<T, NC> G, gs, du;
+  v_add<NC>(gs.v, gL.v, gR.v);
+  v_sub<NC>(du.v, uR.v, uL.v);
+  v_scale<NC>(gs.v, T(0.5), gs.v);
+  v_fma<NC>(G.v, T(-0.5) * Lam, du.v, gs.v);
   const T dFx = s.F0[R][0] - s.F0[L][0], dFy = s.F0[R][1] - s.F0[L][1];
   const T mid = T(0.5) * (uL.v[0] + uR.v[0]);
   const T inv2 = (Lam > T(0)) ? fdiv(T(1), T(2) * Lam) : T(0);
@@ -262,13 +277,15 @@ __device__ __forceinline__ void curved_load(CurvedSmem<P, LAW, T>& s, const Inst
   const T q1x = geo[GEO_Q1X * N + g], q1y = geo[GEO_Q1Y * N + g], q2x = geo[GEO_Q2X * N + g], q2y = geo[GEO_Q2Y * N + g];
   Vec<T, NC> vu, f1, f2, g1, g2;
 #pragma unroll
-  for (int q = 0; q < NC; ++q) {
-    vu.v[q] = u[q];
-    f1.v[q] = r1x * fx[q] + r1y * fy[q];
-    f2.v[q] = r2x * fx[q] + r2y * fy[q];
-    g1.v[q] = q1x * fx[q] + q1y * fy[q];
-    g2.v[q] = q2x * fx[q] + q2y * fy[q];
-  }
+  for (int q = 0; q < NC; ++q) vu.v[q] = u[q];
+  v_scale<NC>(f1.v, r1y, fy);
+  v_fma<NC>(f1.v, r1x, fx, f1.v);
+  v_scale<NC>(f2.v, r2y, fy);
+  v_fma<NC>(f2.v, r2x, fx, f2.v);
+  v_scale<NC>(g1.v, q1y, fy);
+  v_fma<NC>(g1.v, q1x, fx, g1.v);
+  v_scale<NC>(g2.v, q2y, fy);
+  v_fma<NC>(g2.v, q2x, fx, g2.v);
   s.u[t] = vu;
   s.aux[t] = ax;
   s.f1[t] = f1;
@@ -478,26 +495,43 @@ __device__ __forceinline__ void curved_stage_body(CurvedSmem<P, LAW, T>& s, cons
   for (int c = 0; c < n; ++c) {
     const V F1c = s.f1[lx + c], F2c = s.f2[ly + c * n];
     const T dx = tab.D[b * n + c], dy = tab.D[a * n + c];
-#pragma unroll
-    for (int q = 0; q < NC; ++q) { sx[q] += dx * F1c.v[q]; sy[q] += dy * F2c.v[q]; }
+    v_fma<NC>(sx, dx, F1c.v, sx);
+    v_fma<NC>(sy, dy, F2c.v, sy);
   }
   const V Gr = (b < P) ? s.Gx[t] : V{}, Gl = (b > 0) ? s.Gx[t - 1] : V{};
   const V Gu = (a < P) ? s.Gy[t] : V{}, Gd = (a > 0) ? s.Gy[t - n] : V{};
   T uL[NC], rx[NC], ry[NC], out[NC];
+  T gr[NC], gl[NC], gu[NC], gd[NC];
 #pragma unroll
   for (int q = 0; q < NC; ++q) {
     if (b == 0) sx[q] += FX.Fn[q] - FX.Fh[q];
     if (b == P) sx[q] += FX.Fh[q] - FX.Fn[q];
     if (a == 0) sy[q] += FY.Fn[q] - FY.Fh[q];
     if (a == P) sy[q] += FY.Fh[q] - FY.Fn[q];
-    const T rHx = -wa * sx[q], rHy = -wb * sy[q];
-    const T gr = (b < P) ? Gr.v[q] : FX.Fh[q], gl = (b > 0) ? Gl.v[q] : FX.Fh[q];
-    const T gu = (a < P) ? Gu.v[q] : FY.Fh[q], gd = (a > 0) ? Gd.v[q] : FY.Fh[q];
-    const T rLx = -wa * (gr - gl), rLy = -wb * (gu - gd);
-    uL[q] = u[q] + dtm * (rLx + rLy);
-    out[q] = (limiter == 0) ? u[q] + dtm * (rHx + rHy) : uL[q];
-    rx[q] = rHx - rLx;
-    ry[q] = rHy - rLy;
+    gr[q] = (b < P) ? Gr.v[q] : FX.Fh[q];
+    gl[q] = (b > 0) ? Gl.v[q] : FX.Fh[q];
+    gu[q] = (a < P) ? Gu.v[q] : FY.Fh[q];
+    gd[q] = (a > 0) ? Gd.v[q] : FY.Fh[q];
+  }
+  {
+    T rHx[NC], rHy[NC], rLx[NC], rLy[NC], tq[NC];
+    v_scale<NC>(rHx, -wa, sx);
+    v_scale<NC>(rHy, -wb, sy);
+    v_sub<NC>(tq, gr, gl);
+    v_scale<NC>(rLx, -wa, tq);
+    v_sub<NC>(tq, gu, gd);
+    v_scale<NC>(rLy, -wb, tq);
+    v_add<NC>(tq, rLx, rLy);
+    v_fma<NC>(uL, dtm, tq, u);
+    if (limiter == 0) {
+      v_add<NC>(tq, rHx, rHy);
+      v_fma<NC>(out, dtm, tq, u);
+    } else {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) out[q] = uL[q];
+    }
+    v_sub<NC>(rx, rHx, rLx);
+    v_sub<NC>(ry, rHy, rLy);
   }
   if (limiter < 2 && act) {
 #pragma unroll
@@ -560,8 +594,7 @@ __device__ __forceinline__ void curved_stage_body(CurvedSmem<P, LAW, T>& s, cons
     if (act) {
       const T ak = s.aK[le];
       T fe[NC];
-#pragma unroll
-      for (int q = 0; q < NC; ++q) fe[q] = uL[q] + ak * dtm * rn[q];
+      v_fma<NC>(fe, ak * dtm, rn, uL);
       if constexpr (sizeof(T) == 4) {
         if (!(fe[0] >= lo && fe[0] <= hi))  // rare: the rounding scale only where it is needed
           nudged = accept_rounded(fe[0], lo, hi, curved_stencil_scale<P>(s, t, a, b, u[0], FX.um, FY.um) +
@@ -646,8 +679,12 @@ __device__ __forceinline__ void curved_stage_body(CurvedSmem<P, LAW, T>& s, cons
     const T ayp = (a < P) ? tmin(at, s.alpha[t + n]) : T(0);
     const T aym = (a > 0) ? tmin(at, s.alpha[t - n]) : T(0);
     T fe[NC];
-#pragma unroll
-    for (int q = 0; q < NC; ++q) fe[q] = uL[q] + dtm * (axp * xp[q] - axm * xm[q] + ayp * yp[q] - aym * ym[q]);
+    T acc[NC];
+    v_scale<NC>(acc, axp, xp);
+    v_fma<NC>(acc, -axm, xm, acc);
+    v_fma<NC>(acc, ayp, yp, acc);
+    v_fma<NC>(acc, -aym, ym, acc);
+    v_fma<NC>(fe, dtm, acc, uL);
     if constexpr (sizeof(T) == 4) {
       if (!(fe[0] >= lo && fe[0] <= hi))  // rare: the rounding scale only where it is needed
         nudged = accept_rounded(fe[0], lo, hi, curved_stencil_scale<P>(s, t, a, b, u[0], FX.um, FY.um) +
@@ -655,8 +692,16 @@ __device__ __forceinline__ void curved_stage_body(CurvedSmem<P, LAW, T>& s, cons
                                                    dtm * (fabs(axp * xp[0]) + fabs(axm * xm[0]) + fabs(ayp * yp[0]) +
                                                           fabs(aym * ym[0])));
     }
+    T res[NC];
+    if (I.c0 == T(0)) {
 #pragma unroll
-    for (int q = 0; q < NC; ++q) I.uout[q * N + g] = (I.c0 == T(0)) ? fe[q] : I.c0 * u0[q] + I.c1 * fe[q];
+      for (int q = 0; q < NC; ++q) res[q] = fe[q];
+    } else {  // the SSP-RK3 combination c0 u^n + c1 u^FE
+      v_scale<NC>(res, I.c1, fe);
+      v_fma<NC>(res, I.c0, u0, res);
+    }
+#pragma unroll
+    for (int q = 0; q < NC; ++q) I.uout[q * N + g] = res[q];
     if constexpr (STATS) {
       if (I.stats && move) curved_violations<P, LAW, T>(s, I, lp, e, t, a, b, fe, lo, hi, K, v, ev);
     }

@@ -648,9 +648,11 @@ __device__ __forceinline__ void face_eval_r(S& s, int k, int L, const Vec<T, LAW
   const V FL = k ? s.fy[L] : s.fx[L];
   const typename LAW::Aux aL = s.aux[L];
   const T lam = LAW::lam(k, uL.v, aL, uR.v, aR, lp);
-  V fb;
-#pragma unroll
-  for (int q = 0; q < NC; ++q) fb.v[q] = T(0.5) * (FL.v[q] + FR.v[q]) - T(0.5) * lam * (uR.v[q] - uL.v[q]);
+  V fb, fs, du;
+  v_add<NC>(fs.v, FL.v, FR.v);
+  v_sub<NC>(du.v, uR.v, uL.v);
+  v_scale<NC>(fs.v, T(0.5), fs.v);
+  v_fma<NC>(fb.v, T(-0.5) * lam, du.v, fs.v);
   Vec<T, LAW::kEntropy ? 2 : 1> bb;
   bb.v[0] = (lam > T(0)) ? T(0.5) * (uL.v[0] + uR.v[0]) - fdiv(FR.v[0] - FL.v[0], T(2) * lam)
                          : T(0.5) * (uL.v[0] + uR.v[0]);
@@ -814,8 +816,8 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
       const V Fxc = s.fx[lx + c];
       const V Fyc = s.fy[ly + c * n];
       const T dx = s.D[b * n + c], dy = s.D[a * n + c];
-#pragma unroll
-      for (int q = 0; q < NC; ++q) { sx[q] += dx * Fxc.v[q]; sy[q] += dy * Fyc.v[q]; }
+      v_fma<NC>(sx, dx, Fxc.v, sx);
+      v_fma<NC>(sy, dy, Fyc.v, sy);
     }
     const V vu = s.u[me], vfx = s.fx[me], vfy = s.fy[me];
     const V fl = s.fbx[ix], fr = s.fbx[ixr], fd = s.fby[iy], fu = s.fby[iyu];
@@ -834,23 +836,38 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
     }
     T out[NC];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) {
+    for (int q = 0; q < NC; ++q) {  // element-face terms of the high-order residual
       if (b == 0) sx[q] += vfx.v[q] - fl.v[q];
       if (b == P) sx[q] += fr.v[q] - vfx.v[q];
       if (a == 0) sy[q] += vfy.v[q] - fd.v[q];
       if (a == P) sy[q] += fu.v[q] - vfy.v[q];
-      const T rHx = -hwa * sx[q], rHy = -hwb * sy[q];
-      T rLx = -hwa * (fr.v[q] - fl.v[q]);
-      T rLy = -hwb * (fu.v[q] - fd.v[q]);
-      if constexpr (DENSE) {  // dense volume term and graph viscosity, element-face fluxes only
-        rLx = hwa * (dvx[q] + dgx[q] + ((b == 0) ? fl.v[q] : T(0)) - ((b == P) ? fr.v[q] : T(0)));
-        rLy = hwb * (dvy[q] + dgy[q] + ((a == 0) ? fd.v[q] : T(0)) - ((a == P) ? fu.v[q] : T(0)));
-      }
-      uL[q] = vu.v[q] + dtm * (rLx + rLy);
-      out[q] = (limiter == 0) ? vu.v[q] + dtm * (rHx + rHy) : uL[q];
-      rx[q] = rHx - rLx;
-      ry[q] = rHy - rLy;
     }
+    T rHx[NC], rHy[NC], rLx[NC], rLy[NC], tq[NC];
+    v_scale<NC>(rHx, -hwa, sx);
+    v_scale<NC>(rHy, -hwb, sy);
+    if constexpr (DENSE) {  // dense volume term and graph viscosity, element-face fluxes only
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        rLx[q] = hwa * (dvx[q] + dgx[q] + ((b == 0) ? fl.v[q] : T(0)) - ((b == P) ? fr.v[q] : T(0)));
+        rLy[q] = hwb * (dvy[q] + dgy[q] + ((a == 0) ? fd.v[q] : T(0)) - ((a == P) ? fu.v[q] : T(0)));
+      }
+    } else {
+      v_sub<NC>(tq, fr.v, fl.v);
+      v_scale<NC>(rLx, -hwa, tq);
+      v_sub<NC>(tq, fu.v, fd.v);
+      v_scale<NC>(rLy, -hwb, tq);
+    }
+    v_add<NC>(tq, rLx, rLy);
+    v_fma<NC>(uL, dtm, tq, vu.v);
+    if (limiter == 0) {
+      v_add<NC>(tq, rHx, rHy);
+      v_fma<NC>(out, dtm, tq, vu.v);
+    } else {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) out[q] = uL[q];
+    }
+    v_sub<NC>(rx, rHx, rLx);
+    v_sub<NC>(ry, rHy, rLy);
     if (limiter < 2 && act) {  // high-order target or low-order update only: done
 #pragma unroll
       for (int q = 0; q < NC; ++q)
@@ -987,8 +1004,12 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
     const T axm = (b > 0) ? tmin(at, s.alpha[me - 1]) : T(0);
     const T ayp = (a < P) ? tmin(at, s.alpha[me + n]) : T(0);
     const T aym = (a > 0) ? tmin(at, s.alpha[me - n]) : T(0);
-#pragma unroll
-    for (int q = 0; q < NC; ++q) fe[q] = uL[q] + dtm * (axp * xp[q] - axm * xm[q] + ayp * yp[q] - aym * ym[q]);
+    T acc[NC];
+    v_scale<NC>(acc, axp, xp);
+    v_fma<NC>(acc, -axm, xm, acc);
+    v_fma<NC>(acc, ayp, yp, acc);
+    v_fma<NC>(acc, -aym, ym, acc);
+    v_fma<NC>(fe, dtm, acc, uL);
     if constexpr (sizeof(T) == 4) {
       if (!(fe[0] >= lo && fe[0] <= hi)) {  // rare: the rounding scale only where it is needed
         const T mag = stencil_scale<P, TX, TY, DENSE>(s, me, le, a, b, row, col) + fabs(uL[0]) +
@@ -998,8 +1019,16 @@ __device__ __forceinline__ void stage_body(TileSmem<P, TX, TY, LAW, T>& s, const
       }
     }
     if (act) {
+      T res[NC];
+      if (I.c0 == T(0)) {
 #pragma unroll
-      for (int q = 0; q < NC; ++q) I.uout[q * N + g] = (I.c0 == T(0)) ? fe[q] : I.c0 * u0[q] + I.c1 * fe[q];
+        for (int q = 0; q < NC; ++q) res[q] = fe[q];
+      } else {  // the SSP-RK3 combination c0 u^n + c1 u^FE
+        v_scale<NC>(res, I.c1, fe);
+        v_fma<NC>(res, I.c0, u0, res);
+      }
+#pragma unroll
+      for (int q = 0; q < NC; ++q) I.uout[q * N + g] = res[q];
     }
   }
   if (STATS && I.stats) {  // statistics: compiled only into the statistics kernels
