@@ -251,9 +251,24 @@ sidp_status sidp_stage(sidp_ctx* ctx, int k, double dt);
 sidp_status sidp_step(sidp_ctx* ctx, int nsteps);
 
 /* Element tile (elements per CTA along x and y) that the stage kernels use; chosen per
- * (law, p, precision) by timing the candidates at the first sidp_step (SIDP_TILE=<0..3> forces
- * one, SIDP_AUTOTUNE=0 keeps the default, SIDP_TUNE_FILE=<path> persists the choices). */
+ * (law, p, precision) by timing the candidates at the first sidp_step (SIDP_TILE=<index> forces
+ * one, SIDP_AUTOTUNE=0 keeps the default, SIDP_TUNE_FILE=<path> persists the choices).  The
+ * candidates are indices 0..3, tiles of the node kernel (one thread per node), and, for the
+ * Euler law, indices 4..5, tiles of the line kernel (one thread per element line).  Both compute
+ * the same stage update (Sec. 4 with subcell limiting); they differ in the order of the rounding
+ * of sums.  Modes other than subcell limiting without the smoothness indicator run the node
+ * kernel with tile 0. */
 sidp_status sidp_get_tile(const sidp_ctx* ctx, int* tx, int* ty);
+
+/* The candidate index of the tile in use (see sidp_get_tile): 0..3 node kernel, 4..5 line
+ * kernel.  SIDP_ERR_ARG for a null argument. */
+sidp_status sidp_get_tile_index(const sidp_ctx* ctx, int* index);
+
+/* Use tile candidate `index` (see sidp_get_tile) from now on, instead of the autotuner's choice.
+ * Index 0 is valid in every mode; the others only for subcell limiting without the smoothness
+ * indicator on a Cartesian mesh (the line kernel's indices only for the Euler law); otherwise
+ * SIDP_ERR_ARG.  SIDP_ERR_STATE between stages 1 and 3 of an explicit step. */
+sidp_status sidp_set_tile(sidp_ctx* ctx, int index);
 
 /* Enable (1) or disable (0) CUDA-graph replay in sidp_step (default 1). */
 sidp_status sidp_set_graph(sidp_ctx* ctx, int use_graph);

@@ -1,6 +1,7 @@
 // Stage and time-step kernels of the burgers law in double, degrees 1, 2, 3, 4, 5, 6, 7
 // (split into translation units so that the build runs in parallel).
 #include "sidp_curved.cuh"
+#include "sidp_lines.cuh"
 
 namespace sidp {
 SIDP_INSTANTIATE_P(LAW_BURGERS, LawBurgers, double, 1)

@@ -1,6 +1,7 @@
 // Stage and time-step kernels of the euler law in double, degrees 4, 5
 // (split into translation units so that the build runs in parallel).
 #include "sidp_curved.cuh"
+#include "sidp_lines.cuh"
 
 namespace sidp {
 SIDP_INSTANTIATE_P(LAW_EULER, LawEuler, double, 4)

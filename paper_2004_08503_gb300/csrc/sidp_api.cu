@@ -138,7 +138,7 @@ struct sidp_ctx {
   long long steps = 0;
   cudaGraphExec_t graph = nullptr;
   bool graph_warm = false;
-  int tile = 0;          // index into kTiles[p]
+  int tile = 0;          // tile candidate: kTiles[p][tile] (< kNumTiles), else a line-kernel tile
   bool tuned = false;
   double xi[kMaxN], w[kMaxN], D[kMaxN * kMaxN];
   std::string err;
@@ -285,7 +285,8 @@ void tune_table_init() {
     if (FILE* fp = std::fopen(f, "r")) {
       int law, p, mixed, tile;
       while (std::fscanf(fp, "%d %d %d %d", &law, &p, &mixed, &tile) == 4)
-        if (law >= 1 && law <= 3 && p >= 1 && p <= kMaxP && (mixed == 0 || mixed == 1) && tile >= 0 && tile < kNumTiles)
+        if (law >= 1 && law <= 3 && p >= 1 && p <= kMaxP && (mixed == 0 || mixed == 1) && tile >= 0 &&
+            tile < num_tile_candidates(law))
           g_tune[law][p][mixed] = tile;
       std::fclose(fp);
     }
@@ -313,7 +314,7 @@ namespace sidp {
 int tuned_tile(int law, int p, int mixed) {
   if (const char* f = std::getenv("SIDP_TILE")) {
     const int t = std::atoi(f);
-    if (t >= 0 && t < kNumTiles) return t;
+    if (t >= 0 && t < num_tile_candidates(law)) return t;
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
   tune_table_init();
@@ -332,7 +333,7 @@ cudaError_t autotune(sidp_ctx* c) {
   if (c->cfg.limiter != 2 || c->cfg.smoothness) { c->tile = 0; return cudaSuccess; }
   if (const char* f = std::getenv("SIDP_TILE")) {
     const int t = std::atoi(f);
-    if (t >= 0 && t < kNumTiles) c->tile = t;
+    if (t >= 0 && t < num_tile_candidates(c->cfg.law)) c->tile = t;
     return cudaSuccess;
   }
   const char* off = std::getenv("SIDP_AUTOTUNE");
@@ -348,7 +349,7 @@ cudaError_t autotune(sidp_ctx* c) {
   float best = 1e30f;
   int best_t = 0;
   const int saved = c->tile;
-  for (int t = 0; t < kNumTiles && err == cudaSuccess; ++t) {
+  for (int t = 0; t < num_tile_candidates(c->cfg.law) && err == cudaSuccess; ++t) {
     c->tile = t;
     if ((err = run_dt(c, false)) != cudaSuccess) break;
     if ((err = run_stage(c, 1)) != cudaSuccess) break;  // warm-up (and kernel attributes)
@@ -853,8 +854,27 @@ sidp_status sidp_get_diag(sidp_ctx* c, sidp_diag* out) {
 
 sidp_status sidp_get_tile(const sidp_ctx* c, int* tx, int* ty) {
   if (!c) return fail(nullptr, SIDP_ERR_ARG, "null context");
-  if (tx) *tx = kTiles[c->cfg.p][c->tile].tx;
-  if (ty) *ty = kTiles[c->cfg.p][c->tile].ty;
+  if (tx) *tx = tile_shape(c->cfg.p, c->tile).tx;
+  if (ty) *ty = tile_shape(c->cfg.p, c->tile).ty;
+  return SIDP_OK;
+}
+
+sidp_status sidp_set_tile(sidp_ctx* c, int index) {
+  if (!c) return fail(c, SIDP_ERR_ARG, "null context");
+  if (index < 0 || index >= num_tile_candidates(c->cfg.law))
+    return fail(c, SIDP_ERR_ARG, "tile index out of range for this law");
+  if (index != 0 && (c->curved || c->cfg.limiter != 2 || c->cfg.smoothness || c->cfg.unsparsified))
+    return fail(c, SIDP_ERR_ARG, "only subcell limiting without the smoothness indicator on a Cartesian mesh has tile candidates");
+  if (c->stage_done != 0) return fail(c, SIDP_ERR_STATE, "an SSP-RK3 step is half done (stage 1 or 2 ran)");
+  c->tile = index;
+  c->tuned = true;
+  drop_graph(c);
+  return SIDP_OK;
+}
+
+sidp_status sidp_get_tile_index(const sidp_ctx* c, int* index) {
+  if (!c || !index) return fail(nullptr, SIDP_ERR_ARG, "null argument");
+  *index = c->tile;
   return SIDP_OK;
 }
 

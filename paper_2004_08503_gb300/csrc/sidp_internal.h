@@ -69,6 +69,25 @@ constexpr TileShape kTiles[kMaxP + 1][kNumTiles] = {
     {{1, 4}, {4, 1}, {2, 2}, {4, 2}},     // p=7: 256 / 256 / 256 / 512
 };
 
+// Element tiles of the line-parallel stage kernel (one thread per element line; Euler, subcell
+// limiting without the smoothness indicator).  Tile index kNumTiles + i selects kLineTiles[p][i].
+constexpr int kNumLineTiles = 2;
+constexpr TileShape kLineTiles[kMaxP + 1][kNumLineTiles] = {
+    {{0, 0}, {0, 0}},
+    {{16, 8}, {8, 8}},  // p=1: 256 / 128 threads
+    {{8, 8}, {10, 8}},  // p=2: 192 / 240
+    {{8, 4}, {8, 8}},   // p=3: 128 / 256
+    {{8, 4}, {6, 6}},   // p=4: 160 / 180
+    {{4, 4}, {6, 4}},   // p=5: 96 / 144
+    {{4, 4}, {4, 2}},   // p=6: 112 / 56
+    {{4, 4}, {4, 2}},   // p=7: 128 / 64
+};
+constexpr int kMaxCand = kNumTiles + kNumLineTiles;
+// Candidates of the tile autotuner for a law: the node kernel's shapes, then (Euler) the line
+// kernel's.
+inline int num_tile_candidates(int law) { return kNumTiles + (law == LAW_EULER ? kNumLineTiles : 0); }
+inline TileShape tile_shape(int p, int t) { return t < kNumTiles ? kTiles[p][t] : kLineTiles[p][t - kNumTiles]; }
+
 // Reference-element tables for one degree p, in the stage precision T.
 template <typename T>
 struct Tables {
@@ -256,11 +275,13 @@ SIDP_DECLARE_ALL(LAW_ADVECTION_VAR, float)
     }                                                                                                  \
     if (a.limiter == 3 && !bits) /* elementwise limiting: its own kernel, default tile shape */       \
       return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, true>(a, bits, s);       \
+    if (tile >= kNumTiles && !bits && a.limiter == 2 && !a.si.on) /* the line kernel (and its statistics variant) */ \
+      return LineDispatch<LAWID, P, LAWTPL<TT>, TT>::stage(tile - kNumTiles, a, a.inst.stats != nullptr, s); \
     if (a.inst.stats && !bits) /* statistics on: the statistics kernel, default tile shape */         \
       return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, false, false, true>(a, bits, s); \
     if (!bits && (a.limiter != 2 || a.si.on)) /* other modes: the general kernel, default tile shape */ \
       return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT>(a, bits, s);             \
-    switch (tile) { /* subcell limiting without the indicator (and the time step): every tile shape */ \
+    switch (tile < kNumTiles ? tile : 0) { /* subcell limiting without the indicator (and the time step): every tile shape */ \
       case 0: return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, false, false, false, true>(a, bits, s); \
       case 1: return launch_tile<P, kTiles[P][1].tx, kTiles[P][1].ty, LAWTPL<TT>, TT, false, false, false, true>(a, bits, s); \
       case 2: return launch_tile<P, kTiles[P][2].tx, kTiles[P][2].ty, LAWTPL<TT>, TT, false, false, false, true>(a, bits, s); \

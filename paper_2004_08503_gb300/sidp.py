@@ -73,6 +73,8 @@ _SIGS = {
     "sidp_step": (ctypes.c_int, [_P, ctypes.c_int]),
     "sidp_set_graph": (ctypes.c_int, [_P, ctypes.c_int]),
     "sidp_get_tile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "sidp_get_tile_index": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "sidp_set_tile": (ctypes.c_int, [_P, ctypes.c_int]),
     "sidp_set_stats": (ctypes.c_int, [_P, ctypes.c_int]),
     "sidp_set_debug": (ctypes.c_int, [_P, ctypes.c_int]),
     "sidp_get_bounds": (ctypes.c_int, [_P, _D, _D, _D, _D]),
@@ -279,6 +281,16 @@ def sidp_get_tile(ctx):
     tx, ty = ctypes.c_int(), ctypes.c_int()
     _check(load().sidp_get_tile(ctx, ctypes.byref(tx), ctypes.byref(ty)), ctx)
     return tx.value, ty.value
+
+
+def sidp_get_tile_index(ctx):
+    i = ctypes.c_int()
+    _check(load().sidp_get_tile_index(ctx, ctypes.byref(i)), ctx)
+    return i.value
+
+
+def sidp_set_tile(ctx, index):
+    _check(load().sidp_set_tile(ctx, int(index)), ctx)
 
 
 def sidp_set_graph(ctx, on):
@@ -490,3 +502,11 @@ class Solver:
 
     def synchronize(self):
         sidp_synchronize(self.ctx)
+
+    def tile(self):
+        """(tx, ty, index) of the stage kernel's tile candidate (index >= 4: the line kernel)."""
+        tx, ty = sidp_get_tile(self.ctx)
+        return tx, ty, sidp_get_tile_index(self.ctx)
+
+    def set_tile(self, index):
+        sidp_set_tile(self.ctx, index)

@@ -1,0 +1,245 @@
+"""The line-parallel stage kernel (tile candidates 4 and 5: one thread per element line, Euler,
+subcell limiting) through the C-ABI, against the FP64 oracle on seeded inputs.
+
+The same bars as the node kernel's parity tests: per stage, the conditioning-aware comparator of
+the limited update (every alpha admissible and maximal under the oracle's own constraints, the
+update rebuilt from it equal to the GPU's to 1e-12); whole steps at 1e-12 relative per field; the
+captured bounds at 1e-13.  Meshes span several tiles of the line kernel and end in ragged tiles.
+"""
+import numpy as np
+import pytest
+
+from fe_compare import euler_fe_check
+from oracle import laws, scheme
+from paper_2004_08503_gb300 import build, inputs, sidp
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+G = 1.4
+# element tiles of the line kernel, tile index 4 and 5 (kLineTiles)
+LINE_TILES = {1: [(16, 8), (8, 8)], 2: [(8, 8), (10, 8)], 3: [(8, 4), (8, 8)], 4: [(8, 4), (6, 6)],
+              5: [(4, 4), (6, 4)], 6: [(4, 4), (4, 2)], 7: [(4, 4), (4, 2)]}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    sidp.load()
+
+
+def rel(a, b):
+    a = a.reshape(b.shape[0], -1)
+    b = b.reshape(b.shape[0], -1)
+    return np.max(np.abs(a - b), axis=1) / np.maximum(np.max(np.abs(b), axis=1), 1e-300)
+
+
+def make(p, nx, ny, bc, tile, precision="fp64", cfl=0.5, domain=None):
+    if domain is None:
+        domain = (0.0, nx / max(nx, ny), 0.0, ny / max(nx, ny))
+    pb = scheme.Problem(laws.Euler(G), p, nx, ny, domain=domain, bc=bc, cfl=cfl, limiter="subcell")
+    sv = sidp.Solver(law="euler", p=p, nx=nx, ny=ny, precision=precision, domain=domain, bc=bc, cfl=cfl,
+                     limiter="subcell", gamma=G)
+    sv.set_tile(tile)
+    tx, ty, idx = sv.tile()
+    assert idx == tile and (tx, ty) == (LINE_TILES[p][tile - 4] if tile >= 4 else (tx, ty))
+    return pb, sv
+
+
+def span(p, tile):
+    """A mesh of two by two line tiles, the second ones ragged."""
+    tx, ty = LINE_TILES[p][tile - 4]
+    return tx + max(1, tx // 2 - 1), ty + max(1, ty // 2)
+
+
+@pytest.mark.parametrize("tile", [4, 5])
+@pytest.mark.parametrize("p", range(1, 8))
+def test_line_stages_fe_check(p, tile):
+    """Three forward-Euler stages (each from the oracle's stage input), four-quadrant data."""
+    nx, ny = span(p, tile)
+    bc = ("outflow",) * 4 if p % 2 else ("periodic",) * 4
+    pb, sv = make(p, nx, ny, bc, tile)
+    X, Y = pb.node_coords()
+    U0 = inputs.four_quadrant(X, Y, seed=p)
+    U0, _ = pb.ssp_rk3_step(U0)  # the limiter active away from t = 0
+    dt = pb.compute_dt(U0)
+    sv.set_debug(True)
+    cur = U0
+    for k in (1, 2, 3):
+        sv.set_state(cur.reshape(4, -1))
+        sv.stage(1, dt)
+        # four-quadrant plateaus: entropy roots and Zalesak ratios that rounding decides cover up to
+        # about 0.57 of the nodes of these small meshes (0.565 at p = 6 on 5 x 3 elements)
+        euler_fe_check(pb, cur, dt, sv.get_state(1), sv.bounds()["alpha"], max_relaxed=0.6)
+        if k == 1:
+            _, info = pb.fe_stage(cur, dt, full=True)
+            bd = sv.bounds()
+            np.testing.assert_allclose(bd["lo"], info["lo"].ravel(), rtol=1e-13, atol=1e-13)
+            np.testing.assert_allclose(bd["hi"], info["hi"].ravel(), rtol=1e-13, atol=1e-13)
+            np.testing.assert_allclose(bd["K"], info["K"].ravel(), rtol=1e-12)
+        cur = pb.stage(cur, U0, dt, k)
+
+
+@pytest.mark.parametrize("tile", [4, 5])
+def test_line_rk_combination(tile):
+    """Stages 2 and 3 (u^n read back by the kernel): c0 u^n + c1 FE(u^(k-1)) with FE from a second
+    context on the same kernel, to float64 rounding; FE itself by the comparator."""
+    p = 3
+    nx, ny = span(p, tile)
+    pb, sv = make(p, nx, ny, ("periodic",) * 4, tile)
+    _, fe = make(p, nx, ny, ("periodic",) * 4, tile)
+    X, Y = pb.node_coords()
+    U0, _ = pb.ssp_rk3_step(inputs.four_quadrant(X, Y, seed=2))
+    dt = pb.compute_dt(U0)
+    sv.set_debug(True)
+    sv.set_state(U0.reshape(4, -1))
+    sv.stage(1, dt)
+    u1 = sv.get_state(1)
+    euler_fe_check(pb, U0, dt, u1, sv.bounds()["alpha"], max_relaxed=0.6)
+    prev = u1
+    for k, (c0, c1), buf in ((2, (0.75, 0.25), 2), (3, (1.0 / 3.0, 2.0 / 3.0), 0)):
+        sv.stage(k, dt)
+        got = sv.get_state(buf)
+        fe.set_state(prev)
+        fe.stage(1, dt)
+        expect = c0 * U0.reshape(4, -1) + c1 * fe.get_state(1)
+        assert np.all(rel(got, expect) <= 1e-14), (k, rel(got, expect))
+        prev = got
+
+
+def test_line_euler_64x64_p4_steps():
+    """Euler 64x64 p=4 FP64, outflow, seeded four-quadrant data: whole steps with the device time
+    step, each from the oracle's state, at 1e-12."""
+    pb, sv = make(4, 64, 64, ("outflow",) * 4, 4)
+    X, Y = pb.node_coords()
+    U = inputs.four_quadrant(X, Y, seed=0)
+    for s in range(2):
+        sv.set_state(U.reshape(4, -1))
+        Un, dt = pb.ssp_rk3_step(U)
+        sv.step(1)
+        assert sv.tile()[2] == 4  # an explicit choice is kept (no autotuning)
+        assert np.all(rel(sv.get_state(0), Un) <= TOL), rel(sv.get_state(0), Un)
+        U = Un
+
+
+@pytest.mark.parametrize("tile", [4, 5])
+def test_line_conservation_periodic(tile):
+    p = 3
+    nx, ny = span(p, tile)
+    pb, sv = make(p, nx, ny, ("periodic",) * 4, tile)
+    X, Y = pb.node_coords()
+    sv.set_state(inputs.four_quadrant(X, Y, seed=5).reshape(4, -1))
+    m0 = np.array(sv.diag()["mass"])
+    sv.step(20)
+    m1 = np.array(sv.diag()["mass"])
+    assert np.all(np.abs(m1 - m0) <= 1e-13 * np.maximum(1.0, np.abs(m0)))
+
+
+@pytest.mark.parametrize("bc", [("wall", "outflow", "wall", "outflow"), ("wall", "wall", "periodic", "periodic")])
+def test_line_wall_stages(bc):
+    """Slip walls (Sec. 5.7) on the line kernel's halo: per-stage comparator."""
+    import test_oracle_wall as tw
+    p, tile = 3, 4
+    nx, ny = span(p, tile)
+    dom = (0.0, 1.0, 0.0, ny / nx)
+    pb, sv = make(p, nx, ny, bc, tile, domain=dom)
+    X, Y = pb.node_coords()
+    U0 = pb.law.prim_to_cons(*tw._data(X, Y))
+    dt = pb.compute_dt(U0)
+    sv.set_debug(True)
+    cur = U0
+    for k in (1, 2, 3):
+        sv.set_state(cur.reshape(4, -1))
+        sv.stage(1, dt)
+        euler_fe_check(pb, cur, dt, sv.get_state(1), sv.bounds()["alpha"])
+        cur = pb.stage(cur, U0, dt, k)
+
+
+def test_line_split_boundaries_low_order_free():
+    """Split boundaries of the double Mach reflection at t = 0.013 with the line kernel: one step
+    with the device clock against the oracle's (the comparator per stage)."""
+    p, tile = 3, 4
+    nx, ny = 12, 5
+    split = inputs.double_mach_boundaries()
+    bc = ("split", "outflow", "split", "split")
+    dom = (0.0, nx / ny, 0.0, 1.0)
+    pb = scheme.Problem(laws.Euler(G), p, nx, ny, domain=dom, bc=bc, limiter="subcell", split=split)
+    sv = sidp.Solver(law="euler", p=p, nx=nx, ny=ny, domain=dom, bc=bc, limiter="subcell", gamma=G)
+    for side, sp in split.items():
+        sv.set_split(side, sp["s0"], sp["speed"], sp["a"], sp["b"])
+    sv.set_tile(tile)
+    X, Y = pb.node_coords()
+    U0 = inputs.double_mach(X, Y)
+    pb.time = 0.013
+    sv.set_time(0.013)
+    dt = pb.compute_dt(U0)
+    sv.set_debug(True)
+    sv.set_state(U0.reshape(4, -1))
+    sv.stage(1, dt)
+    euler_fe_check(pb, U0, dt, sv.get_state(1), sv.bounds()["alpha"])
+
+
+def test_line_exact_state_vortex():
+    """Exact-state ghost traces on the line kernel's halo (the vortex order test's boundary data)."""
+    p, nel = 3, 10
+    pb0 = scheme.Problem(laws.Euler(G), p, nel, nel)
+    pos = (np.arange(nel)[:, None] + pb0.xi[None, :]) * pb0.h
+    ghost = {"W": inputs.vortex(0 * pos, pos), "E": inputs.vortex(0 * pos + 1, pos),
+             "S": inputs.vortex(pos, 0 * pos), "N": inputs.vortex(pos, 0 * pos + 1)}
+    pb = scheme.Problem(laws.Euler(G), p, nel, nel, bc=("exact",) * 4, limiter="subcell", ghost=ghost)
+    sv = sidp.Solver(law="euler", p=p, nx=nel, ny=nel, bc=("exact",) * 4, limiter="subcell", gamma=G)
+    sv.set_tile(4)
+    for s in "WESN":
+        sv.set_ghost(s, ghost[s].reshape(4, -1))
+    X, Y = pb.node_coords()
+    U = inputs.vortex(X, Y)
+    dt = pb.compute_dt(U)
+    sv.set_state(U.reshape(4, -1))
+    sv.set_debug(True)
+    sv.stage(1, dt)
+    euler_fe_check(pb, U, dt, sv.get_state(1), sv.bounds()["alpha"])
+
+
+@pytest.mark.parametrize("p,kind", [(3, "quad"), (3, "blast"), (4, "quad"), (7, "quad")])
+def test_line_mixed_invariants_and_node_kernel(p, kind):
+    """Mixed precision, 30 steps: the line kernel's statistics variant reports positive density
+    and pressure, zero density-bound violations on the stored float32 state and the entropy
+    minimum held to 1e-6; its trajectory stays close to the node kernel's and to the FP64 form's."""
+    nx, ny = span(p, 4)
+    nx, ny = 2 * nx, 2 * ny
+    res = {}
+    for name, prec, tile in (("line", "mixed", 4), ("node", "mixed", 0), ("fp64", "fp64", 0)):
+        sv = sidp.Solver(law="euler", p=p, nx=nx, ny=ny, precision=prec, bc=("outflow",) * 4, gamma=G,
+                         domain=(0.0, nx / max(nx, ny), 0.0, ny / max(nx, ny)))
+        sv.set_tile(tile)
+        sv.set_stats(True)
+        x, y = sv.node_coords()
+        U = inputs.four_quadrant(x, y, 4) if kind == "quad" else inputs.blast(x, y)
+        sv.set_state(U)
+        sv.step(30)
+        res[name] = (sv.get_state(0), sv.diag())
+        assert sv.tile()[2] == tile
+    d = res["line"][1]
+    assert d["rho_min"] > 0 and d["p_min"] > 0 and d["nonfinite"] == 0
+    assert d["max_bound_violation"] == 0.0
+    assert d["max_entropy_violation"] <= 1e-6
+    assert d["rootfind_cap_hits"] == 0
+    a = res["line"][0]
+    for other in ("node", "fp64"):
+        b = res[other][0]
+        l1 = np.abs(a - b).mean(axis=1) / np.abs(b).mean(axis=1)
+        assert np.all(l1 < 1e-4), (other, l1)
+
+
+def test_set_tile_rejections():
+    sv = sidp.Solver(law="euler", p=3, nx=4, ny=4, limiter="lo")
+    with pytest.raises(Exception):
+        sv.set_tile(4)  # line tiles: subcell limiting only
+    sv.set_tile(0)
+    sb = sidp.Solver(law="burgers", p=3, nx=4, ny=4)
+    with pytest.raises(Exception):
+        sb.set_tile(4)  # no line kernel for the scalar laws
+    se = sidp.Solver(law="euler", p=3, nx=4, ny=4)
+    with pytest.raises(Exception):
+        se.set_tile(6)
+    se.set_tile(5)
+    assert se.tile() == (8, 8, 5)
