@@ -33,9 +33,21 @@ struct LineGeom {
   static constexpr int NL = NE * n;  // element lines: the working threads
   static constexpr int THREADS = ((NL + 31) / 32) * 32;
   static constexpr int NX = EX * n, NY = EY * n;
-  // element stride in shared memory: padded so that the column accesses of a warp (lanes of
-  // consecutive elements reading the same row) fall in distinct banks
-  static constexpr int SE = NN + (NN == 4 ? 2 : NN == 16 ? 4 : NN == 64 ? 8 : 0);
+  // Shared-memory layout of an element's nodes.  p = 3: the rows of element le are rotated by
+  // (le / 2) mod 4, so that both a warp's row accesses (16-byte vectors of 8 consecutive
+  // elements' rows) and its column accesses (one value per lane of the same row of 8 elements)
+  // fall in distinct banks.  Other degrees: rows in order, the element stride padded against the
+  // column accesses' conflicts.
+  static constexpr bool SWZ = (n == 4);
+  static constexpr int SE = SWZ ? NN : NN + (NN == 4 ? 2 : NN == 64 ? 8 : 0);
+  // slot of node (a, 0) of element le
+  __device__ __forceinline__ static int rs(int le, int a) {
+    if constexpr (SWZ) return le * SE + n * ((a + (le >> 1)) & 3);
+    else return le * SE + n * a;
+  }
+  // a warp holds whole tile rows of elements: the west and east neighbours of a row come from the
+  // adjacent lanes' registers
+  static constexpr bool XSHFL = (EX * n == 32);
   static constexpr int NTP = ((NE * SE + 3) / 4) * 4;
   static constexpr int NH = 2 * NX + 2 * NY;  // halo slots: W[NY], E[NY], S[NX], N[NX]
   static constexpr int hW = NTP, hE = NTP + NY, hS = NTP + 2 * NY, hN = NTP + 2 * NY + NX;
@@ -162,6 +174,25 @@ __device__ __forceinline__ void st_node(S& s, int slot, const T* uu, const typen
   if constexpr (LAW::kEntropy) s.sig[slot] = sg;
 }
 
+// dst = src of lane (lane + delta) (all 32 lanes call it; lanes whose source is outside the warp
+// get an unspecified node and overwrite it)
+template <class LAW, typename T>
+__device__ __forceinline__ void shfl_node(const LNode<LAW, T>& src, LNode<LAW, T>& dst, int delta) {
+  constexpr int NA = AuxWords<LAW, T>::value;
+  auto sh = [&](T v) {
+    return delta > 0 ? __shfl_down_sync(0xffffffffu, v, (unsigned)delta) : __shfl_up_sync(0xffffffffu, v, (unsigned)(-delta));
+  };
+#pragma unroll
+  for (int q = 0; q < LAW::NC; ++q) dst.u[q] = sh(src.u[q]);
+  if constexpr (NA > 0) {
+    const T* as = reinterpret_cast<const T*>(&src.ax);
+    T* ad = reinterpret_cast<T*>(&dst.ax);
+#pragma unroll
+    for (int k = 0; k < NA; ++k) ad[k] = sh(as[k]);
+  }
+  dst.s = LAW::kEntropy ? sh(src.s) : T(0);
+}
+
 template <class LAW, typename T>
 __device__ __forceinline__ void node_aux(const T* uu, T x, T y, typename LAW::Aux& ax, const LawParamsT<T>& lp) {
   if constexpr (HasPosition<LAW>::value) LAW::aux_at(uu, x, y, ax, lp);
@@ -252,16 +283,16 @@ struct LineNbr {
   using G = LineGeom<P, EX, EY>;
   static constexpr int n = P + 1;
   __device__ __forceinline__ static int west(int le, int tx, int ty, int j) {
-    return (tx > 0) ? (le - 1) * G::SE + j * n + P : G::hW + ty * n + j;
+    return (tx > 0) ? G::rs(le - 1, j) + P : G::hW + ty * n + j;
   }
   __device__ __forceinline__ static int east(int le, int tx, int ty, int j) {
-    return (tx < EX - 1) ? (le + 1) * G::SE + j * n : G::hE + ty * n + j;
+    return (tx < EX - 1) ? G::rs(le + 1, j) : G::hE + ty * n + j;
   }
   __device__ __forceinline__ static int south(int le, int tx, int ty, int j) {
-    return (ty > 0) ? (le - EX) * G::SE + P * n + j : G::hS + tx * n + j;
+    return (ty > 0) ? G::rs(le - EX, P) + j : G::hS + tx * n + j;
   }
   __device__ __forceinline__ static int north(int le, int tx, int ty, int j) {
-    return (ty < EY - 1) ? (le + EX) * G::SE + j : G::hN + tx * n + j;
+    return (ty < EY - 1) ? G::rs(le + EX, 0) + j : G::hN + tx * n + j;
   }
 };
 
@@ -272,12 +303,11 @@ __device__ __forceinline__ auto line_stencil_scale(const S& s, int le, int tx, i
   using G = LineGeom<P, EX, EY>;
   using N4 = LineNbr<P, EX, EY>;
   constexpr int n = P + 1;
-  const int sb = le * G::SE;
-  const int me = sb + j * n + b;
+  const int me = G::rs(le, j) + b;
   const int l = (b > 0) ? me - 1 : N4::west(le, tx, ty, j);
   const int r = (b < P) ? me + 1 : N4::east(le, tx, ty, j);
-  const int d = (j > 0) ? me - n : N4::south(le, tx, ty, b);
-  const int u = (j < P) ? me + n : N4::north(le, tx, ty, b);
+  const int d = (j > 0) ? G::rs(le, j - 1) + b : N4::south(le, tx, ty, b);
+  const int u = (j < P) ? G::rs(le, j + 1) + b : N4::north(le, tx, ty, b);
   auto S0 = tmax(tmax(fabs(s.u[0][l]), fabs(s.u[0][r])), tmax(fabs(s.u[0][d]), fabs(s.u[0][u])));
   return fabs(s.u[0][me]) + decltype(S0)(2) * S0;
 }
@@ -296,12 +326,12 @@ __device__ __forceinline__ double line_entropy_violation64(const S& s, int le, i
     for (int q = 0; q < 4; ++q) uu[q] = s.u[q][slot];
     return (double)LAW::rhoe(uu) * (double)powf(uu[0], -lp.gamma);
   };
-  const int me = le * G::SE + j * n + b;
+  const int me = G::rs(le, j) + b;
   double K = sig(me);
   K = fmin(K, sig((b > 0) ? me - 1 : N4::west(le, tx, ty, j)));
   K = fmin(K, sig((b < P) ? me + 1 : N4::east(le, tx, ty, j)));
-  K = fmin(K, sig((j > 0) ? me - n : N4::south(le, tx, ty, b)));
-  K = fmin(K, sig((j < P) ? me + n : N4::north(le, tx, ty, b)));
+  K = fmin(K, sig((j > 0) ? G::rs(le, j - 1) + b : N4::south(le, tx, ty, b)));
+  K = fmin(K, sig((j < P) ? G::rs(le, j + 1) + b : N4::north(le, tx, ty, b)));
   if (!((double)fe[0] > 0.0)) return 1.0;
   const double sf = (double)LAW::rhoe(fe) * (double)powf(fe[0], -lp.gamma);
   return fmax(0.0, 1.0 - sf / K);
@@ -324,7 +354,7 @@ __device__ __forceinline__ void stage_lines_body(LineSmem<P, EX, EY, LAW, T>& s,
   const bool act = live && ex < I.nx && ey < I.ny;
   const long long N = I.N;
   const long long grow = act ? ((long long)ey * I.nx + ex) * NN + j * n : 0;  // global index of node (j, 0)
-  const int sb = le * G::SE, srow = sb + j * n;
+  const int srow = G::rs(le, j);
   const T h = I.hT;
   const T wj = pick<n>(tab.w, j);
   const T xij = pick<n>(tab.xi, j);
@@ -392,14 +422,14 @@ __device__ __forceinline__ void stage_lines_body(LineSmem<P, EX, EY, LAW, T>& s,
   if (live) {
     Nd nd[n], lft, rgt;
 #pragma unroll
-    for (int a = 0; a < n; ++a) ld_node<LAW, T>(s, sb + a * n + j, nd[a]);
+    for (int a = 0; a < n; ++a) ld_node<LAW, T>(s, G::rs(le, a) + j, nd[a]);
     ld_node<LAW, T>(s, N4::south(le, tx, ty, j), lft);
     ld_node<LAW, T>(s, N4::north(le, tx, ty, j), rgt);
     T rl[n][NC], lo[n], hi[n], K[n], S[n][NC];
     line_residuals<P, 1, LAW, T>(tab, lp, nd, lft, rgt, h * wj, rl, lo, hi, K, S);
 #pragma unroll
     for (int a = 0; a < n; ++a) {
-      const int sl = sb + a * n + j;
+      const int sl = G::rs(le, a) + j;
 #pragma unroll
       for (int q = 0; q < NC; ++q) s.rly[q][sl] = rl[a][q];
       if (a < P) {
@@ -444,8 +474,17 @@ __device__ __forceinline__ void stage_lines_body(LineSmem<P, EX, EY, LAW, T>& s,
         for (int b = 0; b < n; ++b) nd[b].s = T(0);
       }
     }
-    ld_node<LAW, T>(s, N4::west(le, tx, ty, j), lft);
-    ld_node<LAW, T>(s, N4::east(le, tx, ty, j), rgt);
+    if constexpr (G::XSHFL) {
+      // the row's west neighbour is node P of the same row n lanes down, its east neighbour node 0
+      // n lanes up; the tile's edge columns read the halo
+      shfl_node<LAW, T>(nd[P], lft, -n);
+      shfl_node<LAW, T>(nd[0], rgt, n);
+      if (tx == 0) ld_node<LAW, T>(s, G::hW + ty * n + j, lft);
+      if (tx == EX - 1) ld_node<LAW, T>(s, G::hE + ty * n + j, rgt);
+    } else {
+      ld_node<LAW, T>(s, N4::west(le, tx, ty, j), lft);
+      ld_node<LAW, T>(s, N4::east(le, tx, ty, j), rgt);
+    }
     line_residuals<P, 0, LAW, T>(tab, lp, nd, lft, rgt, h * wj, rlx, lox, hix, Kx, Sx);
   }
   __syncthreads();
@@ -476,7 +515,7 @@ __device__ __forceinline__ void stage_lines_body(LineSmem<P, EX, EY, LAW, T>& s,
 #pragma unroll
       for (int b = 0; b < n; ++b) yp[b][q] = v[b];
       if (j > 0) {
-        ld_line<n>(&s.sy[q][srow - n], v);
+        ld_line<n>(&s.sy[q][G::rs(le, j > 0 ? j - 1 : 0)], v);
       } else {
 #pragma unroll
         for (int b = 0; b < n; ++b) v[b] = T(0);
@@ -540,8 +579,8 @@ __device__ __forceinline__ void stage_lines_body(LineSmem<P, EX, EY, LAW, T>& s,
   int nudged = 0;
   if (live) {
     T aup[n], adn[n];
-    if (j < P) ld_line<n>(&s.alpha[srow + n], aup);
-    if (j > 0) ld_line<n>(&s.alpha[srow - n], adn);
+    if (j < P) ld_line<n>(&s.alpha[G::rs(le, j + 1)], aup);
+    if (j > 0) ld_line<n>(&s.alpha[G::rs(le, j - 1)], adn);
     T res[NC][n];
 #pragma unroll
     for (int b = 0; b < n; ++b) {
