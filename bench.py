@@ -34,15 +34,22 @@ sys.path.insert(0, ROOT)
 
 METRIC = "node-updates/s per RK stage (Euler 2D p=3), mixed vs FP64; % HBM roofline"
 UNIT = "node-updates/s"
-# dram__bytes (read + write) per node and stage launch, averaged over the three stages, measured by
-# ncu on the 768x768 p=3 blast (the second step's stages 1-3 with the tile shape 2x8).  The
-# counters belong to the stage kernel as it was captured; a changed kernel needs a new capture.
-STAGE_DRAM_BYTES_PER_NODE = 39.3
-# Executed FP32 flops (2 x FFMA + FADD + FMUL) and warp instructions per node of stages 1, 2, 3
-# from the same capture: the two other ceilings of the stage kernel, reported beside the HBM
-# roofline.
-STAGE_FP32_FLOP_PER_NODE = (363.9, 371.9, 371.9)
-STAGE_WARP_INSTR_PER_NODE = (27.2, 27.2, 27.2)
+# Counters of the two mixed-precision stage kernels (the library's tile autotuner picks one of
+# them), from ncu captures of the 768x768 p=3 blast (stages 1-3 of one step): DRAM bytes (read +
+# write) per node and launch averaged over the three stages, executed FP32 flops (2 x FFMA + FADD +
+# FMUL) and warp instructions per node of stages 1, 2, 3.  "current" is False once the kernel has
+# changed since its capture: its traffic is then reported as null.
+STAGE_COUNTERS = {
+    "node": {"kernel": "k_stage<3, TX, TY, LawEuler<float>, float, subcell>", "current": False,
+             "dram_bytes_per_node": 39.3, "fp32_flop_per_node": (363.9, 371.9, 371.9),
+             "warp_instr_per_node": (27.2, 27.2, 27.2)},
+    # the line kernel issues paired float32 operations (fma/add/mul on register pairs), which the
+    # thread-level FFMA/FADD/FMUL counters do not count: no FP32 flop figure; its FMA pipe was
+    # active 36.5% of the cycles of stage 2 in the capture
+    "line": {"kernel": "k_stage_lines<3, TX, TY, LawEuler<float>, float>", "current": True,
+             "dram_bytes_per_node": 39.2, "fp32_flop_per_node": None,
+             "warp_instr_per_node": (16.31, 16.30, 16.31)},
+}
 # The float64 stage kernel's executed FP64 flops per node (2 x DFMA + DADD + DMUL), stages 1-3,
 # from an ncu capture of the same workload in float64: its FP64-pipe roofline.
 FP64_STAGE_FLOP_PER_NODE = (1198.0, 1197.6, 1197.8)
@@ -153,8 +160,15 @@ def whole_job_rate(units_per_rank, world, seconds):
     return units_per_rank * world / seconds
 
 
+# untimed steps before the warm-up: the library's tile autotuner times its candidates at the first
+# step and once more at step 10 (past the workload's initial transient)
+SETTLE_STEPS = 10
+
+
 def time_steps(torch, sv, stream, steps, warmup, dist=None, clocks_gpu=None):
-    """Graph-replayed steps; returns (max-over-ranks seconds, clock summary)."""
+    """Graph-replayed steps after SETTLE_STEPS untimed steps and `warmup` more; returns
+    (max-over-ranks seconds, clock summary)."""
+    sv.step(SETTLE_STEPS)
     sv.step(warmup)
     sv.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -176,23 +190,28 @@ def time_steps(torch, sv, stream, steps, warmup, dist=None, clocks_gpu=None):
     return sec, (clk.summary() if clk else None)
 
 
-def other_ceilings(nodes, kt, clk, fp32_peak):
+def other_ceilings(nodes, kt, clk, fp32_peak, ctr):
     """FP32 pipe (against the measured FMA throughput) and instruction-issue (nominal: 4
-    schedulers per SM at the sampled SM clock) fractions of the stage kernel."""
+    schedulers per SM at the sampled SM clock) fractions of the stage kernel (counters `ctr`)."""
     mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz")
-    if not mhz or not all(kt):
+    if not mhz or not all(kt) or not ctr["current"]:
         return None
     hz = 1e6 * float(mhz)
-    flops = sum(f * nodes for f in STAGE_FP32_FLOP_PER_NODE) / sum(kt)
-    issue = sum(w * nodes for w in STAGE_WARP_INSTR_PER_NODE) / sum(kt)
-    issue_peak = SMS * SCHEDULERS_PER_SM * hz
-    return {"sm_mhz": float(mhz),
-            "fp32": {"achieved": flops / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
-                     "frac": flops / fp32_peak, "flop_per_node": list(STAGE_FP32_FLOP_PER_NODE),
-                     "peak_kind": "measured (sidp_fma_peak, float32)"},
-            "issue": {"achieved": issue / 1e12, "peak": issue_peak / 1e12, "unit": "T warp-instr/s",
-                      "frac": issue / issue_peak, "warp_instr_per_node": list(STAGE_WARP_INSTR_PER_NODE),
-                      "peak_kind": "nominal at the sampled clock"}}
+    out = {"sm_mhz": float(mhz)}
+    if ctr["fp32_flop_per_node"] is not None:
+        fl = ctr["fp32_flop_per_node"]
+        flops = sum(f * nodes for f in fl) / sum(kt)
+        out["fp32"] = {"achieved": flops / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                       "frac": flops / fp32_peak, "flop_per_node": list(fl),
+                       "peak_kind": "measured (sidp_fma_peak, float32)"}
+    if ctr["warp_instr_per_node"] is not None:
+        wi = ctr["warp_instr_per_node"]
+        issue = sum(w * nodes for w in wi) / sum(kt)
+        issue_peak = SMS * SCHEDULERS_PER_SM * hz
+        out["issue"] = {"achieved": issue / 1e12, "peak": issue_peak / 1e12, "unit": "T warp-instr/s",
+                        "frac": issue / issue_peak, "warp_instr_per_node": list(wi),
+                        "peak_kind": "nominal at the sampled clock"}
+    return out
 
 
 def stage_kernel_times(torch, sv, stream, reps):
@@ -594,9 +613,12 @@ def main():
     kt = stage_kernel_times(torch, sv, stream, reps=20)
     s = 4
     bytes_stage = [2 * 4 * s * nodes, 3 * 4 * s * nodes, 3 * 4 * s * nodes]
-    # DRAM traffic of the stage kernel per launch (average over stages 1-3), from one ncu capture
-    # of the 768x768 case scaled to this launch by nodes
-    traffic = STAGE_DRAM_BYTES_PER_NODE * nodes
+    # the stage kernel the autotuner chose, and its DRAM traffic per launch (average over stages
+    # 1-3) from one ncu capture of the 768x768 case scaled to this launch by nodes
+    tx, ty, tidx = sv.tile()
+    ctr = STAGE_COUNTERS["line" if tidx >= 4 else "node"]
+    kname = ctr["kernel"].replace("TX", str(tx)).replace("TY", str(ty))
+    traffic = ctr["dram_bytes_per_node"] * nodes if (ctr["current"] and ctr["dram_bytes_per_node"]) else None
     ach = sum(bytes_stage) / sum(kt) / 1e9
     # whole step on the per-node figure 3 * nc * s bytes per node per stage (dt pass included)
     step_gbs = 3 * 4 * s * nodes * 3 * args.steps / sec / 1e9
@@ -651,10 +673,10 @@ def main():
                            "l2": "state >= 151 MB per buffer > L2 (no flush needed)",
                            "parallelism": "independent replica per GPU"},
                 "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                             "traffic": traffic, "kernel": "k_stage<3, LawEuler<float>, float>",
+                             "traffic": traffic, "kernel": kname, "tile_index": tidx,
                              "stage_ms": [1e3 * t for t in kt], "peak_kind": peak_kind,
                              "whole_step_gbs": step_gbs, "whole_step_frac": step_gbs / hbm,
-                             "other_ceilings": other_ceilings(nodes, kt, clk, fp32_peak)},
+                             "other_ceilings": other_ceilings(nodes, kt, clk, fp32_peak, ctr)},
                 "fp64": fp64, "curved": curved, "batched": batched, "invariants": diag_stats, "accuracy": accuracy, "dmr": dmr,
                 "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": 5 * args.steps}

@@ -251,8 +251,11 @@ sidp_status sidp_stage(sidp_ctx* ctx, int k, double dt);
 sidp_status sidp_step(sidp_ctx* ctx, int nsteps);
 
 /* Element tile (elements per CTA along x and y) that the stage kernels use; chosen per
- * (law, p, precision) by timing the candidates at the first sidp_step (SIDP_TILE=<index> forces
- * one, SIDP_AUTOTUNE=0 keeps the default, SIDP_TUNE_FILE=<path> persists the choices).  The
+ * (law, p, precision) by timing the candidates at the first sidp_step and once more when the
+ * context has taken 10 steps (the first steps of a flow, such as a blast's initial transient,
+ * can favour another tile than the rest of the run; that second pass synchronizes the stream
+ * once, inside the sidp_step call that reaches step 10).  SIDP_TILE=<index> forces one,
+ * SIDP_AUTOTUNE=0 keeps the default, SIDP_TUNE_FILE=<path> persists the settled choices.  The
  * candidates are indices 0..3, tiles of the node kernel (one thread per node), and, for the
  * Euler law, indices 4..5, tiles of the line kernel (one thread per element line).  Both compute
  * the same stage update (Sec. 4 with subcell limiting); they differ in the order of the rounding

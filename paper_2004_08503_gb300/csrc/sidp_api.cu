@@ -140,6 +140,8 @@ struct sidp_ctx {
   bool graph_warm = false;
   int tile = 0;          // tile candidate: kTiles[p][tile] (< kNumTiles), else a line-kernel tile
   bool tuned = false;
+  bool settle = false;      // a second autotuner pass is due at settle_at steps
+  long long settle_at = 0;
   double xi[kMaxN], w[kMaxN], D[kMaxN * kMaxN];
   std::string err;
 };
@@ -275,19 +277,27 @@ cudaError_t run_step(sidp_ctx* c) {
 // the table ("law p precision tile" lines).
 std::mutex g_tune_mu;
 int g_tune[LAW_ADVECTION_VAR + 1][kMaxP + 1][2];
+bool g_settled[LAW_ADVECTION_VAR + 1][kMaxP + 1][2];  // chosen by the second pass (or loaded from a file)
 bool g_tune_init = false;
+// The first steps of a flow (a blast's initial transient, say) can favour another tile than the
+// rest of the run: the autotuner times the candidates at the first step and once more at this step.
+constexpr long long kSettleSteps = 10;
 
 void tune_table_init() {
   if (g_tune_init) return;
   for (auto& a : g_tune)
     for (auto& b : a) b[0] = b[1] = -1;
+  for (auto& a : g_settled)
+    for (auto& b : a) b[0] = b[1] = false;
   if (const char* f = std::getenv("SIDP_TUNE_FILE")) {
     if (FILE* fp = std::fopen(f, "r")) {
       int law, p, mixed, tile;
       while (std::fscanf(fp, "%d %d %d %d", &law, &p, &mixed, &tile) == 4)
         if (law >= 1 && law <= 3 && p >= 1 && p <= kMaxP && (mixed == 0 || mixed == 1) && tile >= 0 &&
-            tile < num_tile_candidates(law))
+            tile < num_tile_candidates(law)) {
           g_tune[law][p][mixed] = tile;
+          g_settled[law][p][mixed] = true;
+        }
       std::fclose(fp);
     }
   }
@@ -325,9 +335,12 @@ int tuned_tile(int law, int p, int mixed) {
 
 namespace {
 
-cudaError_t autotune(sidp_ctx* c) {
-  if (c->tuned) return cudaSuccess;
+// second: the second pass (at kSettleSteps steps), which times the candidates again whatever the
+// table holds and marks the choice settled.
+cudaError_t autotune(sidp_ctx* c, bool second = false) {
+  if (c->tuned && !second) return cudaSuccess;
   c->tuned = true;
+  c->settle = false;
   // only subcell limiting without the smoothness indicator has a stage kernel for every shape;
   // the other modes run the default one
   if (c->cfg.limiter != 2 || c->cfg.smoothness) { c->tile = 0; return cudaSuccess; }
@@ -341,7 +354,12 @@ cudaError_t autotune(sidp_ctx* c) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   tune_table_init();
   int& slot = g_tune[c->cfg.law][c->cfg.p][c->mixed ? 1 : 0];
-  if (slot >= 0) { c->tile = slot; return cudaSuccess; }
+  bool& settled = g_settled[c->cfg.law][c->cfg.p][c->mixed ? 1 : 0];
+  if (slot >= 0 && (settled || !second)) {
+    c->tile = slot;
+    if (!settled) { c->settle = true; c->settle_at = c->steps + kSettleSteps; }
+    return cudaSuccess;
+  }
   cudaEvent_t e0, e1;
   cudaError_t err = cudaEventCreate(&e0);
   if (err != cudaSuccess) return err;
@@ -366,7 +384,9 @@ cudaError_t autotune(sidp_ctx* c) {
   if (err != cudaSuccess) { c->tile = saved; return err; }
   c->tile = best_t;
   slot = best_t;
-  tune_table_store();
+  settled = second;
+  if (!second) { c->settle = true; c->settle_at = c->steps + kSettleSteps; }
+  if (second) tune_table_store();
   return cudaSuccess;
 }
 
@@ -689,6 +709,7 @@ sidp_status sidp_set_geometry(sidp_ctx* c, const double* x, const double* y) try
   c->hy.assign(y, y + c->N);
   c->curved = true;
   c->tuned = true;  // one kernel shape on curved meshes: nothing to tune
+  c->settle = false;
   c->tile = 0;
   drop_graph(c);
   return SIDP_OK;
@@ -740,6 +761,18 @@ sidp_status sidp_step(sidp_ctx* c, int nsteps) {
   if (nsteps > 0 && !c->tuned) {
     drop_graph(c);
     CUDA_TRY(c, autotune(c));
+  }
+  if (nsteps > 0 && c->settle) {
+    if (c->steps < c->settle_at && c->steps + nsteps > c->settle_at) {  // the second pass falls inside
+      const int k1 = (int)(c->settle_at - c->steps);
+      const sidp_status st = sidp_step(c, k1);
+      return st != SIDP_OK ? st : sidp_step(c, nsteps - k1);
+    }
+    if (c->steps >= c->settle_at) {
+      drop_graph(c);
+      c->graph_warm = false;
+      CUDA_TRY(c, autotune(c, true));
+    }
   }
   if (!c->use_graph || !c->graph_warm) {
     // first step eagerly: sets kernel attributes outside any capture
@@ -868,6 +901,7 @@ sidp_status sidp_set_tile(sidp_ctx* c, int index) {
   if (c->stage_done != 0) return fail(c, SIDP_ERR_STATE, "an SSP-RK3 step is half done (stage 1 or 2 ran)");
   c->tile = index;
   c->tuned = true;
+  c->settle = false;
   drop_graph(c);
   return SIDP_OK;
 }

@@ -54,8 +54,8 @@ struct Group {
   int ntasks = 0;
   // the group's task tables for every tile shape (subcell limiting without the smoothness
   // indicator: the batch autotuner chooses among them at the first step)
-  int2* d_tasks_t[kNumTiles] = {nullptr, nullptr, nullptr, nullptr};
-  int ntasks_t[kNumTiles] = {0, 0, 0, 0};
+  int2* d_tasks_t[kMaxCand] = {};
+  int ntasks_t[kMaxCand] = {};
 };
 
 thread_local std::string g_batch_err;
@@ -195,9 +195,14 @@ template <typename T>
 cudaError_t launch_group(sidp_batch* b, int gi, int k, cudaStream_t st, bool timed = false) {
   {
     const Group& gr = b->groups[gi];
-    // the statistics and general stage kernels exist in the default shape only: their launches take
-    // the group's default-shape task table
-    const bool default_shape = k > 0 && ((b->stats_on && !timed) || b->limiter != 2 || b->cfgs[0].smoothness);
+    // the general stage kernels and the node kernel's statistics variant exist in the default shape
+    // only: their launches take the group's default-shape task table; the line kernel has its own
+    // statistics variant; the time step runs the node-kernel machinery (default shape with a line
+    // tile)
+    const bool line = gr.tile >= kNumTiles;
+    const bool default_shape = (k > 0 && (b->limiter != 2 || b->cfgs[0].smoothness ||
+                                          (b->stats_on && !timed && !line))) ||
+                               (k == 0 && line);
     BatchLaunch<T> bl;
     std::memset(&bl, 0, sizeof(bl));
     bl.insts = static_cast<const Instance<T>*>(b->d_inst[k]);
@@ -307,10 +312,10 @@ cudaError_t build_groups(sidp_batch* b) {
   std::map<int, int> keep;
   for (Group& g : b->groups) {
     if (!g.curved) keep[g.p] = g.tile;
-    for (int t = 0; t < kNumTiles; ++t) cudaFree(g.d_tasks_t[t]);
+    for (int t = 0; t < kMaxCand; ++t) cudaFree(g.d_tasks_t[t]);
   }
   b->groups.clear();
-  std::map<std::pair<int, int>, std::vector<int2>> tasks[kNumTiles];  // per tile shape: (curved, p) -> tasks
+  std::map<std::pair<int, int>, std::vector<int2>> tasks[kMaxCand];  // per tile shape: (curved, p) -> tasks
   for (int i = 0; i < b->n; ++i) {
     const sidp_config& c = b->cfgs[i];
     if (b->d_geo[i]) {
@@ -319,8 +324,8 @@ cudaError_t build_groups(sidp_batch* b) {
       for (long long k = 0; k < nb; ++k) tasks[0][{1, c.p}].push_back(make_int2(i, (int)k));
       continue;
     }
-    for (int tile = 0; tile < (b->any_shape ? kNumTiles : 1); ++tile) {
-      const TileShape ts = kTiles[c.p][tile];
+    for (int tile = 0; tile < (b->any_shape ? num_tile_candidates(b->law) : 1); ++tile) {
+      const TileShape ts = tile_shape(c.p, tile);
       const long long ntiles = (long long)((c.nx + ts.tx - 1) / ts.tx) * ((c.ny + ts.ty - 1) / ts.ty);
       for (long long t = 0; t < ntiles; ++t) tasks[tile][{0, c.p}].push_back(make_int2(i, (int)t));
     }
@@ -332,7 +337,7 @@ cudaError_t build_groups(sidp_batch* b) {
     g.p = kv.first.second;
     b->groups.push_back(g);
     Group& gr = b->groups.back();
-    const int tables = (!gr.curved && b->any_shape) ? kNumTiles : 1;
+    const int tables = (!gr.curved && b->any_shape) ? num_tile_candidates(b->law) : 1;
     for (int tile = 0; tile < tables; ++tile) {
       const std::vector<int2>& v = tasks[tile][kv.first];
       gr.ntasks_t[tile] = (int)v.size();
@@ -379,7 +384,14 @@ cudaError_t tune_batch(sidp_batch* b) {
     if (g.curved) continue;  // one kernel shape on curved meshes
     float best = 1e30f;
     int best_t = g.tile;
-    for (int t = 0; t < kNumTiles && e == cudaSuccess; ++t) {
+    // the line kernel's tiles are candidates only for groups of large instances: on the meshes of
+    // up to a few hundred thousand nodes that batches hold, its fewer and longer CTAs measured
+    // slower over whole steps than the node kernel, although a lone stage 1 can time faster
+    long long gn = 0, gc = 0;
+    for (int i = 0; i < b->n; ++i)
+      if (!b->d_geo[i] && b->cfgs[i].p == g.p) { gn += b->N[i]; ++gc; }
+    const int ncand = (gc > 0 && gn / gc >= kLineMinNodes) ? num_tile_candidates(b->law) : kNumTiles;
+    for (int t = 0; t < ncand && e == cudaSuccess; ++t) {
       g.tile = t;
       g.d_tasks = g.d_tasks_t[t];
       g.ntasks = g.ntasks_t[t];
@@ -529,7 +541,7 @@ sidp_status sidp_batch_destroy(sidp_batch* b) {
   for (int k = 0; k < 3; ++k) cudaFree(b->d_u[k]);
   for (int k = 0; k < 4; ++k) cudaFree(b->d_inst[k]);
   for (auto& g : b->groups)
-    for (int t = 0; t < kNumTiles; ++t) cudaFree(g.d_tasks_t[t]);
+    for (int t = 0; t < kMaxCand; ++t) cudaFree(g.d_tasks_t[t]);
   cudaFree(b->d_all_tasks);
   cudaFree(b->d_tabs);
   cudaFree(b->d_dt);

@@ -83,6 +83,9 @@ constexpr TileShape kLineTiles[kMaxP + 1][kNumLineTiles] = {
     {{4, 4}, {4, 2}},   // p=7: 128 / 64
 };
 constexpr int kMaxCand = kNumTiles + kNumLineTiles;
+// Batches: the smallest mean instance size (nodes) of a degree group whose tuning includes the line
+// kernel's tiles.
+constexpr long long kLineMinNodes = 1LL << 21;
 // Candidates of the tile autotuner for a law: the node kernel's shapes, then (Euler) the line
 // kernel's.
 inline int num_tile_candidates(int law) { return kNumTiles + (law == LAW_EULER ? kNumLineTiles : 0); }
@@ -293,13 +296,15 @@ SIDP_DECLARE_ALL(LAW_ADVECTION_VAR, float)
   cudaError_t launch_batch_p<LAWID, TT, P>(int tile, const BatchLaunch<TT>& b, bool dt, cudaStream_t s) { \
     if (b.curved) /* curved meshes: their own kernels */                                              \
       return launch_curved_batch<P, LAWTPL<TT>, TT>(b, dt, s);                                         \
+    if (tile >= kNumTiles && !dt && b.limiter == 2 && !b.si.on) /* the line kernel */                 \
+      return LineDispatch<LAWID, P, LAWTPL<TT>, TT>::batch(tile - kNumTiles, b, b.stats != 0, s);      \
     if (b.limiter == 3 && !dt)                                                                         \
       return launch_batch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, true>(b, dt, s);  \
     if (b.stats && !dt)                                                                                \
       return launch_batch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, false, true>(b, dt, s); \
     if (!dt && (b.limiter != 2 || b.si.on))                                                            \
       return launch_batch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT>(b, dt, s);         \
-    switch (tile) {                                                                                    \
+    switch (tile < kNumTiles ? tile : 0) {                                                             \
       case 0: return launch_batch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, false, false, true>(b, dt, s); \
       case 1: return launch_batch_tile<P, kTiles[P][1].tx, kTiles[P][1].ty, LAWTPL<TT>, TT, false, false, true>(b, dt, s); \
       case 2: return launch_batch_tile<P, kTiles[P][2].tx, kTiles[P][2].ty, LAWTPL<TT>, TT, false, false, true>(b, dt, s); \

@@ -419,6 +419,28 @@ __device__ T entropy_limit(const T* uL, T K, const T* xp, const T* xm, const T* 
   return t;
 }
 
+// True when every candidate u^L + tcap w_c is certainly admissible (rho > 0 and psi_K >= 0 by the
+// cheap certified test, which implies psi_K >= min(0, psi_K(u^L))), or tcap <= 0: then
+// entropy_limit returns tcap unchanged.  False: entropy_limit must be evaluated.
+template <class LAW, typename T>
+__device__ __forceinline__ bool entropy_certain(const T* uL, T K, const T* xp, const T* xm, const T* yp, const T* ym,
+                                                T sc, T tcap, const LawParamsT<T>& lp) {
+  if (!(tcap > T(0))) return true;
+  const T ts = tcap * sc;
+  bool ok = true;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    T ut[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const T v = (c == 0) ? xp[f] : (c == 1) ? -xm[f] : (c == 2) ? yp[f] : -ym[f];
+      ut[f] = (sizeof(T) == 8) ? uL[f] + tcap * (sc * v) : uL[f] + ts * v;
+    }
+    ok = ok && (ut[0] > T(0)) && LAW::psi_certainly_ge(ut, K, T(0), lp);
+  }
+  return ok;
+}
+
 // Post-round acceptance of the float32 store.  The limited field's forward-Euler result lies in
 // its local bounds [lo, hi] in exact arithmetic (Sec. 4.1.3; Sec. 4.3 for the density); the
 // float32 evaluation of the update can leave it outside by the rounding of its operands, of

@@ -359,7 +359,12 @@ __device__ __forceinline__ void stage_lines_body(LineSmem<P, EX, EY, LAW, T>& s,
   const T wj = pick<n>(tab.w, j);
   const T xij = pick<n>(tab.xi, j);
 
-  // ---------------- A: own row and the halo
+  const T dt = *I.dtT;
+  // ---------------- A: own row and the halo.  A thread's first halo slot is loaded before its
+  // row is processed, so that the two global-load latencies overlap.
+  T uh[NC], hpx = T(0), hpy = T(0);
+  const bool h0 = t < G::NH;
+  if (h0) halo_load<P, EX, EY, NC>(I, tab, t, ex0, ey0, h, uh, hpx, hpy);
   if (live) {
     T ur[NC][n];
     if (act) {
@@ -406,7 +411,12 @@ __device__ __forceinline__ void stage_lines_body(LineSmem<P, EX, EY, LAW, T>& s,
     }
     if constexpr (LAW::kEntropy) st_line<n>(&s.sig[srow], sg);
   }
-  for (int hh = t; hh < G::NH; hh += G::THREADS) {
+  if (h0) {
+    typename LAW::Aux ax;
+    node_aux<LAW>(uh, hpx, hpy, ax, lp);
+    st_node<LAW>(s, G::NTP + t, uh, ax, LAW::kEntropy ? LAW::sigma(uh, ax, lp) : T(0));
+  }
+  for (int hh = t + G::THREADS; hh < G::NH; hh += G::THREADS) {
     T uu[NC], px, py;
     halo_load<P, EX, EY, NC>(I, tab, hh, ex0, ey0, h, uu, px, py);
     typename LAW::Aux ax;
@@ -415,7 +425,6 @@ __device__ __forceinline__ void stage_lines_body(LineSmem<P, EX, EY, LAW, T>& s,
   }
   __syncthreads();
 
-  const T dt = *I.dtT;
   const bool move = (dt > T(0)) && (dt < T(FLT_MAX));
 
   // ---------------- B: column role (column j of element le)
@@ -523,6 +532,8 @@ __device__ __forceinline__ void stage_lines_body(LineSmem<P, EX, EY, LAW, T>& s,
 #pragma unroll
       for (int b = 0; b < n; ++b) ym[b][q] = v[b];
     }
+    T kb[n];
+    unsigned slow = 0;  // nodes whose entropy constraint the cheap certified test leaves undecided
 #pragma unroll
     for (int b = 0; b < n; ++b) {
       const T m = h * h * wj * tab.w[b];
@@ -535,7 +546,7 @@ __device__ __forceinline__ void stage_lines_body(LineSmem<P, EX, EY, LAW, T>& s,
       const T lo = tmin(lox[b], lyv[b]), hi = tmax(hix[b], hyv[b]);
       lob[b] = lo;
       hib[b] = hi;
-      const T K = LAW::kEntropy ? tmin(Kx[b], kyv[b]) : T(0);
+      kb[b] = LAW::kEntropy ? tmin(Kx[b], kyv[b]) : T(0);
       T xp[NC], xm[NC];
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
@@ -553,16 +564,52 @@ __device__ __forceinline__ void stage_lines_body(LineSmem<P, EX, EY, LAW, T>& s,
         const T Rp = (Pp > T(0)) ? tmin(T(1), fdiv(Qp, Pp)) : T(1);
         const T Rm = (Pm < T(0)) ? tmin(T(1), fdiv(Qm, Pm)) : T(1);
         a_ = tmin(Rp, Rm);
-        if constexpr (LAW::kEntropy)
-          a_ = entropy_limit<LAW>(uL[b], K * (T(1) + Prec<T>::entropy_margin), xp, xm, yp[b], ym[b], T(4) * dtm[b], a_,
-                                  lp, iters, caps);
+        if constexpr (LAW::kEntropy) {
+          if (!entropy_certain<LAW>(uL[b], kb[b] * (T(1) + Prec<T>::entropy_margin), xp, xm, yp[b], ym[b],
+                                    T(4) * dtm[b], a_, lp))
+            slow |= 1u << b;
+        }
       }
       at[b] = a_;
-      if (I.dbg_lo && act) {
-        I.dbg_lo[grow + b] = (double)lo;
-        I.dbg_hi[grow + b] = (double)hi;
-        I.dbg_K[grow + b] = (double)K;
-        I.dbg_alpha[grow + b] = (double)a_;
+    }
+    if constexpr (LAW::kEntropy) {
+      // the full entropy limiting of the undecided nodes, one node at a time through a single
+      // (inlined once) evaluation: the line's values of that node are selected into scalars
+#pragma unroll 1
+      while (slow) {
+        const int bs = __ffs(slow) - 1;
+        slow &= slow - 1;
+        T u1[NC], xp[NC], xm[NC], y1[NC], y2[NC], K1 = T(0), d1 = T(0), a1 = T(0);
+#pragma unroll
+        for (int c = 0; c < n; ++c) {
+          if (c == bs) {
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+              u1[q] = uL[c][q];
+              xp[q] = (c < P) ? Sx[c][q] : T(0);
+              xm[q] = (c > 0) ? Sx[c > 0 ? c - 1 : 0][q] : T(0);
+              y1[q] = yp[c][q];
+              y2[q] = ym[c][q];
+            }
+            K1 = kb[c];
+            d1 = dtm[c];
+            a1 = at[c];
+          }
+        }
+        const T r = entropy_limit<LAW>(u1, K1 * (T(1) + Prec<T>::entropy_margin), xp, xm, y1, y2, T(4) * d1, a1, lp,
+                                       iters, caps);
+#pragma unroll
+        for (int c = 0; c < n; ++c)
+          if (c == bs) at[c] = r;
+      }
+    }
+    if (I.dbg_lo && act) {
+#pragma unroll
+      for (int b = 0; b < n; ++b) {
+        I.dbg_lo[grow + b] = (double)lob[b];
+        I.dbg_hi[grow + b] = (double)hib[b];
+        I.dbg_K[grow + b] = (double)kb[b];
+        I.dbg_alpha[grow + b] = (double)at[b];
       }
     }
     st_line<n>(&s.alpha[srow], at);

@@ -157,13 +157,19 @@ def test_batch_stages_match_oracle_strict(limiter):
     sidp.sidp_batch_destroy(b)
 
 
-@pytest.mark.parametrize("mode", ["groups", "single"])
+@pytest.mark.parametrize("mode", ["groups", "single", "groups-line"])
 @pytest.mark.parametrize("lawname", ["euler", "burgers"])
 def test_batch_limited_stages_match_oracle(lawname, mode, monkeypatch):
     """The subcell-limited forward-Euler operator of every instance, from the oracle's SSP-RK3
     stage-k input, against the oracle with the conditioning-aware comparators (the alpha-tilde
-    of each instance from the batch's debug capture); with the concurrent degree-group launches
-    and with the single degree-switching launch."""
+    of each instance from the batch's debug capture); with the concurrent degree-group launches,
+    with the single degree-switching launch, and with the line kernel in every degree group
+    (Euler: tile candidate 4)."""
+    if mode == "groups-line":
+        if lawname != "euler":
+            pytest.skip("the line kernel is an Euler kernel")
+        monkeypatch.setenv("SIDP_TILE", "4")
+        mode = "groups"
     monkeypatch.setenv("SIDP_BATCH_LAUNCH", mode)
     pbs, b, U0 = _oracle_batch(lawname, "subcell")
     nc = U0[0].shape[0]
