@@ -280,6 +280,8 @@ SIDP_DECLARE_ALL(LAW_ADVECTION_VAR, float)
       return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, true>(a, bits, s);       \
     if (tile >= kNumTiles && !bits && a.limiter == 2 && !a.si.on) /* the line kernel (and its statistics variant) */ \
       return LineDispatch<LAWID, P, LAWTPL<TT>, TT>::stage(tile - kNumTiles, a, a.inst.stats != nullptr, s); \
+    if (tile >= kNumTiles && bits) /* the time step on the line kernel's tiles */                     \
+      return LineDispatch<LAWID, P, LAWTPL<TT>, TT>::dt(tile - kNumTiles, a, bits, s);                  \
     if (a.inst.stats && !bits) /* statistics on: the statistics kernel, default tile shape */         \
       return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, false, false, true>(a, bits, s); \
     if (!bits && (a.limiter != 2 || a.si.on)) /* other modes: the general kernel, default tile shape */ \

@@ -161,7 +161,7 @@ __device__ __forceinline__ void ld_node(const S& s, int slot, LNode<LAW, T>& nd)
   nd.s = LAW::kEntropy ? s.sig[slot] : T(0);
 }
 
-template <class LAW, typename T, class S>
+template <class LAW, typename T, class S, bool SIG = true>
 __device__ __forceinline__ void st_node(S& s, int slot, const T* uu, const typename LAW::Aux& ax, T sg) {
   constexpr int NA = AuxWords<LAW, T>::value;
 #pragma unroll
@@ -171,7 +171,7 @@ __device__ __forceinline__ void st_node(S& s, int slot, const T* uu, const typen
 #pragma unroll
     for (int k = 0; k < NA; ++k) s.aux[k][slot] = aw[k];
   }
-  if constexpr (LAW::kEntropy) s.sig[slot] = sg;
+  if constexpr (LAW::kEntropy && SIG) s.sig[slot] = sg;
 }
 
 // dst = src of lane (lane + delta) (all 32 lanes call it; lanes whose source is outside the warp
@@ -337,6 +337,80 @@ __device__ __forceinline__ double line_entropy_violation64(const S& s, int le, i
   return fmax(0.0, 1.0 - sf / K);
 }
 
+// Phase A of the line kernels: the thread's own row (vector loads; slots outside a ragged mesh edge
+// hold the boundary ghost of the adjacent element), its per-node quantities (and sigma when SIG) into
+// shared memory, then the halo slots.  A thread's first halo slot is loaded before its row is
+// processed, so that the two global-load latencies overlap.  The row's state and per-node
+// quantities are left in ur and ax.
+template <int P, int EX, int EY, class LAW, typename T, bool SIG, class S>
+__device__ __forceinline__ void line_phase_a(S& s, const Instance<T>& I, const Tables<T>& tab, const LawParamsT<T>& lp,
+                                             int t, bool live, bool act, int j, int ex, int ey, int ex0, int ey0,
+                                             long long grow, int srow, T h, T xij, T (&ur)[LAW::NC][P + 1],
+                                             typename LAW::Aux (&ax)[P + 1]) {
+  using G = LineGeom<P, EX, EY>;
+  constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
+  const long long N = I.N;
+  T uh[NC], hpx = T(0), hpy = T(0);
+  const bool h0 = t < G::NH;
+  if (h0) halo_load<P, EX, EY, NC>(I, tab, t, ex0, ey0, h, uh, hpx, hpy);
+  if (live) {
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) ld_line<n>(I.uin + q * N + grow, ur[q]);
+    } else {
+      // slots outside a ragged mesh edge hold the boundary ghost of the adjacent element
+#pragma unroll
+      for (int b = 0; b < n; ++b) {
+        T uu[NC];
+        if (ey < I.ny) neighbor_trace<P, NC>(I, 1, I.nx - 1, ey, j, tab.xi, uu);
+        else if (ex < I.nx) neighbor_trace<P, NC>(I, 3, ex, I.ny - 1, b, tab.xi, uu);
+        else {
+#pragma unroll
+          for (int q = 0; q < NC; ++q) uu[q] = I.uin[q * N + ((long long)ey0 * I.nx + ex0) * NN];
+        }
+#pragma unroll
+        for (int q = 0; q < NC; ++q) ur[q][b] = uu[q];
+      }
+    }
+    T sg[n];
+#pragma unroll
+    for (int b = 0; b < n; ++b) {
+      T uu[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) uu[q] = ur[q][b];
+      const T px = I.x0 + h * (ex < I.nx ? T(ex) + tab.xi[b] : T(I.nx));
+      const T py = I.y0 + h * (ey < I.ny ? T(ey) + xij : T(I.ny));
+      node_aux<LAW>(uu, px, py, ax[b], lp);
+      sg[b] = (LAW::kEntropy && SIG) ? LAW::sigma(uu, ax[b], lp) : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < NC; ++q) st_line<n>(&s.u[q][srow], ur[q]);
+    constexpr int NA = AuxWords<LAW, T>::value;
+    if constexpr (NA > 0) {
+#pragma unroll
+      for (int k = 0; k < NA; ++k) {
+        T v[n];
+#pragma unroll
+        for (int b = 0; b < n; ++b) v[b] = reinterpret_cast<const T*>(&ax[b])[k];
+        st_line<n>(&s.aux[k][srow], v);
+      }
+    }
+    if constexpr (LAW::kEntropy && SIG) st_line<n>(&s.sig[srow], sg);
+  }
+  if (h0) {
+    typename LAW::Aux ah;
+    node_aux<LAW>(uh, hpx, hpy, ah, lp);
+    st_node<LAW, T, S, SIG>(s, G::NTP + t, uh, ah, (LAW::kEntropy && SIG) ? LAW::sigma(uh, ah, lp) : T(0));
+  }
+  for (int hh = t + G::THREADS; hh < G::NH; hh += G::THREADS) {
+    T uu[NC], px, py;
+    halo_load<P, EX, EY, NC>(I, tab, hh, ex0, ey0, h, uu, px, py);
+    typename LAW::Aux ah;
+    node_aux<LAW>(uu, px, py, ah, lp);
+    st_node<LAW, T, S, SIG>(s, G::NTP + hh, uu, ah, (LAW::kEntropy && SIG) ? LAW::sigma(uu, ah, lp) : T(0));
+  }
+}
+
 template <int P, int EX, int EY, class LAW, typename T, bool STATS>
 __device__ __forceinline__ void stage_lines_body(LineSmem<P, EX, EY, LAW, T>& s, const Instance<T>& I,
                                                  const Tables<T>& tab, const LawParamsT<T>& lp, int tile_x,
@@ -360,68 +434,10 @@ __device__ __forceinline__ void stage_lines_body(LineSmem<P, EX, EY, LAW, T>& s,
   const T xij = pick<n>(tab.xi, j);
 
   const T dt = *I.dtT;
-  // ---------------- A: own row and the halo.  A thread's first halo slot is loaded before its
-  // row is processed, so that the two global-load latencies overlap.
-  T uh[NC], hpx = T(0), hpy = T(0);
-  const bool h0 = t < G::NH;
-  if (h0) halo_load<P, EX, EY, NC>(I, tab, t, ex0, ey0, h, uh, hpx, hpy);
-  if (live) {
+  {
     T ur[NC][n];
-    if (act) {
-#pragma unroll
-      for (int q = 0; q < NC; ++q) ld_line<n>(I.uin + q * N + grow, ur[q]);
-    } else {
-      // slots outside a ragged mesh edge hold the boundary ghost of the adjacent element
-#pragma unroll
-      for (int b = 0; b < n; ++b) {
-        T uu[NC];
-        if (ey < I.ny) neighbor_trace<P, NC>(I, 1, I.nx - 1, ey, j, tab.xi, uu);
-        else if (ex < I.nx) neighbor_trace<P, NC>(I, 3, ex, I.ny - 1, b, tab.xi, uu);
-        else {
-#pragma unroll
-          for (int q = 0; q < NC; ++q) uu[q] = I.uin[q * N + ((long long)ey0 * I.nx + ex0) * NN];
-        }
-#pragma unroll
-        for (int q = 0; q < NC; ++q) ur[q][b] = uu[q];
-      }
-    }
-    T sg[n];
     typename LAW::Aux ax[n];
-#pragma unroll
-    for (int b = 0; b < n; ++b) {
-      T uu[NC];
-#pragma unroll
-      for (int q = 0; q < NC; ++q) uu[q] = ur[q][b];
-      const T px = I.x0 + h * (ex < I.nx ? T(ex) + tab.xi[b] : T(I.nx));
-      const T py = I.y0 + h * (ey < I.ny ? T(ey) + xij : T(I.ny));
-      node_aux<LAW>(uu, px, py, ax[b], lp);
-      sg[b] = LAW::kEntropy ? LAW::sigma(uu, ax[b], lp) : T(0);
-    }
-#pragma unroll
-    for (int q = 0; q < NC; ++q) st_line<n>(&s.u[q][srow], ur[q]);
-    constexpr int NA = AuxWords<LAW, T>::value;
-    if constexpr (NA > 0) {
-#pragma unroll
-      for (int k = 0; k < NA; ++k) {
-        T v[n];
-#pragma unroll
-        for (int b = 0; b < n; ++b) v[b] = reinterpret_cast<const T*>(&ax[b])[k];
-        st_line<n>(&s.aux[k][srow], v);
-      }
-    }
-    if constexpr (LAW::kEntropy) st_line<n>(&s.sig[srow], sg);
-  }
-  if (h0) {
-    typename LAW::Aux ax;
-    node_aux<LAW>(uh, hpx, hpy, ax, lp);
-    st_node<LAW>(s, G::NTP + t, uh, ax, LAW::kEntropy ? LAW::sigma(uh, ax, lp) : T(0));
-  }
-  for (int hh = t + G::THREADS; hh < G::NH; hh += G::THREADS) {
-    T uu[NC], px, py;
-    halo_load<P, EX, EY, NC>(I, tab, hh, ex0, ey0, h, uu, px, py);
-    typename LAW::Aux ax;
-    node_aux<LAW>(uu, px, py, ax, lp);
-    st_node<LAW>(s, G::NTP + hh, uu, ax, LAW::kEntropy ? LAW::sigma(uu, ax, lp) : T(0));
+    line_phase_a<P, EX, EY, LAW, T, true>(s, I, tab, lp, t, live, act, j, ex, ey, ex0, ey0, grow, srow, h, xij, ur, ax);
   }
   __syncthreads();
 
@@ -770,12 +786,151 @@ cudaError_t launch_lines_batch(const BatchLaunch<T>& B, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- time step (Eq. cfl-low)
+// The CFL bound m_i / (2 sum_{j != i} d-hat_ij), d-hat = (h w / 2) lambda on the node's four faces,
+// min-reduced into *out_bits, on the line kernel's tiles: each thread evaluates lambda on the faces
+// of its row (west/east neighbours as in the stage kernel) and of its column; the column's sums
+// reach the row threads through shared memory.  The same face arguments and the same arithmetic as
+// the node layout's time-step kernel, hence the same time step.
+template <int P, int EX, int EY, class LAW, typename T>
+struct LineDtSmem {
+  using G = LineGeom<P, EX, EY>;
+  static constexpr int NC = LAW::NC, NA = AuxWords<LAW, T>::value;
+  T u[NC][G::NS];
+  T aux[NA > 0 ? NA : 1][G::NS];
+  T ly[G::NTP];  // per node: lambda on its lower plus its upper y face
+  T red[32];
+};
+
+template <class LAW, typename T, class S>
+__device__ __forceinline__ void ld_node_ua(const S& s, int slot, LNode<LAW, T>& nd) {
+  constexpr int NA = AuxWords<LAW, T>::value;
+#pragma unroll
+  for (int q = 0; q < LAW::NC; ++q) nd.u[q] = s.u[q][slot];
+  if constexpr (NA > 0) {
+    T* aw = reinterpret_cast<T*>(&nd.ax);
+#pragma unroll
+    for (int k = 0; k < NA; ++k) aw[k] = s.aux[k][slot];
+  }
+  nd.s = T(0);
+}
+
+template <int P, int EX, int EY, class LAW, typename T>
+__global__ void __launch_bounds__(LineGeom<P, EX, EY>::THREADS)
+k_dt_lines(const StageLaunch<T> A, unsigned long long* out_bits) {
+  using G = LineGeom<P, EX, EY>;
+  using N4 = LineNbr<P, EX, EY>;
+  using Nd = LNode<LAW, T>;
+  constexpr int n = P + 1, NN = n * n, NC = LAW::NC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  auto& s = *reinterpret_cast<LineDtSmem<P, EX, EY, LAW, T>*>(smem_raw);
+  const Instance<T>& I = A.inst;
+  const Tables<T>& tab = A.tab;
+  const LawParamsT<T>& lp = A.lp;
+  const int tiles_x = (I.nx + EX - 1) / EX;
+  const int tile_y = blockIdx.x / tiles_x, tile_x = blockIdx.x - tile_y * tiles_x;
+  const int t = threadIdx.x;
+  const bool live = (G::NL == G::THREADS) || (t < G::NL);
+  const int le = live ? t / n : 0, j = live ? t - le * n : 0;
+  const int tx = le % EX, ty = le / EX;
+  const int ex0 = tile_x * EX, ey0 = tile_y * EY;
+  const int ex = ex0 + tx, ey = ey0 + ty;
+  const bool act = live && ex < I.nx && ey < I.ny;
+  const long long grow = act ? ((long long)ey * I.nx + ex) * NN + j * n : 0;
+  const int srow = G::rs(le, j);
+  const T h = I.hT;
+  const T wj = pick<n>(tab.w, j);
+  const T xij = pick<n>(tab.xi, j);
+  T ur[NC][n];
+  typename LAW::Aux ax[n];
+  line_phase_a<P, EX, EY, LAW, T, false>(s, I, tab, lp, t, live, act, j, ex, ey, ex0, ey0, grow, srow, h, xij, ur, ax);
+  __syncthreads();
+  T lx[n + 1];
+  if (live) {
+    // column j: lambda on its n + 1 y faces, summed per node for the row threads
+    Nd nd[n], lft, rgt;
+#pragma unroll
+    for (int a = 0; a < n; ++a) ld_node_ua<LAW, T>(s, G::rs(le, a) + j, nd[a]);
+    ld_node_ua<LAW, T>(s, N4::south(le, tx, ty, j), lft);
+    ld_node_ua<LAW, T>(s, N4::north(le, tx, ty, j), rgt);
+    T ly[n + 1];
+    ly[0] = LAW::lam(1, lft.u, lft.ax, nd[0].u, nd[0].ax, lp);
+#pragma unroll
+    for (int a = 1; a < n; ++a) ly[a] = LAW::lam(1, nd[a - 1].u, nd[a - 1].ax, nd[a].u, nd[a].ax, lp);
+    ly[n] = LAW::lam(1, nd[P].u, nd[P].ax, rgt.u, rgt.ax, lp);
+#pragma unroll
+    for (int a = 0; a < n; ++a) s.ly[G::rs(le, a) + j] = ly[a] + ly[a + 1];
+    // row j: lambda on its n + 1 x faces
+#pragma unroll
+    for (int b = 0; b < n; ++b) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) nd[b].u[q] = ur[q][b];
+      nd[b].ax = ax[b];
+      nd[b].s = T(0);
+    }
+    if constexpr (G::XSHFL) {
+      shfl_node<LAW, T>(nd[P], lft, -n);
+      shfl_node<LAW, T>(nd[0], rgt, n);
+      if (tx == 0) ld_node_ua<LAW, T>(s, G::hW + ty * n + j, lft);
+      if (tx == EX - 1) ld_node_ua<LAW, T>(s, G::hE + ty * n + j, rgt);
+    } else {
+      ld_node_ua<LAW, T>(s, N4::west(le, tx, ty, j), lft);
+      ld_node_ua<LAW, T>(s, N4::east(le, tx, ty, j), rgt);
+    }
+    lx[0] = LAW::lam(0, lft.u, lft.ax, nd[0].u, nd[0].ax, lp);
+#pragma unroll
+    for (int b = 1; b < n; ++b) lx[b] = LAW::lam(0, nd[b - 1].u, nd[b - 1].ax, nd[b].u, nd[b].ax, lp);
+    lx[n] = LAW::lam(0, nd[P].u, nd[P].ax, rgt.u, rgt.ax, lp);
+  }
+  __syncthreads();
+  const T big = T(FLT_MAX);
+  T val = big;
+  if (act) {
+    T lyr[n];
+    ld_line<n>(&s.ly[srow], lyr);
+#pragma unroll
+    for (int b = 0; b < n; ++b) {
+      const T wa = wj, wb = tab.w[b];
+      const T sumd = T(0.5) * h * wa * (lx[b] + lx[b + 1]) + T(0.5) * h * wb * lyr[b];
+      if (sumd > T(0)) val = tmin(val, fdiv(h * h * wa * wb, T(2) * sumd));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) val = tmin(val, __shfl_xor_sync(0xffffffffu, val, o));
+  if ((t & 31) == 0) s.red[t >> 5] = val;
+  __syncthreads();
+  if (t < 32) {
+    val = (t < G::THREADS / 32) ? s.red[t] : big;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) val = tmin(val, __shfl_xor_sync(0xffffffffu, val, o));
+    if (t == 0 && val < big) atomicMin(out_bits, (unsigned long long)__double_as_longlong((double)val));
+  }
+}
+
+template <int P, int EX, int EY, class LAW, typename T>
+cudaError_t launch_dt_lines(const StageLaunch<T>& a, unsigned long long* bits, cudaStream_t s) {
+  using G = LineGeom<P, EX, EY>;
+  constexpr size_t smem = sizeof(LineDtSmem<P, EX, EY, LAW, T>);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t err = cudaFuncSetAttribute(k_dt_lines<P, EX, EY, LAW, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
+    attr_set = true;
+  }
+  const long long tiles = (long long)((a.inst.nx + EX - 1) / EX) * ((a.inst.ny + EY - 1) / EY);
+  if (tiles <= 0) return cudaSuccess;
+  k_dt_lines<P, EX, EY, LAW, T><<<(unsigned)tiles, G::THREADS, smem, s>>>(a, bits);
+  return cudaGetLastError();
+}
+
 // Line kernels of one law, degree and precision, by line-tile index: Euler only (the other laws
 // have no line-kernel candidates).
 template <int LAWID, int P, class LAW, typename T>
 struct LineDispatch {
   static cudaError_t stage(int, const StageLaunch<T>&, bool, cudaStream_t) { return cudaErrorInvalidValue; }
   static cudaError_t batch(int, const BatchLaunch<T>&, bool, cudaStream_t) { return cudaErrorInvalidValue; }
+  static cudaError_t dt(int, const StageLaunch<T>&, unsigned long long*, cudaStream_t) { return cudaErrorInvalidValue; }
 };
 
 template <int P, class LAW, typename T>
@@ -785,6 +940,14 @@ struct LineDispatch<LAW_EULER, P, LAW, T> {
     switch (lt) {
       case 0: return stats ? launch_lines<P, t0.tx, t0.ty, LAW, T, true>(a, s) : launch_lines<P, t0.tx, t0.ty, LAW, T, false>(a, s);
       case 1: return stats ? launch_lines<P, t1.tx, t1.ty, LAW, T, true>(a, s) : launch_lines<P, t1.tx, t1.ty, LAW, T, false>(a, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  static cudaError_t dt(int lt, const StageLaunch<T>& a, unsigned long long* bits, cudaStream_t s) {
+    constexpr TileShape t0 = kLineTiles[P][0], t1 = kLineTiles[P][1];
+    switch (lt) {
+      case 0: return launch_dt_lines<P, t0.tx, t0.ty, LAW, T>(a, bits, s);
+      case 1: return launch_dt_lines<P, t1.tx, t1.ty, LAW, T>(a, bits, s);
       default: return cudaErrorInvalidValue;
     }
   }
