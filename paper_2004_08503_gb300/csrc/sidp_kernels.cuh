@@ -397,8 +397,10 @@ __device__ T entropy_limit(const T* uL, T K, const T* xp, const T* xm, const T* 
       // float64 keeps the oracle's order of operations, u^L + t (scale r-bar)
       ut[f] = (sizeof(T) == 8) ? uL[f] + tcap * (sc * v) : uL[f] + ts * v;
     }
-    if (!(ut[0] > T(0) && (LAW::psi_certainly_ge(ut, K, target, lp) || LAW::psi(ut, K, lp) >= target)))
-      fail |= 1u << c;
+    // the precise psi only: the cheap certified test against target has just failed against 0
+    // for this candidate, and target = min(0, psi_K(u^L)) lies within the test's error allowance
+    // of 0 (u^L is in the entropy set up to rounding), so it cannot pass either
+    if (!(ut[0] > T(0) && LAW::psi(ut, K, lp) >= target)) fail |= 1u << c;
   }
   if (!fail) return tcap;
   const T psi0 = LAW::psi(uL, K, lp);
