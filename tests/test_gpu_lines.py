@@ -261,3 +261,52 @@ def test_line_time_step(p, bc, tile):
     ref.set_state(U.reshape(4, -1))
     assert dt_line == ref.compute_dt()
     assert abs(dt_line - pb.compute_dt(U)) <= 1e-13 * pb.compute_dt(U)
+
+
+@pytest.mark.parametrize("nx,ny,bc", [(1, 1, ("periodic",) * 4), (1, 1, ("outflow",) * 4), (1, 5, ("outflow",) * 4),
+                                      (9, 1, ("periodic",) * 4), (3, 2, ("wall",) * 4)])
+def test_line_tiny_meshes(nx, ny, bc):
+    """Meshes smaller than one line tile (one element, one element row or column): every tile
+    slot but a few holds a boundary ghost; the element is its own periodic neighbour."""
+    p, tile = 3, 4
+    pb, sv = make(p, nx, ny, bc, tile)
+    X, Y = pb.node_coords()
+    U0 = inputs.four_quadrant(X, Y, seed=11)
+    dt = pb.compute_dt(U0)
+    sv.set_state(U0.reshape(4, -1))
+    assert abs(sv.compute_dt() - dt) <= 1e-13 * dt
+    sv.set_debug(True)
+    cur = U0
+    for k in (1, 2, 3):
+        sv.set_state(cur.reshape(4, -1))
+        sv.stage(1, dt)
+        euler_fe_check(pb, cur, dt, sv.get_state(1), sv.bounds()["alpha"], max_relaxed=0.75)
+        cur = pb.stage(cur, U0, dt, k)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL), ("mixed", 1e-3)])
+def test_line_full_size_blast_sampled(precision, tol):
+    """The bench workload's size and launch configuration (1024x1024 p=3 blast, 16.8M nodes, the
+    line kernel's 8x4 tile): one stage on the GPU; the FP64 oracle recomputes a sample of elements
+    (random, corners, the blast centre) one by one.  FP64 to 1e-12.  The mixed form to 1e-3
+    normwise per field: the first stage creates the momentum from pressure differences of up to
+    1e3 (pressure ratio 1e8), whose float32 rounding (6e-8 of p) is about 1e-4 of the new momentum
+    (measured 1.2e-4 for both momentum fields; density and energy 0 and 4e-7)."""
+    nel, p = 1024, 3
+    pb, sv = make(p, nel, nel, ("outflow",) * 4, 4, precision=precision)
+    X, Y = pb.node_coords()
+    U = inputs.blast(X, Y)
+    del X, Y
+    sv.set_state(U.reshape(4, -1))
+    dt = sv.compute_dt()
+    sv.stage(1, dt)
+    got = sv.get_state(1).reshape(4, pb.Ne, -1)
+    rng = np.random.default_rng(1)
+    c = nel // 2
+    sample = np.unique(np.concatenate([
+        rng.integers(0, pb.Ne, 48), [0, nel - 1, pb.Ne - nel, pb.Ne - 1],
+        [(c + dy) * nel + c + dx for dy in range(-3, 3) for dx in range(-3, 3)]]))
+    exp = pb.fe_stage(U, dt, elems=sample)
+    err = np.max(np.abs(got[:, sample] - exp), axis=(1, 2)) / np.max(np.abs(exp), axis=(1, 2))
+    print(precision, "max normwise error per field", err)
+    assert np.all(err <= tol), err
