@@ -270,14 +270,18 @@ cudaError_t run_step(sidp_ctx* c) {
 }
 
 // ---------------------------------------------------------------- tile autotuner
-// Picks the element tile shape per (law, p, precision) by timing stage 1 of every candidate in
-// kTiles[p] on the context's current state, once per process (results are identical across
-// shapes: each face and node is evaluated from the same inputs in the same order).  SIDP_TILE=<i>
+// Picks the stage kernel's tile candidate per (law, p, precision, curved or not) by timing stage 1
+// of every candidate on the context's current state: node-layout tiles kTiles[p] and, for Euler,
+// line-layout tiles kLineTiles[p] (on a curved mesh: the node layout and the line layout).  Two
+// passes: at the first step, and once more at kSettleSteps steps, whose choice is kept for the
+// process.  Results differ between the layouts only in the rounding of sums.  SIDP_TILE=<i>
 // forces a candidate, SIDP_AUTOTUNE=0 keeps the default; SIDP_TUNE_FILE=<path> loads and stores
-// the table ("law p precision tile" lines).
+// the settled table ("law p slot tile" lines, slot = precision (0 float64, 1 mixed) + 2 on a
+// curved mesh).
 std::mutex g_tune_mu;
-int g_tune[LAW_ADVECTION_VAR + 1][kMaxP + 1][2];
-bool g_settled[LAW_ADVECTION_VAR + 1][kMaxP + 1][2];  // chosen by the second pass (or loaded from a file)
+// last index: precision (0 float64, 1 mixed) + 2 on curved meshes
+int g_tune[LAW_ADVECTION_VAR + 1][kMaxP + 1][4];
+bool g_settled[LAW_ADVECTION_VAR + 1][kMaxP + 1][4];  // chosen by the second pass (or loaded from a file)
 bool g_tune_init = false;
 // The first steps of a flow (a blast's initial transient, say) can favour another tile than the
 // rest of the run: the autotuner times the candidates at the first step and once more at this step.
@@ -286,14 +290,14 @@ constexpr long long kSettleSteps = 10;
 void tune_table_init() {
   if (g_tune_init) return;
   for (auto& a : g_tune)
-    for (auto& b : a) b[0] = b[1] = -1;
+    for (auto& b : a) b[0] = b[1] = b[2] = b[3] = -1;
   for (auto& a : g_settled)
-    for (auto& b : a) b[0] = b[1] = false;
+    for (auto& b : a) b[0] = b[1] = b[2] = b[3] = false;
   if (const char* f = std::getenv("SIDP_TUNE_FILE")) {
     if (FILE* fp = std::fopen(f, "r")) {
       int law, p, mixed, tile;
       while (std::fscanf(fp, "%d %d %d %d", &law, &p, &mixed, &tile) == 4)
-        if (law >= 1 && law <= 3 && p >= 1 && p <= kMaxP && (mixed == 0 || mixed == 1) && tile >= 0 &&
+        if (law >= 1 && law <= 3 && p >= 1 && p <= kMaxP && mixed >= 0 && mixed <= 3 && tile >= 0 &&
             tile < num_tile_candidates(law)) {
           g_tune[law][p][mixed] = tile;
           g_settled[law][p][mixed] = true;
@@ -310,7 +314,7 @@ void tune_table_store() {
   if (FILE* fp = std::fopen(f, "w")) {
     for (int law = 1; law <= 3; ++law)
       for (int p = 1; p <= kMaxP; ++p)
-        for (int m = 0; m < 2; ++m)
+        for (int m = 0; m < 4; ++m)
           if (g_tune[law][p][m] >= 0) std::fprintf(fp, "%d %d %d %d\n", law, p, m, g_tune[law][p][m]);
     std::fclose(fp);
   }
@@ -353,8 +357,9 @@ cudaError_t autotune(sidp_ctx* c, bool second = false) {
   if (off && off[0] == '0') return cudaSuccess;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   tune_table_init();
-  int& slot = g_tune[c->cfg.law][c->cfg.p][c->mixed ? 1 : 0];
-  bool& settled = g_settled[c->cfg.law][c->cfg.p][c->mixed ? 1 : 0];
+  const int ti = (c->mixed ? 1 : 0) + (c->curved ? 2 : 0);
+  int& slot = g_tune[c->cfg.law][c->cfg.p][ti];
+  bool& settled = g_settled[c->cfg.law][c->cfg.p][ti];
   if (slot >= 0 && (settled || !second)) {
     c->tile = slot;
     if (!settled) { c->settle = true; c->settle_at = c->steps + kSettleSteps; }
@@ -367,7 +372,17 @@ cudaError_t autotune(sidp_ctx* c, bool second = false) {
   float best = 1e30f;
   int best_t = 0;
   const int saved = c->tile;
-  for (int t = 0; t < num_tile_candidates(c->cfg.law) && err == cudaSuccess; ++t) {
+  // candidates: every tile of both layouts on a Cartesian mesh; on a curved mesh the node layout
+  // (0) and, for Euler, the line layout (kNumTiles)
+  int cand[kMaxCand], ncand = 0;
+  if (c->curved) {
+    cand[ncand++] = 0;
+    if (c->cfg.law == LAW_EULER) cand[ncand++] = kNumTiles;
+  } else {
+    for (int t = 0; t < num_tile_candidates(c->cfg.law); ++t) cand[ncand++] = t;
+  }
+  for (int ci = 0; ci < ncand && err == cudaSuccess; ++ci) {
+    const int t = cand[ci];
     c->tile = t;
     if ((err = run_dt(c, false)) != cudaSuccess) break;
     if ((err = run_stage(c, 1)) != cudaSuccess) break;  // warm-up (and kernel attributes)
@@ -708,7 +723,7 @@ sidp_status sidp_set_geometry(sidp_ctx* c, const double* x, const double* y) try
   c->hx.assign(x, x + c->N);
   c->hy.assign(y, y + c->N);
   c->curved = true;
-  c->tuned = true;  // one kernel shape on curved meshes: nothing to tune
+  c->tuned = false;  // curved meshes have their own candidates (node and line layouts)
   c->settle = false;
   c->tile = 0;
   drop_graph(c);
@@ -896,8 +911,10 @@ sidp_status sidp_set_tile(sidp_ctx* c, int index) {
   if (!c) return fail(c, SIDP_ERR_ARG, "null context");
   if (index < 0 || index >= num_tile_candidates(c->cfg.law))
     return fail(c, SIDP_ERR_ARG, "tile index out of range for this law");
-  if (index != 0 && (c->curved || c->cfg.limiter != 2 || c->cfg.smoothness || c->cfg.unsparsified))
-    return fail(c, SIDP_ERR_ARG, "only subcell limiting without the smoothness indicator on a Cartesian mesh has tile candidates");
+  if (index != 0 && (c->cfg.limiter != 2 || c->cfg.smoothness || c->cfg.unsparsified))
+    return fail(c, SIDP_ERR_ARG, "only subcell limiting without the smoothness indicator has tile candidates");
+  if (index != 0 && c->curved && (index != kNumTiles || c->cfg.law != LAW_EULER))
+    return fail(c, SIDP_ERR_ARG, "a curved mesh has two candidates: 0 (node layout) and 4 (line layout, Euler)");
   if (c->stage_done != 0) return fail(c, SIDP_ERR_STATE, "an SSP-RK3 step is half done (stage 1 or 2 ran)");
   c->tile = index;
   c->tuned = true;

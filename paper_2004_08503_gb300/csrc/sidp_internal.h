@@ -269,8 +269,11 @@ SIDP_DECLARE_ALL(LAW_ADVECTION_VAR, float)
   template <>                                                                                          \
   cudaError_t launch_p<LAWID, TT, P>(int tile, const StageLaunch<TT>& a, unsigned long long* bits,     \
                                      cudaStream_t s) {                                                 \
-    if (a.inst.geo) /* curved mesh: its own kernels */                                                 \
+    if (a.inst.geo) { /* curved mesh: its own kernels (node layout; line layout for Euler) */           \
+      if (tile >= kNumTiles && !bits && a.limiter == 2 && !a.si.on)                                    \
+        return CurvedLines<P, LAWTPL<TT>, TT>::stage(a, a.inst.stats != nullptr, s);                   \
       return launch_curved<P, LAWTPL<TT>, TT>(a, bits, s);                                             \
+    }                                                                                                  \
     if (a.dense) { /* unsparsified comparison mode: its own kernels, default tile shape */             \
       if (bits || a.limiter != 3)                                                                      \
         return launch_tile<P, kTiles[P][0].tx, kTiles[P][0].ty, LAWTPL<TT>, TT, false, true>(a, bits, s); \
