@@ -54,11 +54,13 @@ STAGE_COUNTERS = {
 # from an ncu capture of the same workload in float64: its FP64-pipe roofline.
 FP64_STAGE_FLOP_PER_NODE = (1198.0, 1197.6, 1197.8)
 SMS, SCHEDULERS_PER_SM = 152, 4
-# The curved-mesh stage kernel's DRAM traffic per node and launch (stages 1-3 averaged), from one
-# ncu capture of the 768x768 curved leg.  The kernel has changed since (the smoothness-indicator block, off in this workload), so the figure is not
-# reported as the launch's traffic until it is captured again.
-CURVED_DRAM_BYTES_PER_NODE = 93.4
-CURVED_TRAFFIC_CURRENT = False
+# DRAM traffic per node and launch (stages 1-3 averaged) of the two curved-mesh stage kernels, from
+# ncu captures of the 768x768 curved leg; "current" is False once the kernel has changed since.
+CURVED_COUNTERS = {
+    "node": {"kernel": "k_stage_curved<3, LawEuler<float>, float>", "dram_bytes_per_node": 93.4, "current": False},
+    "line": {"kernel": "k_stage_curved_lines<3, LawEuler<float>, float>", "dram_bytes_per_node": None,
+             "current": False},
+}
 NEL, P = 1024, 3
 WORKLOAD = "2D Euler blast, 1024x1024 elements, p=3 (16.8M nodes x 4 fields), outflow, CFL 0.5, subcell convex limiting"
 WORKLOAD_CURVED = ("2D Euler blast on a curved mesh: 1024x1024 elements, p=3, nodes warped by "
@@ -249,6 +251,7 @@ def run_curved(torch, sidp, stream, steps, warmup, hbm, peak_kind):
     sec, _ = time_steps(torch, sv, stream, steps, warmup)
     value = nodes * 3 * steps / sec
     kt = stage_kernel_times(torch, sv, stream, reps=10)
+    ctr = CURVED_COUNTERS["line" if sv.tile()[2] >= 4 else "node"]
     # untimed: three steps with the statistics variant of the curved stage kernel
     sv.set_stats(True)
     sv.step(3)
@@ -265,8 +268,8 @@ def run_curved(torch, sidp, stream, steps, warmup, hbm, peak_kind):
             "steps": steps, "ms_per_step": 1e3 * sec / steps, "stage_ms": [1e3 * t for t in kt],
             "geometry_setup_s": setup,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                         "traffic": CURVED_DRAM_BYTES_PER_NODE * nodes if CURVED_TRAFFIC_CURRENT else None,
-                         "kernel": "k_stage_curved<3, LawEuler<float>, float>",
+                         "traffic": ctr["dram_bytes_per_node"] * nodes if ctr["current"] else None,
+                         "kernel": ctr["kernel"],
                          "bytes_per_node": per_node, "peak_kind": peak_kind},
             "invariants": {k: d[k] for k in ("rho_min", "p_min", "nonfinite", "max_bound_violation",
                                              "max_entropy_violation", "rootfind_max_iters", "rootfind_cap_hits",

@@ -7,9 +7,10 @@
 // from the node's own state and the neighbour's trace, read from global memory, L2-resident).
 // Thread j of element K is the thread of row j and of column j of K:
 //   A  the row's state, contravariant rows r1, corrected rows q1 and masses by vector loads; the
-//      row's per-node quantities and sigma into shared memory; the loads of the four element-face
-//      items of the line (normals and neighbour traces) are issued first;
-//   B  column role: the column's nodes from shared memory, its rows r2 / q2 from global memory;
+//      row's per-node quantities and sigma into shared memory;
+//   B  column role: the element-face items of the column (normals and neighbour traces, loaded at
+//      the start of the role: loaded in phase A they stayed live across the barrier and spilled),
+//      the column's nodes from shared memory, its rows r2 / q2 from global memory;
 //      y subcell faces (Lambda over both nodes' corrected rows, two bar states), the two element
 //      faces, the contraction of r2 . F with D_1D, r^H_y, r^L_y, bounds and prefix sums -> shared
 //      memory for the row threads;
@@ -281,12 +282,7 @@ __device__ __forceinline__ void curved_lines_body(CurvedLineSmem<P, LAW, T>& s, 
   const bool move = (dt > T(0)) && (dt < T(FLT_MAX));
   const T* geo = I.geo;
 
-  // ---------------- A: element-face items first, then the row
-  CurvedItem<LAW, T> itW, itE, itS, itN;
-  curved_item_load<P, LAW>(I, ge, j, 0, 0, itW);
-  curved_item_load<P, LAW>(I, ge, j, P, 1, itE);
-  curved_item_load<P, LAW>(I, ge, 0, j, 2, itS);
-  curved_item_load<P, LAW>(I, ge, P, j, 3, itN);
+  // ---------------- A: the row
   T ur[NC][n], r1[2][n], q1[2][n], mr[n];
 #pragma unroll
   for (int q = 0; q < NC; ++q) ld_line<n>(I.uin + q * N + grow, ur[q]);
@@ -323,6 +319,9 @@ __device__ __forceinline__ void curved_lines_body(CurvedLineSmem<P, LAW, T>& s, 
 
   // ---------------- B: column role (column j of element le)
   if (live) {
+    CurvedItem<LAW, T> itS, itN;
+    curved_item_load<P, LAW>(I, ge, 0, j, 2, itS);
+    curved_item_load<P, LAW>(I, ge, P, j, 3, itN);
     Nd nd[n];
     T fx[n][NC], fy[n][NC], r2[n][2], q2[n][2];
 #pragma unroll
@@ -363,6 +362,9 @@ __device__ __forceinline__ void curved_lines_body(CurvedLineSmem<P, LAW, T>& s, 
   T rlx[n][NC], lox[n], hix[n], Kx[n], Sx[n][NC];
   Face FW, FE;
   if (live) {
+    CurvedItem<LAW, T> itW, itE;
+    curved_item_load<P, LAW>(I, ge, j, 0, 0, itW);
+    curved_item_load<P, LAW>(I, ge, j, P, 1, itE);
     Nd nd[n];
     T fx[n][NC], fy[n][NC], rr[n][2], qq[n][2];
 #pragma unroll
