@@ -58,8 +58,8 @@ SMS, SCHEDULERS_PER_SM = 152, 4
 # ncu captures of the 768x768 curved leg; "current" is False once the kernel has changed since.
 CURVED_COUNTERS = {
     "node": {"kernel": "k_stage_curved<3, LawEuler<float>, float>", "dram_bytes_per_node": 93.4, "current": False},
-    "line": {"kernel": "k_stage_curved_lines<3, LawEuler<float>, float>", "dram_bytes_per_node": None,
-             "current": False},
+    "line": {"kernel": "k_stage_curved_lines<3, LawEuler<float>, float>", "dram_bytes_per_node": 93.9,
+             "current": True},
 }
 NEL, P = 1024, 3
 WORKLOAD = "2D Euler blast, 1024x1024 elements, p=3 (16.8M nodes x 4 fields), outflow, CFL 0.5, subcell convex limiting"
