@@ -310,3 +310,38 @@ def test_line_full_size_blast_sampled(precision, tol):
     err = np.max(np.abs(got[:, sample] - exp), axis=(1, 2)) / np.max(np.abs(exp), axis=(1, 2))
     print(precision, "max normwise error per field", err)
     assert np.all(err <= tol), err
+
+
+def test_autotuner_second_pass_inside_a_call():
+    """The autotuner's second pass at step 10 falls inside a 15-step call: the call is split there,
+    the candidates are timed again and the step graph is captured again.  The trajectory equals,
+    bit for bit, one taken step by step with the first pass's tile for steps 1-10 and the second
+    pass's for steps 11-15 (a context created first takes the first pass's choice from the
+    process's table; when an earlier test has already settled it, both tiles are that choice)."""
+    p, nel = 6, 20
+    pb = scheme.Problem(laws.Euler(G), p, nel, nel, bc=("outflow",) * 4)
+    X, Y = pb.node_coords()
+    U = inputs.four_quadrant(X, Y, seed=3).reshape(4, -1)
+
+    def solver():
+        sv = sidp.Solver(law="euler", p=p, nx=nel, ny=nel, bc=("outflow",) * 4, gamma=G, precision="mixed")
+        sv.set_stats(False)
+        sv.set_state(U)
+        return sv
+
+    c = solver()
+    c.step(1)
+    t1 = c.tile()[2]
+    a = solver()
+    a.step(15)
+    t2 = a.tile()[2]
+    assert 0 <= t1 < 6 and 0 <= t2 < 6
+    b = solver()
+    b.set_tile(t1)
+    for _ in range(10):
+        b.step(1)
+    b.set_tile(t2)
+    for _ in range(5):
+        b.step(1)
+    assert a.diag()["steps"] == b.diag()["steps"] == 15
+    np.testing.assert_array_equal(a.get_state(0), b.get_state(0))
