@@ -33,10 +33,13 @@ constexpr int kRootMaxIt = 60;
 
 template <typename T> struct Prec;
 // root_tol: bracket width at which the entropy line search stops.  entropy_margin: the float32
-// path demands sigma >= K (1 + margin) so that evaluation error in float32 (a few ulp of rho e,
-// amplified where kinetic energy dominates) cannot leave the stored state below the bound.
+// path demands sigma >= K (1 + margin) so that evaluation error in float32 cannot leave the stored
+// state below the bound: a few ulp of rho e (compensated, also where kinetic energy dominates),
+// and the fast power rho^gamma = exp2(gamma log2 rho), whose relative error grows with
+// |gamma log2 rho| (about 1.9e-6 at gamma = 1.4, |log2 rho| = 8) and enters both K_i and the
+// candidates' psi_K: 4e-6 covers the two for densities from 1/256 to 256.
 template <> struct Prec<double> { static constexpr double root_tol = 1e-13; static constexpr double entropy_margin = 0.0; };
-template <> struct Prec<float> { static constexpr float root_tol = 2e-6f; static constexpr float entropy_margin = 1e-6f; };
+template <> struct Prec<float> { static constexpr float root_tol = 2e-6f; static constexpr float entropy_margin = 4e-6f; };
 
 template <typename T, int NC> struct alignas(NC == 4 ? 4 * sizeof(T) : NC == 2 ? 2 * sizeof(T) : sizeof(T)) Vec { T v[NC]; };
 

@@ -251,9 +251,11 @@ struct LawEuler {
   // psi_K(u) = rho e - K rho^gamma and its gradient in conserved variables
   __device__ static T psi(const T* u, T K, const LawParamsT<T>& lp) { return rhoe(u) - K * ppow(u[0], lp.gamma); }
   // True when psi_K(u) >= target is certain from a cheap float32 evaluation: the few roundings
-  // of rho E, |m|^2/(2 rho) and K rho^gamma stay below 1e-6 of their magnitudes (a bound with a
-  // wide margin over the ~10 ulp they can reach), so psi >= psi_fast - err.  False means
-  // "undecided" (the caller evaluates psi precisely).  The float64 path always evaluates psi.
+  // of rho E and |m|^2/(2 rho) stay below 1e-6 of their magnitudes (a wide margin over the ~10
+  // ulp they can reach), and K rho^gamma below 4e-6 of its (the fast power's relative error grows
+  // with |gamma log2 rho|: about 1.9e-6 at gamma = 1.4 for rho = 256 or 1/256), so psi >=
+  // psi_fast - err.  False means "undecided" (the caller evaluates psi in full).  The float64
+  // path always evaluates psi.
   __device__ static bool psi_certainly_ge(const T* u, T K, T target, const LawParamsT<T>& lp) {
     if constexpr (sizeof(T) == 8) {
       return false;
@@ -262,7 +264,7 @@ struct LawEuler {
       const float ke = 0.5f * fmaf(u[1], u[1], u[2] * u[2]) * rinv;
       const float rg = K * ppow(u[0], lp.gamma);
       const float pf = (u[3] - ke) - rg;
-      const float err = 1e-6f * (fabsf(u[3]) + ke + rg);
+      const float err = 1e-6f * (fabsf(u[3]) + ke) + 4e-6f * rg;
       return pf - err >= target;
     }
   }

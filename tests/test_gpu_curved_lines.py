@@ -133,8 +133,9 @@ def test_line_curved_statistics_variant(precision):
 
 
 def test_line_curved_mixed_against_fp64_and_node_layout():
-    """Mixed precision, 20 steps on the warped mesh: close to the FP64 form and to the node
-    layout's mixed run."""
+    """Mixed precision, 20 steps on the warped mesh with four-quadrant data: close to the FP64 form
+    and to the node layout's mixed run, L1-relative per field (a discontinuity's nodes carry the
+    limiter's rounding-decided coefficients, so the max norm is looser)."""
     out = {}
     for name, prec, tile in (("line", "mixed", LINE), ("node", "mixed", 0), ("fp64", "fp64", LINE)):
         pb, sv, X, Y = tc.make("euler", 3, 16, 16, "subcell", L=(1.0, 1.0), precision=prec)
@@ -142,8 +143,14 @@ def test_line_curved_mixed_against_fp64_and_node_layout():
         sv.set_state(tc.data("euler", X, Y, seed=2).reshape(4, -1))
         sv.step(20)
         out[name] = sv.get_state(0)
+        d = sv.diag()
+        assert d["rho_min"] > 0 and d["p_min"] > 0 and d["nonfinite"] == 0
+    a = out["line"]
     for other in ("node", "fp64"):
-        assert np.all(tc.rel(out["line"], out[other]) <= 1e-3), (other, tc.rel(out["line"], out[other]))
+        b = out[other]
+        l1 = np.abs(a - b).mean(axis=1) / np.abs(b).mean(axis=1)
+        mx = tc.rel(a, b)
+        assert np.all(l1 <= 1e-4) and np.all(mx <= 1e-2), (other, l1, mx)
 
 
 def test_line_curved_full_size_blast_sampled():
