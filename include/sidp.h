@@ -251,7 +251,7 @@ sidp_status sidp_stage(sidp_ctx* ctx, int k, double dt);
 sidp_status sidp_step(sidp_ctx* ctx, int nsteps);
 
 /* Element tile (elements per CTA along x and y) that the stage kernels use; chosen per
- * (law, p, precision) by timing the candidates at the first sidp_step and once more when the
+ * (law, p, precision, Cartesian or curved) by timing the candidates at the first sidp_step and once more when the
  * context has taken 10 steps (the first steps of a flow, such as a blast's initial transient,
  * can favour another tile than the rest of the run; that second pass synchronizes the stream
  * once, inside the sidp_step call that reaches step 10).  SIDP_TILE=<index> forces one,
@@ -269,8 +269,10 @@ sidp_status sidp_get_tile_index(const sidp_ctx* ctx, int* index);
 
 /* Use tile candidate `index` (see sidp_get_tile) from now on, instead of the autotuner's choice.
  * Index 0 is valid in every mode; the others only for subcell limiting without the smoothness
- * indicator on a Cartesian mesh (the line kernel's indices only for the Euler law); otherwise
- * SIDP_ERR_ARG.  SIDP_ERR_STATE between stages 1 and 3 of an explicit step. */
+ * indicator and the unsparsified mode: on a Cartesian mesh 1..3 (node kernel) and, for the Euler
+ * law, 4..5 (line kernel); on a curved mesh (after sidp_set_geometry) 4, the curved line kernel,
+ * for the Euler law.  Otherwise SIDP_ERR_ARG.  SIDP_ERR_STATE between stages 1 and 3 of an
+ * explicit step.  sidp_set_geometry returns a context to tile 0 and to autotuning. */
 sidp_status sidp_set_tile(sidp_ctx* ctx, int index);
 
 /* Enable (1) or disable (0) CUDA-graph replay in sidp_step (default 1). */
