@@ -149,7 +149,7 @@ __device__ __forceinline__ void curved_face_line(const Instance<T>& I, const Law
 // two element faces Fl (left/lower) and Fr (right/upper); outputs per node r^L (rl), the bounds and
 // K from the node and its two faces on this line, and the prefix sums S at the P subcell faces.
 // w: the quadrature weight of the line (w_a of a row, w_b of a column).
-template <int P, int DIR, class LAW, typename T>
+template <int P, class LAW, typename T>
 __device__ __forceinline__ void curved_line_residuals(const Tables<T>& tab, const LawParamsT<T>& lp,
                                                       const LNode<LAW, T>* nd, const T (*fx)[LAW::NC],
                                                       const T (*fy)[LAW::NC], const T (*r)[2], const T (*qr)[2],
@@ -340,7 +340,7 @@ __device__ __forceinline__ void curved_lines_body(CurvedLineSmem<P, LAW, T>& s, 
     curved_face_line<LAW, T>(I, lp, 2, itS, nd[0].u, nd[0].ax, fx[0], fy[0], FS);
     curved_face_line<LAW, T>(I, lp, 3, itN, nd[P].u, nd[P].ax, fx[P], fy[P], FN);
     T rl[n][NC], lo[n], hi[n], K[n], S[n][NC];
-    curved_line_residuals<P, 1, LAW, T>(tab, lp, nd, fx, fy, r2, q2, FS, FN, wj, rl, lo, hi, K, S);
+    curved_line_residuals<P, LAW, T>(tab, lp, nd, fx, fy, r2, q2, FS, FN, wj, rl, lo, hi, K, S);
 #pragma unroll
     for (int a = 0; a < n; ++a) {
       const int sl = G::rs(le, a) + j;
@@ -379,7 +379,7 @@ __device__ __forceinline__ void curved_lines_body(CurvedLineSmem<P, LAW, T>& s, 
     }
     curved_face_line<LAW, T>(I, lp, 0, itW, nd[0].u, nd[0].ax, fx[0], fy[0], FW);
     curved_face_line<LAW, T>(I, lp, 1, itE, nd[P].u, nd[P].ax, fx[P], fy[P], FE);
-    curved_line_residuals<P, 0, LAW, T>(tab, lp, nd, fx, fy, rr, qq, FW, FE, wj, rlx, lox, hix, Kx, Sx);
+    curved_line_residuals<P, LAW, T>(tab, lp, nd, fx, fy, rr, qq, FW, FE, wj, rlx, lox, hix, Kx, Sx);
   }
   __syncthreads();
 
